@@ -1,0 +1,754 @@
+/*
+ * lelbm_oracle.c -- plain, slow, FP64 CPU reference of the per-timestep cell
+ * update of the Lagrangian entropic lattice Boltzmann method (LELBM),
+ * W. Noh and C. Lee, arXiv:2508.06911.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the timed CPU
+ * baseline of the benchmark load this library.  It shares no code, header or
+ * table with the CUDA library; the product path never calls it.
+ *
+ * Every function follows the paper's equations in the paper's order and
+ * notation, in lattice units (dx = dt = dV = 1, dC = 1 at refinement level 0,
+ * Sec. II.A):
+ *   macroscopic variables ............ Eq. (IIB6)
+ *   equilibrium raw moments .......... Eq. (IIB7), App. A Eq. (A3), (A7)
+ *   non-equilibrium central moments .. Eq. (IIB9)
+ *   shear / bulk split ............... Eq. (IIB10)-(IIB11)
+ *   heat-flux split .................. Eq. (IIB14)
+ *   collision ........................ Eq. (IIB16)-(IIB17)
+ *   normalisation .................... Eq. (IIB18)
+ *   relaxation frequencies ........... App. C Eq. (C7)-(C8)
+ *   Knudsen limiter .................. App. D Eq. (D2)-(D3)
+ *   LAS stencil and refinement ....... Eq. (IIC6), (IIC9)-(IIC11)
+ *   EPR Newton, Maxwellian start ..... Eq. (IID7)-(IID13)
+ *   moment streaming ................. Eq. (IIE3)
+ *   fluid boundaries ................. Sec. III.A
+ * Readings of passages the paper leaves open are marked "reading:" below.
+ *
+ * Build with -ffp-contract=off: every operation then rounds once, on x86-64
+ * and on aarch64 alike, so the stencil membership tests are reproducible.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXF 10 /* N_f in 2D: 1 + D + D(D+1)/2 + D^2 (Eq. IIB14-16) */
+#define ORC_MAXG 6  /* N_g in 2D: 1 + D + D(D+1)/2 (Eq. IIB16-17)        */
+#define ORC_MAXM 11 /* stored moments in 2D: 8 fluon + 3 phonon (Eq. IIB5) */
+
+/* ------------------------------------------------------------------------ */
+/* parameters and results shared with the Python loader (ctypes layout)      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int D;             /* translational dimensions, 1 or 2                   */
+    double K;          /* internal degrees of freedom                        */
+    double nu_s;       /* kinematic shear viscosity, lattice units           */
+    double nu_b;       /* kinematic bulk viscosity; < 0 selects omega_b = 1  */
+    double Pr;         /* Prandtl number                                     */
+    int limiter;       /* 1: Knudsen limiter on (App. D)                     */
+    double n_conf;     /* conformation number n, 4 (Eq. IIC6)                */
+    double r_min;      /* minimum acoustic radius, 2 (Eq. IIC6)              */
+    double refine_div; /* divisor 3 in N_r (Eq. IIC9)                        */
+    double refine_rad; /* factor 3 in the refinement radius (Eq. IIC10)      */
+    int max_refine;    /* cap on N_r                                         */
+    double tol;        /* EPR residual tolerance, 1e-12 (Sec. II.D)          */
+    int max_iter;      /* Newton iteration cap                               */
+} orc_params;
+
+typedef struct {
+    double rho, u[2], RT;
+    double cf[ORC_MAXF]; /* normalised post-collision fluon constraints    */
+    double cg[ORC_MAXG]; /* normalised post-collision phonon constraints   */
+    double omega[3];     /* omega_f, omega_b, omega_h after the limiter    */
+    double Kn;           /* local Knudsen number, Eq. (D2)                 */
+} orc_collision;
+
+typedef struct {
+    double c[2]; /* particle velocity c_i (lattice frame)                    */
+    double dC;   /* velocity volume Delta C_i (Eq. IIA8, IIC11)              */
+    int level;   /* refinement level of the point                           */
+} orc_point;
+
+typedef struct {
+    long long cells;         /* emitting cells processed                    */
+    long long newton_hist[64];/* Newton updates per solve (f and g)          */
+    long long fallback_eq;   /* solves redone with equilibrium constraints  */
+    long long fallback_mx;   /* solves that fell back to Maxwellian weights */
+    long long q_max;         /* largest stencil                             */
+    double disp_max;         /* largest |c_i| (lattice Courant, Eq. IIC3)   */
+} orc_stats;
+
+typedef struct {
+    int D, nx, ny;           /* interior size (ny = 1 in 1D)                */
+    int periodic[2];         /* per axis                                    */
+    int pad;                 /* pad layers on every non-periodic side       */
+    int bc[4];               /* x-, x+, y-, y+: 0 outflow, 1 inflow         */
+    double inlet[4];         /* rho, ux, uy, RT of the inflow state         */
+    const unsigned char* solid; /* padded-grid solid flags or NULL          */
+} orc_grid;
+
+int orc_nmom(int D) { return D == 1 ? 6 : 11; }
+int orc_nf(int D) { return D == 1 ? 4 : 10; }
+int orc_ng(int D) { return D == 1 ? 3 : 6; }
+
+/* Stored-moment positions (Eq. IIB5): 1D {M0,Mx,Mxx,MDx,G0,Gx},
+ * 2D {M0,Mx,My,Mxx,Mxy,Myy,MDx,MDy,G0,Gx,Gy}.                              */
+static int iM1(int D, int a) { (void)D; return 1 + a; }
+static int iM2(int D, int a, int b) {
+    if (D == 1) return 2;
+    if (a == 0 && b == 0) return 3;
+    if (a == 1 && b == 1) return 5;
+    return 4;
+}
+static int iMD(int D, int g) { return D == 1 ? 3 : 6 + g; }
+static int iG0(int D) { return D == 1 ? 4 : 8; }
+static int iG1(int D, int g) { return D == 1 ? 5 : 9 + g; }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (IIB7) with App. A Eq. (A3a-b), (A3g), (A7a-b): equilibrium raw moments */
+/* ------------------------------------------------------------------------ */
+void orc_eq_moments(int D, double K, double rho, const double* u, double RT, double* M)
+{
+    double usq = 0.0;
+    for (int a = 0; a < D; a++) usq += u[a] * u[a];
+    for (int i = 0; i < orc_nmom(D); i++) M[i] = 0.0;
+    M[0] = rho;                                             /* (A3a) */
+    for (int a = 0; a < D; a++) M[iM1(D, a)] = rho * u[a]; /* (A3b) */
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++)                          /* (IIB7a) */
+            M[iM2(D, a, b)] = rho * (u[a] * u[b] + (a == b ? RT : 0.0));
+    for (int g = 0; g < D; g++)                              /* (IIB7b) */
+        M[iMD(D, g)] = rho * (usq + (D + 2) * RT) * u[g];
+    M[iG0(D)] = rho * K * RT;                                /* (IIB7c) */
+    for (int g = 0; g < D; g++) M[iG1(D, g)] = rho * K * RT * u[g]; /* (IIB7d) */
+}
+
+/* Eq. (IIB6): density, velocity and temperature from the raw moments. */
+void orc_macros(int D, double K, const double* M, double* rho, double* u, double* RT)
+{
+    double r = M[0];
+    double usq = 0.0, trace = 0.0;
+    for (int a = 0; a < D; a++) {
+        u[a] = M[iM1(D, a)] / r;
+        usq += u[a] * u[a];
+        trace += M[iM2(D, a, a)];
+    }
+    *rho = r;
+    *RT = ((trace + M[iG0(D)]) / r - usq) / (D + K);
+}
+
+/* Eq. (IIB9): non-equilibrium central moments.
+ * out: P[a][b] = M~neq_ab, Q[g] = M~neq_Dg, *G0n = G~neq_0, Gn[g] = G~neq_g. */
+void orc_neq(int D, double K, const double* M, double rho, const double* u, double RT,
+             double* P /* [2][2] */, double* Q, double* G0n, double* Gn)
+{
+    double usq = 0.0;
+    for (int a = 0; a < D; a++) usq += u[a] * u[a];
+    for (int a = 0; a < D; a++)                               /* (IIB9a) */
+        for (int b = 0; b < D; b++)
+            P[2 * a + b] = M[iM2(D, a, b)] - rho * (u[a] * u[b] + (a == b ? RT : 0.0));
+    double trP = 0.0;
+    for (int a = 0; a < D; a++) trP += P[2 * a + a];
+    for (int g = 0; g < D; g++) {                             /* (IIB9b) */
+        double s = 0.0;
+        for (int a = 0; a < D; a++) s += u[a] * P[2 * a + g];
+        Q[g] = M[iMD(D, g)] - 2.0 * s - u[g] * trP - rho * (usq + (D + 2) * RT) * u[g];
+    }
+    *G0n = M[iG0(D)] - rho * K * RT;                          /* (IIB9c) */
+    for (int g = 0; g < D; g++) Gn[g] = M[iG1(D, g)] - u[g] * M[iG0(D)]; /* (IIB9d) */
+}
+
+/* App. C Eq. (C7)-(C8): implicit collision frequencies from the kinematic
+ * transport coefficients.  nu_s = mu_s/rho = RT (1/omega_f - 1/2);
+ * Pr = mu_s C_p / kappa gives 1/omega_h - 1/2 = (1/omega_f - 1/2) / Pr;
+ * nu_b = RT (2/D - 2/(D+K)) (1/omega_b - 1/2), or omega_b = 1 (Sec. II.B). */
+void orc_omegas(int D, double K, double RT, double nu_s, double nu_b, double Pr, double* om)
+{
+    double inv_f = nu_s / RT + 0.5;
+    om[0] = 1.0 / inv_f;
+    double fb = 2.0 / D - 2.0 / (D + K);
+    if (nu_b < 0.0 || fb <= 0.0)
+        om[1] = 1.0;
+    else
+        om[1] = 1.0 / (nu_b / (RT * fb) + 0.5);
+    om[2] = 1.0 / ((inv_f - 0.5) / Pr + 0.5);
+}
+
+/* App. D Eq. (D2): local Knudsen number.  reading: every moment is
+ * normalised by rho (G too), the first sum runs over all index pairs
+ * (alpha, beta), the second over the components gamma. */
+double orc_knudsen(int D, double K, double rho, double RT, const double* P, const double* Q,
+                   double G0n, const double* Gn)
+{
+    double s2 = 0.0, s3 = 0.0;
+    for (int a = 0; a < D; a++)
+        for (int b = 0; b < D; b++) s2 += fabs(P[2 * a + b] / rho);
+    s2 += fabs(G0n / rho);
+    for (int g = 0; g < D; g++) s3 += fabs(Q[g] / rho) + fabs(Gn[g] / rho);
+    double k2 = s2 / ((D + K) * RT);
+    double k3 = s3 / ((D + K + 2) * pow(RT, 1.5));
+    return k2 > k3 ? k2 : k3;
+}
+
+/* App. D Eq. (D3) with the thresholds stated after it (Kn*_L = -2,
+ * Kn*_H = -1, omega_H = 1).  reading: the case labels of (D3b) are taken
+ * from the text: no change below Kn = 0.01, equilibrium above Kn = 0.1,
+ * linear in log10 Kn in between. */
+double orc_limit_omega(double Kn, double omega)
+{
+    const double kl = -2.0, kh = -1.0, wh = 1.0;
+    if (!(Kn > 0.0)) return omega;
+    double ks = log10(Kn);
+    if (ks <= kl) return omega;
+    if (ks >= kh) return wh;
+    return (wh - omega) / (kh - kl) * (ks - kl) + omega;
+}
+
+/* Collision module (Fig. collision_module): Eq. (IIB6), (IIB9)-(IIB18). */
+void orc_collide(const orc_params* p, const double* M, orc_collision* out)
+{
+    int D = p->D;
+    double K = p->K;
+    double rho, u[2] = {0, 0}, RT;
+    orc_macros(D, K, M, &rho, u, &RT);
+    double P[4] = {0, 0, 0, 0}, Q[2] = {0, 0}, G0n, Gn[2] = {0, 0};
+    orc_neq(D, K, M, rho, u, RT, P, Q, &G0n, Gn);
+
+    double om[3];
+    orc_omegas(D, K, RT, p->nu_s, p->nu_b, p->Pr, om);
+    double Kn = orc_knudsen(D, K, rho, RT, P, Q, G0n, Gn);
+    if (p->limiter)
+        for (int i = 0; i < 3; i++) om[i] = orc_limit_omega(Kn, om[i]);
+    double wf = om[0], wb = om[1], wh = om[2];
+
+    /* Eq. (IIB10)-(IIB11): bulk and shear parts of M~neq_ab. */
+    double bulk = -G0n / D;
+    double shear[4];
+    for (int a = 0; a < D; a++)
+        for (int b = 0; b < D; b++) shear[2 * a + b] = P[2 * a + b] - (a == b ? bulk : 0.0);
+
+    /* Eq. (IIB14): per-dimension heat-flux constraints M~neq_{aa|g}. */
+    double h[2][2];
+    for (int a = 0; a < D; a++)
+        for (int g = 0; g < D; g++) h[a][g] = (1.0 + 2.0 * (a == g)) / (D + 2) * Q[g];
+
+    /* Eq. (IIB16)-(IIB17), normalised by Eq. (IIB18).  Constraint order
+     * follows the basis T_j of orc_basis_f / orc_basis_g below. */
+    double *cf = out->cf, *cg = out->cg;
+    for (int j = 0; j < ORC_MAXF; j++) cf[j] = 0.0;
+    for (int j = 0; j < ORC_MAXG; j++) cg[j] = 0.0;
+    cf[0] = (rho) / rho;                   /* (IIB16a) M~*_0 = rho        */
+    /* (IIB16b): M~*_a = 0 -> cf[1..D] stay zero                          */
+    int j = 1 + D;
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++) {      /* (IIB16c)                     */
+            double m = rho * RT * (a == b) + (1.0 - wf) * shear[2 * a + b] +
+                       (1.0 - wb) * (a == b ? bulk : 0.0);
+            cf[j++] = m / rho;
+        }
+    for (int g = 0; g < D; g++)            /* (IIB16d)                     */
+        for (int a = 0; a < D; a++) cf[j++] = (1.0 - wh) * h[a][g] / rho;
+
+    if (K > 0.0) {
+        double nrm = rho * K * RT;
+        cg[0] = (rho * K * RT + (1.0 - wb) * G0n) / nrm;          /* (IIB16e) */
+        for (int g = 0; g < D; g++) cg[1 + g] = (1.0 - wh) * Gn[g] / nrm; /* (IIB16f) */
+        int k = 1 + D;
+        for (int a = 0; a < D; a++)
+            for (int b = a; b < D; b++)                            /* (IIB17) */
+                cg[k++] = (a == b) ? rho * K * RT * RT / nrm : 0.0;
+    }
+    out->rho = rho;
+    out->u[0] = u[0];
+    out->u[1] = D == 2 ? u[1] : 0.0;
+    out->RT = RT;
+    out->omega[0] = wf;
+    out->omega[1] = wb;
+    out->omega[2] = wh;
+    out->Kn = Kn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lagrangian acoustic stencils, Eq. (IIC6), (IIC9)-(IIC11)                 */
+/* ------------------------------------------------------------------------ */
+
+/* [x]: round half away from zero (C99 round). */
+static double rnd(double x) { return round(x); }
+
+/* Eq. (IIC6): R_ac = max([n sqrt(RT)], r_min). */
+int orc_acoustic_radius(const orc_params* p, double RT)
+{
+    double r = rnd(p->n_conf * sqrt(RT));
+    if (r < p->r_min) r = p->r_min;
+    return (int)r;
+}
+
+/* Eq. (IIC9): N_r = [1 / (3 sqrt(RT))], capped at max_refine. */
+int orc_refine_levels(const orc_params* p, double RT)
+{
+    double n = rnd(1.0 / (p->refine_div * sqrt(RT)));
+    if (n > p->max_refine) n = p->max_refine;
+    return (int)n;
+}
+
+static double dist2(int D, const double* c, const double* u)
+{
+    double s = 0.0;
+    for (int a = 0; a < D; a++) {
+        double d = c[a] - u[a];
+        s = s + d * d;
+    }
+    return s;
+}
+
+/* LAS module (Fig. las_module).  reading of Eq. (IIC6): level-0 points are
+ * the integer velocities whose distance to the unrounded bulk velocity is at
+ * most R_ac + 1/2 (inclusive); this reproduces the 284 points of Fig. 3.
+ * reading of Eq. (IIC10)-(IIC11): for Lvl = 1..N_r every point of level
+ * Lvl-1 within 3 * 0.5^Lvl of u is replaced by 2^D children at +-h/4 per
+ * axis (h = its spacing) with dC scaled by 0.5^D; this reproduces the 41
+ * points of Fig. 4.  Returns q, or -q_needed when max_pts is too small. */
+int orc_las(int D, const double* u_in, double RT, const orc_params* p, orc_point* pts, int max_pts)
+{
+    double u[2] = {u_in[0], D == 2 ? u_in[1] : 0.0};
+    int R = orc_acoustic_radius(p, RT);
+    double rr = R + 0.5;
+    double rr2 = rr * rr;
+    int Nr = orc_refine_levels(p, RT);
+
+    /* level 0: scan the bounding box, keep the disk */
+    int lo[2], hi[2];
+    for (int a = 0; a < 2; a++) {
+        if (a < D) {
+            lo[a] = (int)floor(u[a] - rr) - 1;
+            hi[a] = (int)ceil(u[a] + rr) + 1;
+        } else {
+            lo[a] = hi[a] = 0;
+        }
+    }
+    int cap = 64;
+    orc_point* cur = (orc_point*)malloc(sizeof(orc_point) * cap);
+    int n = 0;
+    for (int cy = lo[1]; cy <= hi[1]; cy++)
+        for (int cx = lo[0]; cx <= hi[0]; cx++) {
+            double c[2] = {(double)cx, (double)cy};
+            if (dist2(D, c, u) <= rr2) {
+                if (n == cap) {
+                    cap *= 2;
+                    cur = (orc_point*)realloc(cur, sizeof(orc_point) * cap);
+                }
+                cur[n].c[0] = c[0];
+                cur[n].c[1] = D == 2 ? c[1] : 0.0;
+                cur[n].dC = 1.0;
+                cur[n].level = 0;
+                n++;
+            }
+        }
+
+    /* internal refinement, one level at a time */
+    double h = 1.0;
+    for (int L = 1; L <= Nr; L++) {
+        double rad = p->refine_rad * pow(0.5, L);
+        double rad2 = rad * rad;
+        int cap2 = n * (1 << D) + 8;
+        orc_point* nxt = (orc_point*)malloc(sizeof(orc_point) * cap2);
+        int m = 0;
+        for (int i = 0; i < n; i++) {
+            if (cur[i].level == L - 1 && dist2(D, cur[i].c, u) <= rad2) {
+                double q4 = h / 4.0;
+                int nch = 1 << D;
+                for (int k = 0; k < nch; k++) {
+                    orc_point ch = cur[i];
+                    ch.c[0] = cur[i].c[0] + ((k & 1) ? q4 : -q4);
+                    if (D == 2) ch.c[1] = cur[i].c[1] + ((k & 2) ? q4 : -q4);
+                    ch.dC = cur[i].dC * pow(0.5, D);
+                    ch.level = L;
+                    nxt[m++] = ch;
+                }
+            } else {
+                nxt[m++] = cur[i];
+            }
+        }
+        free(cur);
+        cur = nxt;
+        n = m;
+        h = h / 2.0;
+    }
+    if (n > max_pts) {
+        free(cur);
+        return -n;
+    }
+    memcpy(pts, cur, sizeof(orc_point) * n);
+    free(cur);
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Entropic population reconstruction, Eq. (IID7)-(IID13)                   */
+/* ------------------------------------------------------------------------ */
+
+/* Fluon basis T_j(c~): 1, c~_a, c~_a c~_b (a <= b), c~_a^2 c~_g (Eq. IIB14-16),
+ * ordered g-major: (xx|x, yy|x, xx|y, yy|y) in 2D. Order of each in ord. */
+void orc_basis_f(int D, const double* ct, double* T, int* ord)
+{
+    int j = 0;
+    T[j] = 1.0; if (ord) ord[j] = 0; j++;
+    for (int a = 0; a < D; a++) { T[j] = ct[a]; if (ord) ord[j] = 1; j++; }
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++) { T[j] = ct[a] * ct[b]; if (ord) ord[j] = 2; j++; }
+    for (int g = 0; g < D; g++)
+        for (int a = 0; a < D; a++) { T[j] = ct[a] * ct[a] * ct[g]; if (ord) ord[j] = 3; j++; }
+}
+
+/* Phonon basis: 1, c~_g, c~_a c~_b (a <= b) (Eq. IIB16e-f, IIB17). */
+void orc_basis_g(int D, const double* ct, double* T, int* ord)
+{
+    int j = 0;
+    T[j] = 1.0; if (ord) ord[j] = 0; j++;
+    for (int a = 0; a < D; a++) { T[j] = ct[a]; if (ord) ord[j] = 1; j++; }
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++) { T[j] = ct[a] * ct[b]; if (ord) ord[j] = 2; j++; }
+}
+
+/* Plain Cholesky factorisation A = L L^T and solve A x = b (Golub & Van Loan).
+ * A is n x n row-major and is overwritten by L; b is overwritten by x.
+ * Returns 0, or -1 on a non-positive pivot. */
+int orc_cholesky_solve(int n, double* A, double* b)
+{
+    for (int j = 0; j < n; j++) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; k++) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0)) return -1;
+        double d = sqrt(s);
+        A[j * n + j] = d;
+        for (int i = j + 1; i < n; i++) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; k++) t -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = t / d;
+        }
+    }
+    for (int i = 0; i < n; i++) { /* L y = b */
+        double t = b[i];
+        for (int k = 0; k < i; k++) t -= A[i * n + k] * b[k];
+        b[i] = t / A[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) { /* L^T x = y */
+        double t = b[i];
+        for (int k = i + 1; k < n; k++) t -= A[k * n + i] * b[k];
+        b[i] = t / A[i * n + i];
+    }
+    return 0;
+}
+
+/* Eq. (IID13): Maxwellian start, lambda_0 = -1 + D/2 ln(2 pi RT),
+ * lambda_ab = delta_ab / (2 RT), all others 0 (for f and g alike). */
+void orc_maxwell_lambda(int D, int kind, double RT, double* lam)
+{
+    int n = kind == 0 ? orc_nf(D) : orc_ng(D);
+    for (int j = 0; j < n; j++) lam[j] = 0.0;
+    lam[0] = -1.0 + 0.5 * D * log(2.0 * M_PI * RT);
+    int j = 1 + D;
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++) { lam[j] = (a == b) ? 1.0 / (2.0 * RT) : 0.0; j++; }
+}
+
+/* EPR module (Fig. epr_module).  Newton-Raphson on the Lagrange multipliers
+ * of f'_i = dC_i exp[-(1 + sum_j lambda_j T_j(c~_i))] (Eq. IID7), with
+ * A_ij = sum_k T_i f_k T_j (IID11a), dM_i = sum_k T_i f_k - M~'_i (IID11c),
+ * A dLambda = dM (IID10) solved by Cholesky (Sec. II.D), lambda += dLambda
+ * (IID9).  reading: converged when max_j |dM_j| / sqrt(RT)^order_j <= tol
+ * (the residual in thermal units), followed by one more (polishing) update.
+ * kind 0: fluons (basis orc_basis_f), 1: phonons (orc_basis_g).
+ * lam holds the start on entry (NULL-equivalent: caller fills Eq. IID13) and
+ * the solution on exit; pop receives f'_i.  Returns the number of updates,
+ * or -1 (Cholesky breakdown or non-finite value), -2 (iteration cap). */
+int orc_epr(int D, int kind, int q, const orc_point* pts, const double* u, double RT,
+            const double* con, const orc_params* p, double* lam, double* pop)
+{
+    int n = kind == 0 ? orc_nf(D) : orc_ng(D);
+    int ord[ORC_MAXF];
+    double T[ORC_MAXF];
+    double scale[ORC_MAXF];
+    double ct0[2] = {0.0, 0.0};
+    if (kind == 0) orc_basis_f(D, ct0, T, ord); else orc_basis_g(D, ct0, T, ord);
+    for (int j = 0; j < n; j++) scale[j] = pow(sqrt(RT), ord[j]);
+
+    int updates = 0, polished = 0;
+    for (int it = 0;; it++) {
+        double r[ORC_MAXF];
+        for (int j = 0; j < n; j++) r[j] = 0.0;
+        for (int k = 0; k < q; k++) {
+            double ct[2] = {pts[k].c[0] - u[0], D == 2 ? pts[k].c[1] - u[1] : 0.0};
+            if (kind == 0) orc_basis_f(D, ct, T, NULL); else orc_basis_g(D, ct, T, NULL);
+            double e = 1.0;
+            for (int j = 0; j < n; j++) e += lam[j] * T[j];
+            pop[k] = pts[k].dC * exp(-e);                       /* (IID7)  */
+            for (int j = 0; j < n; j++) r[j] += T[j] * pop[k];
+        }
+        double rmax = 0.0;
+        for (int j = 0; j < n; j++) {
+            r[j] -= con[j];                                    /* (IID11c) */
+            if (!isfinite(r[j])) return -1;
+            double a = fabs(r[j]) / scale[j];
+            if (a > rmax) rmax = a;
+        }
+        if (polished) return updates;
+        int conv = rmax <= p->tol;
+        if (!conv && it >= p->max_iter) return -2;
+
+        double A[ORC_MAXF * ORC_MAXF];                          /* (IID11a) */
+        for (int i = 0; i < n * n; i++) A[i] = 0.0;
+        for (int k = 0; k < q; k++) {
+            double ct[2] = {pts[k].c[0] - u[0], D == 2 ? pts[k].c[1] - u[1] : 0.0};
+            if (kind == 0) orc_basis_f(D, ct, T, NULL); else orc_basis_g(D, ct, T, NULL);
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) A[i * n + j] += T[i] * pop[k] * T[j];
+        }
+        if (orc_cholesky_solve(n, A, r) != 0) return -1;        /* (IID10) */
+        for (int j = 0; j < n; j++) lam[j] += r[j];            /* (IID9)  */
+        updates++;
+        if (conv) polished = 1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* single-cell operation and moment streaming                               */
+/* ------------------------------------------------------------------------ */
+
+static void equilibrium_constraints(int D, double RT, double* cf, double* cg)
+{
+    for (int j = 0; j < ORC_MAXF; j++) cf[j] = 0.0;
+    for (int j = 0; j < ORC_MAXG; j++) cg[j] = 0.0;
+    cf[0] = 1.0;
+    cg[0] = 1.0;
+    int j = 1 + D;
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++) {
+            cf[j] = (a == b) ? RT : 0.0;
+            cg[j] = (a == b) ? RT : 0.0;
+            j++;
+        }
+}
+
+/* reading (failure handling, not in the paper): a solve that breaks down
+ * is redone for f and g with the equilibrium constraints (omega = 1, the
+ * Knudsen limiter's end state); if that also fails, the populations are the
+ * Maxwellian weights of Eq. (IID12) scaled to carry the exact mass. */
+static int solve_cell(const orc_params* p, int q, const orc_point* pts, const orc_collision* co,
+                      double* popf, double* popg, orc_stats* st)
+{
+    int D = p->D;
+    int has_g = p->K > 0.0;
+    double lf[ORC_MAXF], lg[ORC_MAXG];
+    orc_maxwell_lambda(D, 0, co->RT, lf);
+    int sf = orc_epr(D, 0, q, pts, co->u, co->RT, co->cf, p, lf, popf);
+    int sg = 0;
+    if (has_g) {
+        orc_maxwell_lambda(D, 1, co->RT, lg);
+        sg = orc_epr(D, 1, q, pts, co->u, co->RT, co->cg, p, lg, popg);
+    }
+    if (sf >= 0 && sg >= 0) {
+        if (st) {
+            st->newton_hist[sf < 63 ? sf : 63]++;
+            if (has_g) st->newton_hist[sg < 63 ? sg : 63]++;
+        }
+        return 0;
+    }
+    double cf[ORC_MAXF], cg[ORC_MAXG];
+    equilibrium_constraints(D, co->RT, cf, cg);
+    orc_maxwell_lambda(D, 0, co->RT, lf);
+    sf = orc_epr(D, 0, q, pts, co->u, co->RT, cf, p, lf, popf);
+    sg = 0;
+    if (has_g) {
+        orc_maxwell_lambda(D, 1, co->RT, lg);
+        sg = orc_epr(D, 1, q, pts, co->u, co->RT, cg, p, lg, popg);
+    }
+    if (sf >= 0 && sg >= 0) {
+        if (st) st->fallback_eq++;
+        return 1;
+    }
+    double s = 0.0;
+    for (int k = 0; k < q; k++) {
+        double ct[2] = {pts[k].c[0] - co->u[0], D == 2 ? pts[k].c[1] - co->u[1] : 0.0};
+        double w = pts[k].dC * exp(-dist2(D, ct, (double[2]){0.0, 0.0}) / (2.0 * co->RT));
+        popf[k] = w;
+        s += w;
+    }
+    for (int k = 0; k < q; k++) {
+        popf[k] /= s;
+        if (has_g) popg[k] = popf[k];
+    }
+    if (st) st->fallback_mx++;
+    return 2;
+}
+
+/* Populations of one cell: collision, LAS and EPR (Fig. LELBM_algorithm
+ * steps 1-3).  pts, popf, popg must hold max_pts entries.  Returns q (or
+ * -q_needed), *status the fallback level (0, 1 or 2). */
+int orc_cell_populations(const orc_params* p, const double* M, orc_collision* co, orc_point* pts,
+                         double* popf, double* popg, int max_pts, int* status)
+{
+    orc_collide(p, M, co);
+    int q = orc_las(p->D, co->u, co->RT, p, pts, max_pts);
+    if (q < 0) return q;
+    *status = solve_cell(p, q, pts, co, popf, popg, NULL);
+    return q;
+}
+
+/* Raw moment basis of the stored moments (Eq. IIB5, IIE3a):
+ * fluons 1, c_a, c_a c_b (a <= b), |c|^2 c_g; phonons 1, c_g. */
+static void raw_contrib(int D, const double* c, double mf, double mg, double* dM)
+{
+    double csq = 0.0;
+    for (int a = 0; a < D; a++) csq += c[a] * c[a];
+    dM[0] = mf;
+    for (int a = 0; a < D; a++) dM[iM1(D, a)] = c[a] * mf;
+    for (int a = 0; a < D; a++)
+        for (int b = a; b < D; b++) dM[iM2(D, a, b)] = c[a] * c[b] * mf;
+    for (int g = 0; g < D; g++) dM[iMD(D, g)] = csq * c[g] * mf;
+    dM[iG0(D)] = mg;
+    for (int g = 0; g < D; g++) dM[iG1(D, g)] = c[g] * mg;
+}
+
+static int grid_NX(const orc_grid* g) { return g->nx + (g->periodic[0] ? 0 : 2 * g->pad); }
+static int grid_NY(const orc_grid* g)
+{
+    if (g->D == 1) return 1;
+    return g->ny + (g->periodic[1] ? 0 : 2 * g->pad);
+}
+
+/* Sec. III.A fluid boundary: pad cells take, on an inflow side, the
+ * equilibrium moments of the prescribed state (non-equilibrium dropped),
+ * elsewhere the full raw moments of the nearest interior cell.
+ * reading: "first-order extrapolation" is the zero-gradient copy; an inflow
+ * side wins at corners (x sides before y sides). */
+void orc_fill_pads(const orc_grid* g, const orc_params* p, double* M)
+{
+    int D = g->D, NX = grid_NX(g), NY = grid_NY(g), nm = orc_nmom(D);
+    long ncell = (long)NX * NY;
+    int px = g->periodic[0] ? 0 : g->pad;
+    int py = (D == 1 || g->periodic[1]) ? 0 : g->pad;
+    int ny = D == 1 ? 1 : g->ny;
+    double Meq[ORC_MAXM];
+    double uin[2] = {g->inlet[1], g->inlet[2]};
+    orc_eq_moments(D, p->K, g->inlet[0], uin, g->inlet[3], Meq);
+    for (int iy = 0; iy < NY; iy++)
+        for (int ix = 0; ix < NX; ix++) {
+            int inx = ix >= px && ix < px + g->nx;
+            int iny = iy >= py && iy < py + ny;
+            if (inx && iny) continue;
+            int inflow = 0;
+            if (ix < px && g->bc[0] == 1) inflow = 1;
+            if (ix >= px + g->nx && g->bc[1] == 1) inflow = 1;
+            if (D == 2 && iy < py && g->bc[2] == 1) inflow = 1;
+            if (D == 2 && iy >= py + ny && g->bc[3] == 1) inflow = 1;
+            long dst = (long)iy * NX + ix;
+            if (inflow) {
+                for (int m = 0; m < nm; m++) M[m * ncell + dst] = Meq[m];
+            } else {
+                int sx = ix < px ? px : (ix >= px + g->nx ? px + g->nx - 1 : ix);
+                int sy = iy < py ? py : (iy >= py + ny ? py + ny - 1 : iy);
+                long src = (long)sy * NX + sx;
+                for (int m = 0; m < nm; m++) M[m * ncell + dst] = M[m * ncell + src];
+            }
+        }
+}
+
+/* Landing cell along one axis; returns -1 when the population leaves the
+ * interior of a padded axis (it is discarded, Sec. III) . */
+static int land_axis(int i, int n, int pad, int periodic)
+{
+    if (periodic) {
+        int r = i % n;
+        return r < 0 ? r + n : r;
+    }
+    if (i < pad || i >= pad + n) return -1;
+    return i;
+}
+
+/* One time step over a padded grid: fill the pads, then for every non-solid
+ * cell run collision, LAS and EPR and stream the moment fractions
+ * T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i to x + c_i (Eq. IIE3).
+ * reading: a refined point lands off the lattice; its fractions are shared
+ * between the cells it overlaps by cloud-in-cell weights (cell averaging,
+ * Eq. IIA10-11).  Min and Mout are SoA [nmom][NY*NX]; Min is not modified.
+ * Returns 0, or -1 on allocation failure. */
+int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* Mout, orc_stats* st)
+{
+    int D = g->D, NX = grid_NX(g), NY = grid_NY(g), nm = orc_nmom(D);
+    long ncell = (long)NX * NY;
+    int px = g->periodic[0] ? 0 : g->pad;
+    int py = (D == 1 || g->periodic[1]) ? 0 : g->pad;
+    int ny = D == 1 ? 1 : g->ny;
+    double* W = (double*)malloc(sizeof(double) * nm * ncell);
+    if (!W) return -1;
+    memcpy(W, Min, sizeof(double) * nm * ncell);
+    orc_fill_pads(g, p, W);
+    memset(Mout, 0, sizeof(double) * nm * ncell);
+
+    int cap = 4096;
+    orc_point* pts = (orc_point*)malloc(sizeof(orc_point) * cap);
+    double* popf = (double*)malloc(sizeof(double) * cap);
+    double* popg = (double*)malloc(sizeof(double) * cap);
+    for (int iy = 0; iy < NY; iy++)
+        for (int ix = 0; ix < NX; ix++) {
+            long cell = (long)iy * NX + ix;
+            if (g->solid && g->solid[cell]) continue;
+            double M[ORC_MAXM];
+            for (int m = 0; m < nm; m++) M[m] = W[m * ncell + cell];
+            orc_collision co;
+            orc_collide(p, M, &co);
+            int q = orc_las(D, co.u, co.RT, p, pts, cap);
+            if (q < 0) {
+                cap = -q;
+                pts = (orc_point*)realloc(pts, sizeof(orc_point) * cap);
+                popf = (double*)realloc(popf, sizeof(double) * cap);
+                popg = (double*)realloc(popg, sizeof(double) * cap);
+                q = orc_las(D, co.u, co.RT, p, pts, cap);
+            }
+            solve_cell(p, q, pts, &co, popf, popg, st);
+            if (st) {
+                st->cells++;
+                if (q > st->q_max) st->q_max = q;
+            }
+            double mscale = co.rho;                  /* rho dV f'   (IIE3a) */
+            double gscale = co.rho * p->K * co.RT;   /* rho K RT dV g'      */
+            for (int k = 0; k < q; k++) {
+                const double* c = pts[k].c;
+                if (st) {
+                    double cm = sqrt(dist2(D, c, (double[2]){0.0, 0.0}));
+                    if (cm > st->disp_max) st->disp_max = cm;
+                }
+                double dM[ORC_MAXM];
+                raw_contrib(D, c, mscale * popf[k], p->K > 0.0 ? gscale * popg[k] : 0.0, dM);
+                /* cloud-in-cell split of the landing position x + c */
+                int i0[2] = {0, 0};
+                double w1[2] = {0.0, 0.0};
+                for (int a = 0; a < D; a++) {
+                    double fl = floor(c[a]);
+                    i0[a] = (int)fl;
+                    w1[a] = c[a] - fl;
+                }
+                int ncx = w1[0] > 0.0 ? 2 : 1;
+                int ncy = (D == 2 && w1[1] > 0.0) ? 2 : 1;
+                for (int sy = 0; sy < ncy; sy++)
+                    for (int sx = 0; sx < ncx; sx++) {
+                        double w = (sx ? w1[0] : 1.0 - w1[0]);
+                        if (D == 2) w *= (sy ? w1[1] : 1.0 - w1[1]);
+                        /* px = 0 on a periodic axis, py likewise */
+                        int tx = land_axis(ix + i0[0] + sx, g->nx, px, g->periodic[0]);
+                        int ty = 0;
+                        if (D == 2) ty = land_axis(iy + i0[1] + sy, ny, py, g->periodic[1]);
+                        if (tx < 0 || ty < 0) continue;
+                        long tgt = (long)ty * NX + tx;
+                        if (g->solid && g->solid[tgt]) continue;
+                        for (int m = 0; m < nm; m++) Mout[m * ncell + tgt] += w * dM[m];
+                    }
+            }
+        }
+    free(pts);
+    free(popf);
+    free(popg);
+    free(W);
+    return 0;
+}
