@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the LELBM time step on GB300 (one JSON line on rank 0).
+
+Default workload: 4096 seeded 1D Riemann problems of uneven length (256-4096 cells,
+log-uniform), pressure ratios 10-1000, |u| up to Mach 3, one batch handle.  A step is
+one time step of every instance (fluid-boundary fill, collision, LAS, EPR, moment
+streaming).  MLUPS = interior cell updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batch1d|hotbox2d|riemann2d]
+
+--impl reference times the plain FP64 CPU oracle (the correctness reference) on a
+bounded sample of the same workload.  Under torchrun each rank runs its own batch
+(weak scaling, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline, FP32+learned-EPR vs plain FP64, at matched L1 error"
+
+# Algorithmic FP64 work per stencil point and Newton pass: exponent (N FMA), residual (N FMA)
+# and the packed Jacobian (N(N+1)/2 FMA) for N constraints; moment streaming: one multiply and
+# one add per stored moment.  Exponentials are not counted.
+N_F = {1: 4, 2: 10}
+N_G = {1: 3, 2: 6}
+N_M = {1: 6, 2: 11}
+
+
+def newton_flops(n: int) -> int:
+    return 2 * (2 * n + n * (n + 1) // 2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch1d", choices=["batch1d", "hotbox2d", "riemann2d"])
+    ap.add_argument("--n-batch", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=1024, help="2D grid size")
+    ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def make_workload(args, rank):
+    from paper_2508_06911_gb300 import workloads as W
+
+    if args.workload == "batch1d":
+        w = W.riemann_1d_batch(n_batch=args.n_batch, seed_index=1 + 1000 * rank)
+        desc = {"workload": f"riemann1d_batch_{args.n_batch}", "dims": 1, "instances": args.n_batch,
+                "lengths": "256-4096 log-uniform", "pressure_ratio": "10-1000", "mach_max": 3,
+                "interior_cells": int(w.lengths.sum()), "pad_cells": int(2 * w.pads.sum())}
+        return w, desc
+    if args.workload == "hotbox2d":
+        w = W.hot_box(2, args.n, args.rt)
+        return w, {"workload": f"hotbox2d_{args.n}x{args.n}_RT{args.rt}", "dims": 2, "u": [10, 10],
+                   "interior_cells": args.n * args.n}
+    w = W.riemann_2d(n=args.n, seed_index=2 + 1000 * rank)
+    return w, {"workload": f"riemann2d_{args.n}x{args.n}", "dims": 2, "interior_cells": args.n * args.n}
+
+
+def clock_sampler_start():
+    out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=out, stderr=subprocess.DEVNULL)
+    except Exception:
+        p = None
+    return p, out.name
+
+
+def clock_sampler_stop(state, gpu_index=0):
+    p, path = state
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or not f[0].isdigit() or int(f[0]) != gpu_index:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    os.unlink(path)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, budget_s=15.0):
+    """The CPU oracle, as it stands (serial FP64 C), on a bounded sample of the workload."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle as O
+    from parity_util import oracle_1d_instance, oracle_2d
+    from paper_2508_06911_gb300 import workloads as W
+
+    O.build()
+    t0 = time.perf_counter()
+    cells = 0
+    if args.workload == "batch1d":
+        w = W.riemann_1d_batch(n_batch=args.n_batch, seed_index=1)
+        b = 0
+        while time.perf_counter() - t0 < budget_s and b < w.n_batch:
+            oracle_1d_instance(w, b, 1)
+            cells += int(w.lengths[b])
+            b += 1
+        sample = f"first {b} instances of the batch ({cells} interior cells), one time step each"
+    else:
+        n = 64
+        w = W.hot_box(2, n, args.rt) if args.workload == "hotbox2d" else W.riemann_2d(n=n, seed_index=2)
+        steps = 0
+        while time.perf_counter() - t0 < budget_s:
+            oracle_2d(w, 1)
+            cells += n * n
+            steps += 1
+        sample = f"{n}x{n} crop-size instance of the workload, {steps} time steps"
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": round(dt, 2)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """Reference arm: the CPU oracle, each step a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle as O
+    from parity_util import oracle_1d_instance, oracle_2d
+    from paper_2508_06911_gb300 import workloads as W
+
+    O.build()
+    w, desc = make_workload(args, 0)
+    per_step = []
+    cells_step = 0
+
+    def one_step():
+        nonlocal cells_step
+        c = 0
+        if args.workload == "batch1d":
+            for b in range(16):
+                oracle_1d_instance(w, b, 1)
+                c += int(w.lengths[b])
+        else:
+            small = W.hot_box(2, 48, args.rt) if args.workload == "hotbox2d" else W.riemann_2d(n=48, seed_index=2)
+            oracle_2d(small, 1)
+            c = 48 * 48
+        cells_step = c
+        return c
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    tot = 0
+    for _ in range(args.steps):
+        ts = time.perf_counter()
+        tot += one_step()
+        per_step.append(time.perf_counter() - ts)
+    dt = time.perf_counter() - t0
+    v = tot / dt / 1e6
+    sample = (f"first 16 instances of the batch ({cells_step} interior cells) per step"
+              if args.workload == "batch1d" else "48x48 instance of the workload per step")
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": desc, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2508_06911_gb300 import build as B, lelbm as L
+    from paper_2508_06911_gb300.solver import Solver
+
+    B.build()
+    w, desc = make_workload(args, rank)
+    stream = torch.cuda.current_stream()
+    if desc["dims"] == 1:
+        s = Solver.riemann1d(w, stream=stream.cuda_stream)
+    else:
+        s = Solver.grid2d(w, stream=stream.cuda_stream)
+    D = desc["dims"]
+    interior = desc["interior_cells"]
+    state_bytes = s.n_mom * s.n_cells * 8
+
+    # warm-up
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    L.lelbm_reset_stats(s.h)
+    L.lelbm_set_timing(s.h, True)
+
+    barrier()
+    torch.cuda.synchronize()
+    clk = clock_sampler_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clock_sampler_stop(clk, local)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = s.stats()
+    status = s.synchronize()
+    value = interior * args.steps * world / (ms / 1e3) / 1e6
+
+    # dominant kernel: the fused cell update, FP64-ALU bound
+    kern_ms = st.cell_kernel_ms / max(st.cell_kernel_launches, 1)
+    flops = (st.points_f * newton_flops(N_F[D]) + st.points_g * newton_flops(N_G[D]) +
+             st.points_ms * 2 * N_M[D]) / max(st.cell_kernel_launches, 1)
+    fp64_peak = 1.25e12  # nominal FP64 rate of GB300 (no tensor path for FP64)
+    achieved = flops / (kern_ms / 1e3)
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    alg_bytes = (2 * s.n_mom * 8 + 1) * interior  # read state + write next state + type byte
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                "kernel": "cell_update_kernel", "kernel_ms": kern_ms,
+                "hbm": {"achieved_gbs": alg_bytes / (kern_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                        "frac": alg_bytes / (kern_ms / 1e3) / 1e9 / hbm_peak,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}}
+    hist = list(st.newton_hist)
+    solves = sum(hist)
+    mean_updates = sum(i * h for i, h in enumerate(hist)) / max(solves, 1)
+
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((s.n_mom, s.n_cells), dtype=torch.float64, pin_memory=True).numpy()
+        s.get_moments()
+        L.lelbm_get_moments(s.h, host)
+        ke = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            L.lelbm_set_moments(s.h, host)
+            s.step(1)
+            L.lelbm_get_moments(s.h, host)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": interior * ke * world / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": state_bytes,
+               "d2h_bytes_per_step": state_bytes, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        desc.update({"precision": "fp64", "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB x 2 buffers)"
+                     if 2 * state_bytes > 129e6 else "state fits in L2",
+                     "parallelism": f"{world} independent replica(s)" if world > 1 else "single GPU"})
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+                "config": desc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(args.steps * (2 if s.n_cells > interior else 1)),
+                "clocks": clocks, "status": L.STATUS.get(status, status),
+                "newton_mean_updates": mean_updates, "fallback_eq": st.fallback_eq,
+                "fallback_mx": st.fallback_mx, "q_max": st.q_max, "disp_max": st.disp_max}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

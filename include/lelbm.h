@@ -1,0 +1,185 @@
+/*
+ * lelbm.h -- C ABI of the GB300 (sm_103a) implementation of the per-timestep
+ * cell update of the Lagrangian entropic lattice Boltzmann method (LELBM),
+ * W. Noh and C. Lee, arXiv:2508.06911.
+ *
+ * One time step ("lelbm_step") is, for every cell of a padded grid:
+ *   - fluid boundary fill of the pad cells ............... Sec. III.A
+ *   - macroscopic variables, non-equilibrium central moments,
+ *     regularised central-moment collision, Knudsen limiter,
+ *     normalisation (collision module, Fig. 6) ........... Eq. (IIB6)-(IIB18), App. C, App. D
+ *   - Lagrangian acoustic stencil with internal refinement
+ *     (LAS module, Fig. 7) .............................. Eq. (IIC6), (IIC9)-(IIC11)
+ *   - entropic population reconstruction, Newton on the
+ *     Lagrange multipliers with Cholesky solves (EPR module,
+ *     Fig. 8) ........................................... Eq. (IID7)-(IID13)
+ *   - moment streaming of T_N(c_i) rho f'_i and
+ *     T_N(c_i) rho K RT g'_i to x + c_i (MS module, Fig. 9) Eq. (IIE3)
+ * All quantities are in lattice units (dx = dt = dV = 1, Sec. II.A).
+ *
+ * State layout ("moments"): structure of arrays, [n_mom][n_cells] doubles, in
+ * the order of Eq. (IIB5):
+ *   1D: M0, Mx, Mxx, MDx, G0, Gx                              (n_mom = 6)
+ *   2D: M0, Mx, My, Mxx, Mxy, Myy, MDx, MDy, G0, Gx, Gy       (n_mom = 11)
+ * where MD_g = sum_i |c_i|^2 c_ig f_i.  Cells run over the PADDED grid:
+ *   2D: index = iy * NX + ix with NX = nx + 2 pad (nx if x is periodic),
+ *       NY = ny + 2 pad (ny if y is periodic);
+ *   1D: the instances of a batch are concatenated, each as
+ *       [pad | interior of lengths[b] cells | pad] (no pads when periodic).
+ * Pad cells are overwritten by the boundary fill at the start of every step;
+ * after a step they read zero.
+ *
+ * Ownership: the library allocates and owns all device memory of a handle.
+ * Host pointers passed in are read (or written) during the call only.
+ * Functions ending in _device take device pointers the caller owns; they are
+ * ordered on the handle's stream and do not synchronise.
+ *
+ * Errors: every function returns a status code.  The message of the last
+ * failure of a handle is kept until the next failing call and is returned by
+ * lelbm_last_error().  There is no CPU fallback: a handle cannot be created
+ * without a CUDA device.
+ */
+#ifndef LELBM_H
+#define LELBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LELBM_OK 0
+#define LELBM_E_INVAL 1   /* invalid argument or parameter                   */
+#define LELBM_E_NOMEM 2   /* device or host allocation failed                */
+#define LELBM_E_CUDA 3    /* a CUDA call failed (message has the CUDA error)  */
+#define LELBM_E_EPR 4     /* an EPR solve fell back to Maxwellian weights     */
+#define LELBM_E_TIMEOUT 5 /* a bounded device wait ran out                    */
+#define LELBM_E_STATE 6   /* non-physical state (rho <= 0, RT <= 0, NaN)      */
+
+/* boundary kinds per side (x-, x+, y-, y+), Sec. III.A */
+#define LELBM_BC_OUTFLOW 0  /* pads copy the nearest interior cell (zero gradient)   */
+#define LELBM_BC_INFLOW 1   /* pads hold the equilibrium of the prescribed state      */
+#define LELBM_BC_PERIODIC 2 /* wrap-around; must be set on both sides of an axis      */
+
+/* arithmetic of the step */
+#define LELBM_FP64 0 /* every operation in FP64                                     */
+
+typedef struct lelbm* lelbm_t;
+
+typedef struct {
+    int dims;            /* 1 or 2                                                     */
+    int nx, ny;          /* interior cells (ny = 1 in 1D)                              */
+    int n_batch;         /* 1D: number of independent instances (<= 1: a single one)   */
+    const int* lengths;  /* 1D batch, host [n_batch]: interior length of each instance */
+    const int* pads;     /* 1D batch, host [n_batch]: pad layers of each instance;
+                            NULL: "pad" for every instance                           */
+    int bc[4];           /* LELBM_BC_* for x-, x+, y-, y+                              */
+    double inlet[4];     /* rho, ux, uy, RT of the inflow state                        */
+    int pad;             /* pad layers on non-periodic sides (>= 1 if any)             */
+    double K;            /* internal degrees of freedom, >= 0 (gamma = (D+K+2)/(D+K))  */
+    double nu_shear;     /* kinematic shear viscosity, >= 0 (Eq. C8a)                  */
+    double nu_bulk;      /* kinematic bulk viscosity (Eq. C8b); < 0 selects omega_b = 1 */
+    double prandtl;      /* Prandtl number, > 0 (Eq. C8c)                              */
+    int limiter;         /* 1: Knudsen limiter (App. D) on                              */
+    double n_conform;    /* conformation number n of Eq. (IIC6); paper: 4              */
+    double r_min;        /* minimum acoustic radius of Eq. (IIC6); paper: 2            */
+    double refine_div;   /* divisor of N_r, Eq. (IIC9); paper: 3                       */
+    double refine_rad;   /* refinement radius factor, Eq. (IIC10); paper: 3            */
+    int max_refine;      /* cap on N_r, 0..4                                           */
+    double tol;          /* EPR residual tolerance in thermal units; paper: 1e-12      */
+    int max_newton;      /* Newton update cap per solve, 1..60                         */
+    int precision;       /* LELBM_FP64                                                 */
+    const uint8_t* solid;/* host, one byte per padded cell, 1 = solid; NULL: none       */
+    void* stream;        /* cudaStream_t to run on; NULL: a stream owned by the handle  */
+} lelbm_params;
+
+/* Per-handle counters accumulated by every step since the last reset. */
+typedef struct {
+    long long steps;              /* time steps taken                               */
+    long long cells;              /* cell updates (emitting cells x steps)          */
+    long long newton_hist[64];    /* Newton updates per solve, f and g solves alike */
+    long long fallback_eq;        /* cells re-solved with equilibrium constraints   */
+    long long fallback_mx;        /* cells given normalised Maxwellian weights      */
+    long long q_max;              /* largest velocity set                           */
+    double disp_max;              /* largest |c_i| streamed (lattice Courant, IIC3) */
+    long long first_fail_cell;    /* first cell with a Maxwellian fallback, or -1   */
+    double cell_kernel_ms;        /* CUDA-event time of the cell-update kernel      */
+    long long cell_kernel_launches;/* launches timed into cell_kernel_ms            */
+    long long points_f;           /* stencil points visited by fluon Newton passes  */
+    long long points_g;           /* stencil points visited by phonon Newton passes */
+    long long points_ms;          /* stencil points streamed (moment streaming)     */
+} lelbm_stats;
+
+/* Sizes of the structures this library was built with, so a binding can check
+ * its own layout: sizeof(lelbm_params), sizeof(lelbm_stats). */
+void lelbm_abi_sizes(long long* params_size, long long* stats_size);
+
+/* Fill p with the paper's defaults (n = 4, R_min = 2, refinement 3/3, tol 1e-12,
+ * limiter on, omega_b = 1, Pr = 1, K = 0) for a periodic 1D grid of 1 cell. */
+void lelbm_default_params(lelbm_params* p);
+
+/* Validate p, allocate the device state (two moment buffers, cell types, the
+ * instance table, counters) and return a handle in *out.  The state starts at
+ * zero; set it with lelbm_set_state or lelbm_set_moments.
+ * Errors: E_INVAL (bad parameter), E_NOMEM, E_CUDA (no device). */
+int lelbm_create(lelbm_t* out, const lelbm_params* p);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void lelbm_destroy(lelbm_t h);
+
+/* Sizes of the padded state: total cells, moments per cell, NX, NY (1D: NX =
+ * total concatenated cells, NY = 1).  Any output pointer may be NULL. */
+int lelbm_layout(lelbm_t h, long long* n_cells, int* n_mom, int* NX, int* NY);
+
+/* Interior cell range of 1D instance b: first interior cell and length. */
+int lelbm_instance(lelbm_t h, int b, long long* first, int* length);
+
+/* Equilibrium moments (Eq. IIB7) from host primitive fields over the padded
+ * grid: rho[n_cells], u[dims][n_cells] (SoA), RT[n_cells].  Pad and solid
+ * cells are ignored.  Errors: E_STATE if an interior fluid cell has
+ * rho <= 0, RT <= 0 or a non-finite value. */
+int lelbm_set_state(lelbm_t h, const double* rho, const double* u, const double* RT);
+
+/* Copy a host moment state [n_mom][n_cells] in (checkpoint restore). */
+int lelbm_set_moments(lelbm_t h, const double* m);
+
+/* Same from a device buffer owned by the caller (asynchronous on the stream). */
+int lelbm_set_moments_device(lelbm_t h, const double* m_dev);
+
+/* Enqueue n time steps on the handle's stream (n >= 0).  Returns after the
+ * launches; errors of the launches themselves are reported here, counters
+ * and EPR fallbacks at the next synchronising call. */
+int lelbm_step(lelbm_t h, int n);
+
+/* Wait for the stream.  Returns E_EPR if a cell needed the Maxwellian
+ * fallback since the last reset of the counters, E_CUDA on a device error. */
+int lelbm_synchronize(lelbm_t h);
+
+/* Copy the current moment state to a host buffer [n_mom][n_cells]; syncs. */
+int lelbm_get_moments(lelbm_t h, double* m);
+
+/* Copy the current moment state to a caller-owned device buffer (async). */
+int lelbm_get_moments_device(lelbm_t h, double* m_dev);
+
+/* Macroscopic fields (Eq. IIB6) to host buffers rho[n_cells],
+ * u[dims][n_cells], RT[n_cells]; pads and solid cells read zero; syncs. */
+int lelbm_get_macros(lelbm_t h, double* rho, double* u, double* RT);
+
+/* Counters since the last reset; syncs. */
+int lelbm_get_stats(lelbm_t h, lelbm_stats* s);
+
+/* Zero the counters. */
+int lelbm_reset_stats(lelbm_t h);
+
+/* 1: time every cell-update kernel with CUDA events on its own stream. */
+int lelbm_set_timing(lelbm_t h, int on);
+
+/* Message of the last failure of h ("" if none; h may be NULL for create). */
+const char* lelbm_last_error(lelbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LELBM_H */

@@ -1,0 +1,558 @@
+// Host side of the C ABI declared in include/lelbm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lelbm.h"
+#include "lelbm_internal.h"
+
+using namespace lbm;
+
+struct lelbm {
+    lelbm_params p;
+    int D = 1, nmom = 6;
+    int NX = 0, NY = 1;
+    long long ncell = 0;
+    Model model{};
+    Geometry geo{};
+    // host copies of the layout
+    std::vector<long long> inst_lo_h;
+    std::vector<int> inst_n_h;
+    // device memory
+    double* M[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t* d_type = nullptr;
+    int* d_inst = nullptr;
+    long long* d_inst_lo = nullptr;
+    int* d_inst_n = nullptr;
+    long long* d_pad_cell = nullptr;
+    long long* d_pad_src = nullptr;
+    long long npad = 0;
+    DevStats* d_stats = nullptr;
+    long long steps = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int blocks = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+    double timed_ms = 0.0;
+    long long timed_launches = 0;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(lelbm_t h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                             \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return fail((h), LELBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" void lelbm_abi_sizes(long long* params_size, long long* stats_size) {
+    if (params_size) *params_size = (long long)sizeof(lelbm_params);
+    if (stats_size) *stats_size = (long long)sizeof(lelbm_stats);
+}
+
+extern "C" void lelbm_default_params(lelbm_params* p) {
+    std::memset(p, 0, sizeof *p);
+    p->dims = 1;
+    p->nx = 1;
+    p->ny = 1;
+    p->bc[0] = p->bc[1] = p->bc[2] = p->bc[3] = LELBM_BC_PERIODIC;
+    p->inlet[0] = 1.0;
+    p->inlet[3] = 1.0;
+    p->K = 0.0;
+    p->nu_shear = 1e-3;
+    p->nu_bulk = -1.0;
+    p->prandtl = 1.0;
+    p->limiter = 1;
+    p->n_conform = 4.0;
+    p->r_min = 2.0;
+    p->refine_div = 3.0;
+    p->refine_rad = 3.0;
+    p->max_refine = 4;
+    p->tol = 1e-12;
+    p->max_newton = 50;
+    p->precision = LELBM_FP64;
+}
+
+static int validate(const lelbm_params* p) {
+    if (!p) return fail(nullptr, LELBM_E_INVAL, "params is NULL");
+    if (p->dims != 1 && p->dims != 2) return fail(nullptr, LELBM_E_INVAL, "dims must be 1 or 2");
+    if (p->nx < 1 || p->ny < 1) return fail(nullptr, LELBM_E_INVAL, "nx, ny must be >= 1");
+    if (p->dims == 1 && p->ny != 1) return fail(nullptr, LELBM_E_INVAL, "ny must be 1 in 1D");
+    if (p->dims == 2 && p->n_batch > 1) return fail(nullptr, LELBM_E_INVAL, "batches are 1D only");
+    for (int a = 0; a < p->dims; a++) {
+        const int l = p->bc[2 * a], r = p->bc[2 * a + 1];
+        if (l < 0 || l > 2 || r < 0 || r > 2) return fail(nullptr, LELBM_E_INVAL, "bad bc kind");
+        if ((l == LELBM_BC_PERIODIC) != (r == LELBM_BC_PERIODIC))
+            return fail(nullptr, LELBM_E_INVAL, "periodic must be set on both sides of axis %d", a);
+        if (l != LELBM_BC_PERIODIC && p->pad < 1)
+            return fail(nullptr, LELBM_E_INVAL, "non-periodic axis %d needs pad >= 1", a);
+    }
+    if (!(p->K >= 0.0) || !std::isfinite(p->K)) return fail(nullptr, LELBM_E_INVAL, "K must be >= 0");
+    if (!(p->nu_shear >= 0.0)) return fail(nullptr, LELBM_E_INVAL, "nu_shear must be >= 0");
+    if (!(p->prandtl > 0.0)) return fail(nullptr, LELBM_E_INVAL, "prandtl must be > 0");
+    if (!(p->n_conform > 0.0) || !(p->r_min >= 1.0)) return fail(nullptr, LELBM_E_INVAL, "bad stencil radius");
+    if (!(p->refine_div > 0.0) || !(p->refine_rad > 0.0)) return fail(nullptr, LELBM_E_INVAL, "bad refinement");
+    if (p->max_refine < 0 || p->max_refine > 4) return fail(nullptr, LELBM_E_INVAL, "max_refine must be 0..4");
+    if (!(p->tol > 0.0)) return fail(nullptr, LELBM_E_INVAL, "tol must be > 0");
+    if (p->max_newton < 1 || p->max_newton > 60) return fail(nullptr, LELBM_E_INVAL, "max_newton must be 1..60");
+    if (p->precision != LELBM_FP64) return fail(nullptr, LELBM_E_INVAL, "unknown precision");
+    if (p->dims == 1 && p->n_batch > 1 && p->lengths)
+        for (int b = 0; b < p->n_batch; b++)
+            if (p->lengths[b] < 1) return fail(nullptr, LELBM_E_INVAL, "lengths[%d] < 1", b);
+    if (p->dims == 1 && p->n_batch > 1 && p->pads && p->bc[0] != LELBM_BC_PERIODIC)
+        for (int b = 0; b < p->n_batch; b++)
+            if (p->pads[b] < 1) return fail(nullptr, LELBM_E_INVAL, "pads[%d] < 1", b);
+    if (p->dims == 2 && p->bc[0] == LELBM_BC_PERIODIC && p->bc[2] == LELBM_BC_PERIODIC && p->pad != 0)
+        return fail(nullptr, LELBM_E_INVAL, "pad must be 0 on a fully periodic grid");
+    const double* in = p->inlet;
+    bool any_in = false;
+    for (int s = 0; s < 2 * p->dims; s++) any_in = any_in || p->bc[s] == LELBM_BC_INFLOW;
+    if (any_in && !(in[0] > 0.0 && in[3] > 0.0)) return fail(nullptr, LELBM_E_INVAL, "inflow state needs rho, RT > 0");
+    return LELBM_OK;
+}
+
+static void free_all(lelbm* h) {
+    for (auto& e : h->ev_used) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    for (auto& e : h->ev_free) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    cudaFree(h->M[0]);
+    cudaFree(h->M[1]);
+    cudaFree(h->d_type);
+    cudaFree(h->d_inst);
+    cudaFree(h->d_inst_lo);
+    cudaFree(h->d_inst_n);
+    cudaFree(h->d_pad_cell);
+    cudaFree(h->d_pad_src);
+    cudaFree(h->d_stats);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+template <class T>
+static int upload(lelbm* h, T** dst, const std::vector<T>& src) {
+    if (src.empty()) return LELBM_OK;
+    CUDA_TRY(h, cudaMalloc((void**)dst, sizeof(T) * src.size()));
+    CUDA_TRY(h, cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return LELBM_OK;
+}
+
+static int reset_stats_dev(lelbm* h) {
+    DevStats z;
+    std::memset(&z, 0, sizeof z);
+    z.first_fail = ~0ull;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_stats, &z, sizeof z, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->steps = 0;
+    h->timed_ms = 0.0;
+    h->timed_launches = 0;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
+    g_create_err.clear();
+    if (!out) return fail(nullptr, LELBM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev < 1)
+        return fail(nullptr, LELBM_E_CUDA, "no CUDA device: %s", cudaGetErrorString(ce));
+
+    lelbm* h = new (std::nothrow) lelbm();
+    if (!h) return fail(nullptr, LELBM_E_NOMEM, "host allocation failed");
+    h->p = *p;
+    h->p.lengths = nullptr;
+    h->p.pads = nullptr;
+    h->p.solid = nullptr;
+    const int D = p->dims;
+    h->D = D;
+    h->nmom = D == 1 ? 6 : 11;
+    cudaGetDevice(&h->device);
+    if (p->stream) {
+        h->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, LELBM_E_CUDA, "cudaStreamCreate failed");
+        }
+        h->own_stream = true;
+    }
+    Model& m = h->model;
+    m.K = p->K;
+    m.nu_s = p->nu_shear;
+    m.nu_b = p->nu_bulk;
+    m.Pr = p->prandtl;
+    m.limiter = p->limiter;
+    m.n_conf = p->n_conform;
+    m.r_min = p->r_min;
+    m.refine_div = p->refine_div;
+    m.refine_rad = p->refine_rad;
+    m.max_refine = p->max_refine;
+    m.tol = p->tol;
+    m.max_iter = p->max_newton;
+
+    Geometry& g = h->geo;
+    g.D = D;
+    g.periodic[0] = p->bc[0] == LELBM_BC_PERIODIC;
+    g.periodic[1] = D == 2 ? p->bc[2] == LELBM_BC_PERIODIC : 1;
+    std::vector<uint8_t> type;
+    std::vector<long long> pad_cell, pad_src;
+    if (D == 1) {
+        const int nb = p->n_batch > 1 ? p->n_batch : 1;
+        std::vector<int> inst;
+        long long off = 0;
+        int pad = 0;
+        for (int b = 0; b < nb; b++) {
+            const int n = (p->n_batch > 1 && p->lengths) ? p->lengths[b] : p->nx;
+            pad = g.periodic[0] ? 0 : ((p->n_batch > 1 && p->pads) ? p->pads[b] : p->pad);
+            h->inst_lo_h.push_back(off + pad);
+            h->inst_n_h.push_back(n);
+            for (int i = 0; i < n + 2 * pad; i++) {
+                const long long cell = off + i;
+                inst.push_back(b);
+                if (i < pad || i >= pad + n) {
+                    const bool left = i < pad;
+                    const bool inflow = p->bc[left ? 0 : 1] == LELBM_BC_INFLOW;
+                    type.push_back(inflow ? CELL_PAD_IN : CELL_PAD_OUT);
+                    pad_cell.push_back(cell);
+                    pad_src.push_back(inflow ? -1 : (left ? off + pad : off + pad + n - 1));
+                } else {
+                    type.push_back(CELL_FLUID);
+                }
+            }
+            off += n + 2 * pad;
+        }
+        h->ncell = off;
+        h->NX = (int)std::min<long long>(off, 0x7fffffff);
+        h->NY = 1;
+        g.nx = p->nx;
+        g.ny = 1;
+        g.pad = pad;
+        g.n_inst = nb;
+        rc = upload(h, &h->d_inst, inst);
+        if (!rc) rc = upload(h, &h->d_inst_lo, h->inst_lo_h);
+        if (!rc) rc = upload(h, &h->d_inst_n, h->inst_n_h);
+        if (rc) {
+            std::string e = h->err;
+            free_all(h);
+            delete h;
+            return fail(nullptr, rc, "%s", e.c_str());
+        }
+    } else {
+        const int px = g.periodic[0] ? 0 : p->pad;
+        const int py = g.periodic[1] ? 0 : p->pad;
+        // one pad width for all non-periodic sides; periodic axes have none
+        const int NX = p->nx + 2 * px, NY = p->ny + 2 * py;
+        h->NX = NX;
+        h->NY = NY;
+        h->ncell = (long long)NX * NY;
+        g.nx = p->nx;
+        g.ny = p->ny;
+        g.n_inst = 1;
+        type.resize(h->ncell);
+        for (int iy = 0; iy < NY; iy++)
+            for (int ix = 0; ix < NX; ix++) {
+                const long long cell = (long long)iy * NX + ix;
+                const bool inx = ix >= px && ix < px + p->nx;
+                const bool iny = iy >= py && iy < py + p->ny;
+                if (inx && iny) {
+                    type[cell] = (p->solid && p->solid[cell]) ? CELL_SOLID : CELL_FLUID;
+                    continue;
+                }
+                bool inflow = false;
+                if (ix < px && p->bc[0] == LELBM_BC_INFLOW) inflow = true;
+                if (ix >= px + p->nx && p->bc[1] == LELBM_BC_INFLOW) inflow = true;
+                if (iy < py && p->bc[2] == LELBM_BC_INFLOW) inflow = true;
+                if (iy >= py + p->ny && p->bc[3] == LELBM_BC_INFLOW) inflow = true;
+                type[cell] = inflow ? CELL_PAD_IN : CELL_PAD_OUT;
+                pad_cell.push_back(cell);
+                if (inflow) {
+                    pad_src.push_back(-1);
+                } else {
+                    const int sx = std::min(std::max(ix, px), px + p->nx - 1);
+                    const int sy = std::min(std::max(iy, py), py + p->ny - 1);
+                    pad_src.push_back((long long)sy * NX + sx);
+                }
+            }
+        // interior offset of every non-periodic axis (periodic axes have no pads)
+        g.pad = (g.periodic[0] && g.periodic[1]) ? 0 : p->pad;
+    }
+    g.NX = h->NX;
+    g.NY = h->NY;
+    g.ncell = h->ncell;
+    g.inst_of_cell = h->d_inst;
+    g.inst_lo = h->d_inst_lo;
+    g.inst_n = h->d_inst_n;
+    h->npad = (long long)pad_cell.size();
+
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    cudaError_t e1 = cudaMalloc((void**)&h->M[0], bytes);
+    cudaError_t e2 = cudaMalloc((void**)&h->M[1], bytes);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        free_all(h);
+        delete h;
+        return fail(nullptr, LELBM_E_NOMEM, "cudaMalloc of %zu bytes failed", 2 * bytes);
+    }
+    rc = upload(h, &h->d_type, type);
+    if (!rc) rc = upload(h, &h->d_pad_cell, pad_cell);
+    if (!rc) rc = upload(h, &h->d_pad_src, pad_src);
+    if (!rc && cudaMalloc((void**)&h->d_stats, sizeof(DevStats)) != cudaSuccess) rc = LELBM_E_NOMEM;
+    if (!rc && (cudaMemset(h->M[0], 0, bytes) != cudaSuccess || cudaMemset(h->M[1], 0, bytes) != cudaSuccess))
+        rc = LELBM_E_CUDA;
+    if (!rc) rc = reset_stats_dev(h);
+    if (rc) {
+        std::string e = h->err;
+        free_all(h);
+        delete h;
+        return fail(nullptr, rc, "%s", e.empty() ? "device set-up failed" : e.c_str());
+    }
+    h->blocks = cell_update_blocks(D, h->device) * 4;
+    *out = h;
+    return LELBM_OK;
+}
+
+extern "C" void lelbm_destroy(lelbm_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+extern "C" int lelbm_layout(lelbm_t h, long long* n_cells, int* n_mom, int* NX, int* NY) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (n_cells) *n_cells = h->ncell;
+    if (n_mom) *n_mom = h->nmom;
+    if (NX) *NX = h->NX;
+    if (NY) *NY = h->NY;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_instance(lelbm_t h, int b, long long* first, int* length) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (h->D != 1) {
+        if (b != 0) return fail(h, LELBM_E_INVAL, "2D grids have one instance");
+        if (first) *first = 0;
+        if (length) *length = (int)h->ncell;
+        return LELBM_OK;
+    }
+    if (b < 0 || b >= (int)h->inst_lo_h.size()) return fail(h, LELBM_E_INVAL, "instance %d out of range", b);
+    if (first) *first = h->inst_lo_h[b];
+    if (length) *length = h->inst_n_h[b];
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_set_state(lelbm_t h, const double* rho, const double* u, const double* RT) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!rho || !u || !RT) return fail(h, LELBM_E_INVAL, "NULL field");
+    const long long n = h->ncell;
+    // host-side validation of the interior fluid cells
+    std::vector<uint8_t> type(n);
+    CUDA_TRY(h, cudaMemcpy(type.data(), h->d_type, n, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < n; i++) {
+        if (type[i] != CELL_FLUID) continue;
+        bool ok = rho[i] > 0.0 && RT[i] > 0.0 && std::isfinite(rho[i]) && std::isfinite(RT[i]);
+        for (int a = 0; a < h->D; a++) ok = ok && std::isfinite(u[a * n + i]);
+        if (!ok) return fail(h, LELBM_E_STATE, "non-physical state at cell %lld", i);
+    }
+    double *dr = nullptr, *du = nullptr, *dT = nullptr;
+    CUDA_TRY(h, cudaMalloc((void**)&dr, sizeof(double) * n));
+    CUDA_TRY(h, cudaMalloc((void**)&du, sizeof(double) * n * h->D));
+    CUDA_TRY(h, cudaMalloc((void**)&dT, sizeof(double) * n));
+    cudaMemcpyAsync(dr, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(du, u, sizeof(double) * n * h->D, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dT, RT, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+    launch_eq_state(h->D, h->model.K, h->d_type, dr, du, dT, h->M[h->cur], n, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaFree(dr);
+    cudaFree(du);
+    cudaFree(dT);
+    if (e != cudaSuccess) return fail(h, LELBM_E_CUDA, "set_state: %s", cudaGetErrorString(e));
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_set_moments(lelbm_t h, const double* m) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!m) return fail(h, LELBM_E_INVAL, "NULL moments");
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    CUDA_TRY(h, cudaMemcpyAsync(h->M[h->cur], m, bytes, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_set_moments_device(lelbm_t h, const double* m_dev) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!m_dev) return fail(h, LELBM_E_INVAL, "NULL moments");
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    CUDA_TRY(h, cudaMemcpyAsync(h->M[h->cur], m_dev, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return LELBM_OK;
+}
+
+static int take_events(lelbm* h, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
+    if (!h->ev_free.empty()) {
+        *ev = h->ev_free.back();
+        h->ev_free.pop_back();
+        return LELBM_OK;
+    }
+    CUDA_TRY(h, cudaEventCreate(&ev->first));
+    CUDA_TRY(h, cudaEventCreate(&ev->second));
+    return LELBM_OK;
+}
+
+static int collect_timing(lelbm* h) {
+    for (auto& e : h->ev_used) {
+        float ms = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&ms, e.first, e.second));
+        h->timed_ms += ms;
+        h->timed_launches++;
+        h->ev_free.push_back(e);
+    }
+    h->ev_used.clear();
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_step(lelbm_t h, int n) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (n < 0) return fail(h, LELBM_E_INVAL, "n must be >= 0");
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    for (int s = 0; s < n; s++) {
+        double* Min = h->M[h->cur];
+        double* Mout = h->M[1 - h->cur];
+        launch_fill_pads(h->D, h->model, h->p.inlet, Min, h->ncell, h->d_pad_cell, h->d_pad_src, h->npad,
+                         h->stream);
+        CUDA_TRY(h, cudaMemsetAsync(Mout, 0, bytes, h->stream));
+        std::pair<cudaEvent_t, cudaEvent_t> ev{};
+        if (h->timing) {
+            int rc = take_events(h, &ev);
+            if (rc) return rc;
+            CUDA_TRY(h, cudaEventRecord(ev.first, h->stream));
+        }
+        launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->blocks, h->stream);
+        if (h->timing) {
+            CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
+            h->ev_used.push_back(ev);
+        }
+        CUDA_TRY(h, cudaGetLastError());
+        h->cur = 1 - h->cur;
+        h->steps++;
+    }
+    return LELBM_OK;
+}
+
+static int read_stats(lelbm* h, lelbm_stats* s) {
+    DevStats d;
+    CUDA_TRY(h, cudaMemcpyAsync(&d, h->d_stats, sizeof d, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int rc = collect_timing(h);
+    if (rc) return rc;
+    if (s) {
+        std::memset(s, 0, sizeof *s);
+        s->steps = h->steps;
+        s->cells = (long long)d.cells;
+        for (int i = 0; i < 64; i++) s->newton_hist[i] = (long long)d.newton_hist[i];
+        s->fallback_eq = (long long)d.fallback_eq;
+        s->fallback_mx = (long long)d.fallback_mx;
+        s->q_max = (long long)d.q_max;
+        double dm;
+        std::memcpy(&dm, &d.disp_max_bits, sizeof dm);
+        s->disp_max = dm;
+        s->first_fail_cell = d.first_fail == ~0ull ? -1 : (long long)d.first_fail;
+        s->cell_kernel_ms = h->timed_ms;
+        s->cell_kernel_launches = h->timed_launches;
+        s->points_f = (long long)d.points_f;
+        s->points_g = (long long)d.points_g;
+        s->points_ms = (long long)d.points_ms;
+    }
+    return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
+}
+
+extern "C" int lelbm_synchronize(lelbm_t h) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int rc = read_stats(h, nullptr);
+    if (rc == LELBM_E_EPR) return fail(h, LELBM_E_EPR, "EPR fell back to Maxwellian weights");
+    return rc;
+}
+
+extern "C" int lelbm_get_moments(lelbm_t h, double* m) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!m) return fail(h, LELBM_E_INVAL, "NULL output");
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    CUDA_TRY(h, cudaMemcpyAsync(m, h->M[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_get_moments_device(lelbm_t h, double* m_dev) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!m_dev) return fail(h, LELBM_E_INVAL, "NULL output");
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    CUDA_TRY(h, cudaMemcpyAsync(m_dev, h->M[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_get_macros(lelbm_t h, double* rho, double* u, double* RT) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!rho || !u || !RT) return fail(h, LELBM_E_INVAL, "NULL output");
+    const long long n = h->ncell;
+    double* d = nullptr;
+    CUDA_TRY(h, cudaMalloc((void**)&d, sizeof(double) * n * (2 + h->D)));
+    launch_macros(h->D, h->model.K, h->d_type, h->M[h->cur], d, d + n, d + n * (1 + h->D), n, h->stream);
+    cudaMemcpyAsync(rho, d, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(u, d + n, sizeof(double) * n * h->D, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(RT, d + n * (1 + h->D), sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(h, LELBM_E_CUDA, "get_macros: %s", cudaGetErrorString(e));
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_get_stats(lelbm_t h, lelbm_stats* s) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!s) return fail(h, LELBM_E_INVAL, "NULL output");
+    int rc = read_stats(h, s);
+    return rc == LELBM_E_EPR ? LELBM_OK : rc;
+}
+
+extern "C" int lelbm_reset_stats(lelbm_t h) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    int rc = collect_timing(h);
+    if (rc) return rc;
+    return reset_stats_dev(h);
+}
+
+extern "C" int lelbm_set_timing(lelbm_t h, int on) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    h->timing = on != 0;
+    return LELBM_OK;
+}
+
+extern "C" const char* lelbm_last_error(lelbm_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }

@@ -1,0 +1,68 @@
+// Internal declarations shared by the two translation units of liblelbm:
+// lelbm_step.cu (device code) and lelbm_api.cu (the C ABI, host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// Cell kinds of the padded grid.
+enum : uint8_t { CELL_FLUID = 0, CELL_PAD_IN = 1, CELL_PAD_OUT = 2, CELL_SOLID = 3 };
+
+// Physical and numerical constants of one handle (Sec. II, App. C, App. D).
+struct Model {
+    double K;           // internal degrees of freedom
+    double nu_s;        // kinematic shear viscosity
+    double nu_b;        // kinematic bulk viscosity, < 0 -> omega_b = 1
+    double Pr;          // Prandtl number
+    int limiter;        // Knudsen limiter on
+    double n_conf;      // conformation number n
+    double r_min;       // minimum acoustic radius
+    double refine_div;  // divisor in N_r
+    double refine_rad;  // refinement radius factor
+    int max_refine;     // cap on N_r (<= 4)
+    double tol;         // EPR tolerance, thermal units
+    int max_iter;       // Newton update cap
+};
+
+// Padded-grid geometry.  2D: one instance, cell = iy * NX + ix.
+// 1D: n_inst instances concatenated, each [pad | n | pad] (no pads if periodic).
+struct Geometry {
+    int D;
+    int NX, NY;
+    long long ncell;
+    int nx, ny, pad;
+    int periodic[2];
+    int n_inst;
+    const int* inst_of_cell;     // 1D: instance of every cell
+    const long long* inst_lo;    // 1D: first interior cell of each instance
+    const int* inst_n;           // 1D: interior length of each instance
+};
+
+// Device-side counters (all 64-bit, updated with atomics).
+struct DevStats {
+    unsigned long long cells;
+    unsigned long long newton_hist[64];
+    unsigned long long fallback_eq;
+    unsigned long long fallback_mx;
+    unsigned long long q_max;
+    unsigned long long disp_max_bits;  // bit pattern of a non-negative double
+    unsigned long long first_fail;     // smallest failing cell, ~0ull if none
+    unsigned long long points_f;       // stencil points of fluon Newton passes
+    unsigned long long points_g;       // stencil points of phonon Newton passes
+    unsigned long long points_ms;      // stencil points streamed
+};
+
+void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, long long ncell,
+                      const long long* pad_cell, const long long* pad_src, long long npad,
+                      cudaStream_t s);
+void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min,
+                        double* Mout, DevStats* st, int grid_blocks, cudaStream_t s);
+void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u,
+                     const double* RT, double* M, long long ncell, cudaStream_t s);
+void launch_macros(int D, double K, const uint8_t* type, const double* M, double* rho, double* u,
+                   double* RT, long long ncell, cudaStream_t s);
+int cell_update_blocks(int D, int device);
+
+}  // namespace lbm

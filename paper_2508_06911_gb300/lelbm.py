@@ -1,0 +1,242 @@
+"""Thin ctypes binding of the C ABI in include/lelbm.h (argument marshalling only).
+
+Every computation runs in liblelbm.so on the GPU.  There is no fallback: when the
+library is missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblelbm.so")
+
+LELBM_OK, LELBM_E_INVAL, LELBM_E_NOMEM, LELBM_E_CUDA, LELBM_E_EPR, LELBM_E_TIMEOUT, LELBM_E_STATE = range(7)
+LELBM_BC_OUTFLOW, LELBM_BC_INFLOW, LELBM_BC_PERIODIC = 0, 1, 2
+LELBM_FP64 = 0
+STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_EPR", 5: "E_TIMEOUT", 6: "E_STATE"}
+
+
+class lelbm_params(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("n_batch", ctypes.c_int),
+        ("lengths", ctypes.POINTER(ctypes.c_int)),
+        ("pads", ctypes.POINTER(ctypes.c_int)),
+        ("bc", ctypes.c_int * 4),
+        ("inlet", ctypes.c_double * 4),
+        ("pad", ctypes.c_int),
+        ("K", ctypes.c_double),
+        ("nu_shear", ctypes.c_double),
+        ("nu_bulk", ctypes.c_double),
+        ("prandtl", ctypes.c_double),
+        ("limiter", ctypes.c_int),
+        ("n_conform", ctypes.c_double),
+        ("r_min", ctypes.c_double),
+        ("refine_div", ctypes.c_double),
+        ("refine_rad", ctypes.c_double),
+        ("max_refine", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("max_newton", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("solid", ctypes.POINTER(ctypes.c_ubyte)),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lelbm_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_longlong),
+        ("cells", ctypes.c_longlong),
+        ("newton_hist", ctypes.c_longlong * 64),
+        ("fallback_eq", ctypes.c_longlong),
+        ("fallback_mx", ctypes.c_longlong),
+        ("q_max", ctypes.c_longlong),
+        ("disp_max", ctypes.c_double),
+        ("first_fail_cell", ctypes.c_longlong),
+        ("cell_kernel_ms", ctypes.c_double),
+        ("cell_kernel_launches", ctypes.c_longlong),
+        ("points_f", ctypes.c_longlong),
+        ("points_g", ctypes.c_longlong),
+        ("points_ms", ctypes.c_longlong),
+    ]
+
+
+EXPORTS = [
+    "lelbm_abi_sizes", "lelbm_default_params", "lelbm_create", "lelbm_destroy", "lelbm_layout", "lelbm_instance",
+    "lelbm_set_state", "lelbm_set_moments", "lelbm_set_moments_device", "lelbm_step",
+    "lelbm_synchronize", "lelbm_get_moments", "lelbm_get_moments_device", "lelbm_get_macros",
+    "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
+]
+
+_lib = None
+_lock = threading.Lock()
+_DP = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+class LelbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblelbm.so (built by ``paper_2508_06911_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2508_06911_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        L.lelbm_abi_sizes.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+        L.lelbm_abi_sizes.restype = None
+        L.lelbm_default_params.argtypes = [ctypes.POINTER(lelbm_params)]
+        L.lelbm_default_params.restype = None
+        L.lelbm_create.argtypes = [ctypes.POINTER(_H), ctypes.POINTER(lelbm_params)]
+        L.lelbm_destroy.argtypes = [_H]
+        L.lelbm_destroy.restype = None
+        L.lelbm_layout.argtypes = [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.lelbm_instance.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_int)]
+        L.lelbm_set_state.argtypes = [_H, _DP, _DP, _DP]
+        L.lelbm_set_moments.argtypes = [_H, _DP]
+        L.lelbm_set_moments_device.argtypes = [_H, ctypes.c_void_p]
+        L.lelbm_step.argtypes = [_H, ctypes.c_int]
+        L.lelbm_synchronize.argtypes = [_H]
+        L.lelbm_get_moments.argtypes = [_H, _DP]
+        L.lelbm_get_moments_device.argtypes = [_H, ctypes.c_void_p]
+        L.lelbm_get_macros.argtypes = [_H, _DP, _DP, _DP]
+        L.lelbm_get_stats.argtypes = [_H, ctypes.POINTER(lelbm_stats)]
+        L.lelbm_reset_stats.argtypes = [_H]
+        L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
+        L.lelbm_last_error.argtypes = [_H]
+        L.lelbm_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, h=None) -> int:
+    if rc != LELBM_OK:
+        msg = load().lelbm_last_error(h)
+        raise LelbmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _dp(a: np.ndarray):
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("expected a C-contiguous float64 array")
+    return a.ctypes.data_as(_DP)
+
+
+def lelbm_default_params() -> lelbm_params:
+    p = lelbm_params()
+    load().lelbm_default_params(ctypes.byref(p))
+    return p
+
+
+def lelbm_abi_sizes():
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    load().lelbm_abi_sizes(ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def lelbm_create(p: lelbm_params, lengths=None, solid=None, pads=None) -> int:
+    """Create a handle; ``lengths``/``pads`` (1D batch) and ``solid`` (padded uint8 mask) are host arrays."""
+    keep = []
+    if lengths is not None:
+        arr = np.ascontiguousarray(lengths, dtype=np.int32)
+        keep.append(arr)
+        p.lengths = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        p.n_batch = len(arr)
+    if pads is not None:
+        pa = np.ascontiguousarray(pads, dtype=np.int32)
+        keep.append(pa)
+        p.pads = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    if solid is not None:
+        s = np.ascontiguousarray(solid, dtype=np.uint8)
+        keep.append(s)
+        p.solid = s.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    h = _H()
+    rc = load().lelbm_create(ctypes.byref(h), ctypes.byref(p))
+    _check(rc, None)
+    return h.value
+
+
+def lelbm_destroy(h) -> None:
+    load().lelbm_destroy(h)
+
+
+def lelbm_layout(h):
+    n, nm, NX, NY = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().lelbm_layout(h, ctypes.byref(n), ctypes.byref(nm), ctypes.byref(NX), ctypes.byref(NY)), h)
+    return n.value, nm.value, NX.value, NY.value
+
+
+def lelbm_instance(h, b: int):
+    first, length = ctypes.c_longlong(), ctypes.c_int()
+    _check(load().lelbm_instance(h, b, ctypes.byref(first), ctypes.byref(length)), h)
+    return first.value, length.value
+
+
+def lelbm_set_state(h, rho: np.ndarray, u: np.ndarray, RT: np.ndarray) -> None:
+    _check(load().lelbm_set_state(h, _dp(rho), _dp(u), _dp(RT)), h)
+
+
+def lelbm_set_moments(h, m: np.ndarray) -> None:
+    _check(load().lelbm_set_moments(h, _dp(m)), h)
+
+
+def lelbm_set_moments_device(h, ptr: int) -> None:
+    _check(load().lelbm_set_moments_device(h, ctypes.c_void_p(ptr)), h)
+
+
+def lelbm_step(h, n: int = 1) -> None:
+    _check(load().lelbm_step(h, n), h)
+
+
+def lelbm_synchronize(h) -> int:
+    """Returns the status (LELBM_E_EPR is returned, not raised)."""
+    rc = load().lelbm_synchronize(h)
+    if rc not in (LELBM_OK, LELBM_E_EPR):
+        _check(rc, h)
+    return rc
+
+
+def lelbm_get_moments(h, out: np.ndarray) -> np.ndarray:
+    _check(load().lelbm_get_moments(h, _dp(out)), h)
+    return out
+
+
+def lelbm_get_moments_device(h, ptr: int) -> None:
+    _check(load().lelbm_get_moments_device(h, ctypes.c_void_p(ptr)), h)
+
+
+def lelbm_get_macros(h, rho: np.ndarray, u: np.ndarray, RT: np.ndarray) -> None:
+    _check(load().lelbm_get_macros(h, _dp(rho), _dp(u), _dp(RT)), h)
+
+
+def lelbm_get_stats(h) -> lelbm_stats:
+    s = lelbm_stats()
+    _check(load().lelbm_get_stats(h, ctypes.byref(s)), h)
+    return s
+
+
+def lelbm_reset_stats(h) -> None:
+    _check(load().lelbm_reset_stats(h), h)
+
+
+def lelbm_set_timing(h, on: bool) -> None:
+    _check(load().lelbm_set_timing(h, int(on)), h)
+
+
+def lelbm_last_error(h) -> str:
+    m = load().lelbm_last_error(h)
+    return m.decode() if m else ""
