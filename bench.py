@@ -228,7 +228,10 @@ def run_ours(args):
 
     B.build()
     w, desc = make_workload(args, rank)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the legacy default stream has handle 0, which the ABI reads as
+    # "create a stream of your own"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     if desc["dims"] == 1:
         s = Solver.riemann1d(w, stream=stream.cuda_stream)
     else:

@@ -1,0 +1,437 @@
+// Device building blocks of the LELBM single-cell operation (arXiv:2508.06911):
+// collision module, LAS stencil enumeration, EPR Newton and equilibrium moments.
+// Included by the translation units that define kernels; everything here is
+// __device__ and header-only.
+#pragma once
+
+#include <cstdint>
+
+#include "lelbm_internal.h"
+
+namespace lbm {
+
+template <int D>
+struct Dim;
+template <>
+struct Dim<1> {
+    static constexpr int NM = 6, NF = 4, NG = 3;
+};
+template <>
+struct Dim<2> {
+    static constexpr int NM = 11, NF = 10, NG = 6;
+};
+
+// Stored-moment positions, Eq. (IIB5).
+template <int D>
+__device__ __forceinline__ constexpr int iM2(int a, int b) {
+    return D == 1 ? 2 : (a == 0 && b == 0 ? 3 : (a == 1 && b == 1 ? 5 : 4));
+}
+template <int D>
+__device__ __forceinline__ constexpr int iMD(int g) {
+    return D == 1 ? 3 : 6 + g;
+}
+template <int D>
+__device__ __forceinline__ constexpr int iG0() {
+    return D == 1 ? 4 : 8;
+}
+template <int D>
+__device__ __forceinline__ constexpr int iG1(int g) {
+    return D == 1 ? 5 : 9 + g;
+}
+
+// ---------------------------------------------------------------------------
+// Collision module: Eq. (IIB6), (IIB9)-(IIB18), App. C (C7)-(C8), App. D.
+// ---------------------------------------------------------------------------
+template <int D>
+struct CellState {
+    double rho, u[D], RT, sig, inv_sig;
+    double cf[Dim<D>::NF];  // fluon constraints in thermal units
+    double cg[Dim<D>::NG];  // phonon constraints in thermal units
+    bool ok;
+};
+
+template <int D>
+__device__ __forceinline__ void collide(const double* M, const Model& m, CellState<D>& c) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    const double K = m.K;
+    // Eq. (IIB6), with the operation order of a plain loop and one rounding each.
+    const double rho = M[0];
+    double usq = 0.0, tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        c.u[a] = __ddiv_rn(M[1 + a], rho);
+        usq = __dadd_rn(usq, __dmul_rn(c.u[a], c.u[a]));
+        tr = __dadd_rn(tr, M[iM2<D>(a, a)]);
+    }
+    const double RT = __ddiv_rn(__dsub_rn(__ddiv_rn(__dadd_rn(tr, M[iG0<D>()]), rho), usq),
+                                __dadd_rn((double)D, K));
+    c.rho = rho;
+    c.RT = RT;
+    c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
+    if (!c.ok) return;
+    c.sig = sqrt(RT);
+    c.inv_sig = 1.0 / c.sig;
+
+    // Eq. (IIB9): non-equilibrium central moments.
+    double P[D][D];
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = 0; b < D; b++)
+            P[a][b] = M[iM2<D>(a, b)] - rho * (c.u[a] * c.u[b] + (a == b ? RT : 0.0));
+    double trP = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) trP += P[a][a];
+    double Q[D];
+#pragma unroll
+    for (int g = 0; g < D; g++) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) s += c.u[a] * P[a][g];
+        Q[g] = M[iMD<D>(g)] - 2.0 * s - c.u[g] * trP - rho * (usq + (D + 2) * RT) * c.u[g];
+    }
+    const double G0 = M[iG0<D>()];
+    const double G0n = G0 - rho * K * RT;
+    double Gn[D];
+#pragma unroll
+    for (int g = 0; g < D; g++) Gn[g] = M[iG1<D>(g)] - c.u[g] * G0;
+
+    // App. C: implicit collision frequencies from the kinematic coefficients.
+    const double inv_f = m.nu_s / RT + 0.5;
+    double wf = 1.0 / inv_f;
+    const double fb = 2.0 / D - 2.0 / (D + K);
+    double wb = (m.nu_b < 0.0 || fb <= 0.0) ? 1.0 : 1.0 / (m.nu_b / (RT * fb) + 0.5);
+    double wh = 1.0 / ((inv_f - 0.5) / m.Pr + 0.5);
+
+    // App. D: Knudsen number (moments normalised by rho) and limiter.
+    if (m.limiter) {
+        double s2 = 0.0, s3 = 0.0;
+        const double ir = 1.0 / rho;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = 0; b < D; b++) s2 += fabs(P[a][b] * ir);
+        s2 += fabs(G0n * ir);
+#pragma unroll
+        for (int g = 0; g < D; g++) s3 += fabs(Q[g] * ir) + fabs(Gn[g] * ir);
+        const double k2 = s2 / ((D + K) * RT);
+        const double k3 = s3 / ((D + K + 2) * RT * c.sig);
+        const double Kn = fmax(k2, k3);
+        if (Kn > 0.0) {
+            const double ks = log10(Kn);
+            if (ks >= -1.0) {
+                wf = wb = wh = 1.0;
+            } else if (ks > -2.0) {
+                const double x = ks + 2.0;
+                wf += (1.0 - wf) * x;
+                wb += (1.0 - wb) * x;
+                wh += (1.0 - wh) * x;
+            }
+        }
+    }
+
+    // Eq. (IIB10)-(IIB18), then divided by sqrt(RT)^order (thermal units).
+    const double bulk = -G0n / D;
+    const double ir = 1.0 / rho;
+    const double iRT = 1.0 / RT;
+    c.cf[0] = 1.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) c.cf[1 + a] = 0.0;
+    int j = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) {
+            const double sh = P[a][b] - (a == b ? bulk : 0.0);
+            const double mm = (a == b ? rho * RT : 0.0) + (1.0 - wf) * sh + (1.0 - wb) * (a == b ? bulk : 0.0);
+            c.cf[j++] = mm * ir * iRT;
+        }
+    const double s3 = iRT * c.inv_sig;
+#pragma unroll
+    for (int g = 0; g < D; g++)
+#pragma unroll
+        for (int a = 0; a < D; a++) c.cf[j++] = (1.0 - wh) * ((1.0 + 2.0 * (a == g)) / (D + 2) * Q[g]) * ir * s3;
+    (void)NF;
+    if (K > 0.0) {
+        const double nrm = 1.0 / (rho * K * RT);
+        c.cg[0] = (rho * K * RT + (1.0 - wb) * G0n) * nrm;
+#pragma unroll
+        for (int g = 0; g < D; g++) c.cg[1 + g] = (1.0 - wh) * Gn[g] * nrm * c.inv_sig;
+        int k = 1 + D;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++) c.cg[k++] = (a == b) ? 1.0 : 0.0;  // Eq. (IIB17) / RT
+    } else {
+#pragma unroll
+        for (int k = 0; k < NG; k++) c.cg[k] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LAS module: Eq. (IIC6), (IIC9)-(IIC11).  Level-0 points are the integer
+// velocities within R_ac + 1/2 of u; for Lvl = 1..N_r a point of level Lvl-1
+// within refine_rad * 0.5^Lvl of u is split into 2^D children at +-h/4.
+// ---------------------------------------------------------------------------
+template <int D>
+struct Stencil {
+    double u[D];
+    double rr2;      // (R_ac + 1/2)^2
+    int R;           // acoustic radius
+    int Nr;          // refinement levels
+    double rad2[5];  // squared refinement radius of level 1..4 (index = level)
+
+    __device__ __forceinline__ void init(const CellState<D>& c, const Model& m) {
+#pragma unroll
+        for (int a = 0; a < D; a++) u[a] = c.u[a];
+        double r = round(__dmul_rn(m.n_conf, c.sig));
+        if (r < m.r_min) r = m.r_min;
+        R = (int)r;
+        const double rr = (double)R + 0.5;
+        rr2 = rr * rr;
+        double nr = round(__ddiv_rn(1.0, __dmul_rn(m.refine_div, c.sig)));
+        if (nr > (double)m.max_refine) nr = (double)m.max_refine;
+        Nr = (int)nr;
+#pragma unroll
+        for (int L = 0; L < 5; L++) {
+            const double rad = m.refine_rad * ldexp(1.0, -L);
+            rad2[L] = rad * rad;
+        }
+    }
+
+    __device__ __forceinline__ double dist2(const double* c) const {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            const double d = __dsub_rn(c[a], u[a]);
+            s = __dadd_rn(s, __dmul_rn(d, d));
+        }
+        return s;
+    }
+
+    // Visit one level-0 point and its refinement subtree.
+    template <class F>
+    __device__ __forceinline__ void visit0(const double* c0, F& f) const {
+        if (Nr == 0 || dist2(c0) > rad2[1]) {
+            f(c0, 1.0);
+            return;
+        }
+        const int nfine = 1 << (D * Nr);
+        for (int idx = 0; idx < nfine; idx++) {
+            double ctr[D];
+#pragma unroll
+            for (int a = 0; a < D; a++) ctr[a] = c0[a];
+            double h = 1.0;
+            int L = 0;
+            while (L < Nr && dist2(ctr) <= rad2[L + 1]) {
+#pragma unroll
+                for (int a = 0; a < D; a++) {
+                    const int bit = (idx >> (a * Nr + (Nr - 1 - L))) & 1;
+                    ctr[a] += bit ? 0.25 * h : -0.25 * h;
+                }
+                h *= 0.5;
+                L++;
+            }
+            const int mask = (1 << (Nr - L)) - 1;
+            bool first = true;
+#pragma unroll
+            for (int a = 0; a < D; a++) first = first && (((idx >> (a * Nr)) & mask) == 0);
+            if (first) f(ctr, ldexp(1.0, -D * L));
+        }
+    }
+
+    template <class F>
+    __device__ __forceinline__ void for_each(F& f) const {
+        const double rr = sqrt(rr2);
+        if constexpr (D == 1) {
+            int x0 = (int)floor(u[0] - rr) - 1, x1 = (int)ceil(u[0] + rr) + 1;
+            for (int cx = x0; cx <= x1; cx++) {
+                const double c[1] = {(double)cx};
+                if (dist2(c) <= rr2) visit0(c, f);
+            }
+        } else {
+            const int y0 = (int)floor(u[D - 1] - rr) - 1, y1 = (int)ceil(u[D - 1] + rr) + 1;
+            for (int cy = y0; cy <= y1; cy++) {
+                const double dy = __dsub_rn((double)cy, u[D - 1]);
+                const double dy2 = __dmul_rn(dy, dy);
+                if (dy2 > rr2) continue;
+                const double s = sqrt(fmax(rr2 - dy2, 0.0));
+                int x0 = (int)floor(u[0] - s) - 1, x1 = (int)ceil(u[0] + s) + 1;
+                double c[D];
+                c[D - 1] = (double)cy;
+                c[0] = (double)x0;
+                while (x0 <= x1 && dist2(c) > rr2) c[0] = (double)(++x0);
+                c[0] = (double)x1;
+                while (x1 >= x0 && dist2(c) > rr2) c[0] = (double)(--x1);
+                for (int cx = x0; cx <= x1; cx++) {
+                    c[0] = (double)cx;
+                    visit0(c, f);
+                }
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// EPR module: Eq. (IID7)-(IID13) in thermal units.
+// ---------------------------------------------------------------------------
+template <int D, bool FLUON>
+struct Basis {
+    static constexpr int N = FLUON ? Dim<D>::NF : Dim<D>::NG;
+    // fluons: 1, t_a, t_a t_b (a <= b), t_a^2 t_g (g-major); phonons: first 1 + D + D(D+1)/2
+    __device__ __forceinline__ static void eval(const double* t, double* T) {
+        T[0] = 1.0;
+        if constexpr (D == 1) {
+            T[1] = t[0];
+            T[2] = t[0] * t[0];
+            if constexpr (FLUON) T[3] = T[2] * t[0];
+        } else {
+            const double xx = t[0] * t[0], yy = t[D - 1] * t[D - 1];
+            T[1] = t[0];
+            T[2] = t[D - 1];
+            T[3] = xx;
+            T[4] = t[0] * t[D - 1];
+            T[5] = yy;
+            if constexpr (FLUON) {
+                T[6] = xx * t[0];
+                T[7] = yy * t[0];
+                T[8] = xx * t[D - 1];
+                T[9] = yy * t[D - 1];
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Cholesky factorisation of the packed lower triangle and solve A x = b.
+template <int N>
+__device__ __forceinline__ bool chol_solve(double* A, double* b) {
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        double s = A[tri(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; k++) s -= A[tri(j, k)] * A[tri(j, k)];
+        if (!(s > 0.0)) return false;
+        const double d = sqrt(s);
+        const double id = 1.0 / d;
+        A[tri(j, j)] = d;
+#pragma unroll
+        for (int i = j + 1; i < N; i++) {
+            double t = A[tri(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; k++) t -= A[tri(i, k)] * A[tri(j, k)];
+            A[tri(i, j)] = t * id;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        double t = b[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) t -= A[tri(i, k)] * b[k];
+        b[i] = t / A[tri(i, i)];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
+        double t = b[i];
+#pragma unroll
+        for (int k = i + 1; k < N; k++) t -= A[tri(k, i)] * b[k];
+        b[i] = t / A[tri(i, i)];
+    }
+    return true;
+}
+
+// Eq. (IID13) in thermal units: lambda_0 = -1 + D/2 ln(2 pi RT), lambda_aa = 1/2.
+template <int D, int N>
+__device__ __forceinline__ void maxwell_start(double RT, double* lam) {
+#pragma unroll
+    for (int j = 0; j < N; j++) lam[j] = 0.0;
+    lam[0] = -1.0 + 0.5 * D * log(2.0 * 3.14159265358979323846 * RT);
+    int j = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) lam[j++] = (a == b) ? 0.5 : 0.0;
+}
+
+// Newton-Raphson on the multipliers (Eq. IID8-IID11): returns the number of
+// updates (converged, one polishing update included), -1 on a breakdown
+// (non-finite residual, non-positive pivot), -2 at the iteration cap.
+template <int D, bool FLUON>
+__device__ int epr_newton(const CellState<D>& c, const Stencil<D>& st, const double* con, double* lam,
+                          const Model& m, unsigned long long& npts) {
+    using B = Basis<D, FLUON>;
+    constexpr int N = B::N;
+    constexpr int NA = N * (N + 1) / 2;
+    int updates = 0;
+    bool polished = false;
+    for (int it = 0;; it++) {
+        double A[NA];
+#pragma unroll
+        for (int i = 0; i < NA; i++) A[i] = 0.0;
+        const bool needA = !polished;
+        auto acc = [&](const double* cp, double dC) {
+            npts++;
+            double t[D];
+#pragma unroll
+            for (int a = 0; a < D; a++) t[a] = (cp[a] - c.u[a]) * c.inv_sig;
+            double T[N];
+            B::eval(t, T);
+            double e = 1.0;
+#pragma unroll
+            for (int j = 0; j < N; j++) e += lam[j] * T[j];
+            const double f = dC * exp(-e);
+            if (needA) {
+#pragma unroll
+                for (int i = 0; i < N; i++) {
+                    const double tf = T[i] * f;
+#pragma unroll
+                    for (int j = 0; j <= i; j++) A[tri(i, j)] += tf * T[j];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < N; i++) A[tri(i, 0)] += T[i] * f;
+            }
+        };
+        st.for_each(acc);
+        double r[N];
+        double rmax = 0.0;
+        bool finite = true;
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            r[j] = A[tri(j, 0)] - con[j];
+            finite = finite && isfinite(r[j]);
+            rmax = fmax(rmax, fabs(r[j]));
+        }
+        if (!finite) return -1;
+        if (polished) return updates;
+        const bool conv = rmax <= m.tol;
+        if (!conv && it >= m.max_iter) return -2;
+        if (!chol_solve<N>(A, r)) return -1;
+#pragma unroll
+        for (int j = 0; j < N; j++) lam[j] += r[j];
+        updates++;
+        if (conv) polished = true;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void eq_moments(double K, double rho, const double* u, double RT, double* M) {
+    double usq = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) usq += u[a] * u[a];
+    M[0] = rho;
+#pragma unroll
+    for (int a = 0; a < D; a++) M[1 + a] = rho * u[a];
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) M[iM2<D>(a, b)] = rho * (u[a] * u[b] + (a == b ? RT : 0.0));
+#pragma unroll
+    for (int g = 0; g < D; g++) M[iMD<D>(g)] = rho * (usq + (D + 2) * RT) * u[g];
+    M[iG0<D>()] = rho * K * RT;
+#pragma unroll
+    for (int g = 0; g < D; g++) M[iG1<D>(g)] = rho * K * RT * u[g];
+}
+
+}  // namespace lbm
