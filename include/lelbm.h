@@ -178,6 +178,34 @@ int lelbm_set_timing(lelbm_t h, int on);
 /* Message of the last failure of h ("" if none; h may be NULL for create). */
 const char* lelbm_last_error(lelbm_t h);
 
+/* ---- Allocation-free single step (the paper has no counterpart) ----------
+ * For callers that must not allocate device memory: an application that owns all
+ * device memory through its own pool or a fixed budget, or code on a latency-
+ * critical path where cudaFree synchronises the device and cudaMalloc can fail or
+ * fragment.  The caller passes the state buffers it already owns; the step itself
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * p:      the parameters of lelbm_create, with solid == NULL, precision FP64 and
+ *         at most LELBM_NOALLOC_MAX_INSTANCES 1D instances; p->stream is the
+ *         stream to run on (NULL: the legacy default stream).
+ * m_in:   device [n_mom][n_cells] moments at time t in the padded layout above;
+ *         pad cells are not read (they are derived from the interior or the
+ *         inflow state); not modified.
+ * m_out:  device [n_mom][n_cells], overwritten with the moments at t + 1 (pad
+ *         cells zero).  Must not overlap m_in.
+ * stats:  NULL: return after enqueueing the work (asynchronous).  Otherwise the
+ *         call waits for the stream and fills *stats for this step.
+ * Returns E_INVAL (bad parameter or more instances than the maximum), E_CUDA, or
+ * E_EPR (only with stats != NULL) when a cell fell back to Maxwellian weights.
+ *
+ * Scratch: a file-scope device array of 512 KiB (counters and the instance table),
+ * held by every GPU on which the library is loaded until the process exits.  The
+ * first call on a device looks up the array's device address; make that first
+ * call before any stream capture.  All calls share the array and each call resets
+ * what it reads, so calls whose work overlaps on the GPU race with each other. */
+#define LELBM_NOALLOC_MAX_INSTANCES 16384
+int lelbm_step_noalloc(const lelbm_params* p, const double* m_in, double* m_out, lelbm_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

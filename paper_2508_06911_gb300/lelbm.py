@@ -72,7 +72,9 @@ EXPORTS = [
     "lelbm_set_state", "lelbm_set_moments", "lelbm_set_moments_device", "lelbm_step",
     "lelbm_synchronize", "lelbm_get_moments", "lelbm_get_moments_device", "lelbm_get_macros",
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
+    "lelbm_step_noalloc",
 ]
+LELBM_NOALLOC_MAX_INSTANCES = 16384
 
 _lib = None
 _lock = threading.Lock()
@@ -119,6 +121,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
         L.lelbm_last_error.argtypes = [_H]
         L.lelbm_last_error.restype = ctypes.c_char_p
+        L.lelbm_step_noalloc.argtypes = [ctypes.POINTER(lelbm_params), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(lelbm_stats)]
         _lib = L
     return _lib
 
@@ -240,3 +244,23 @@ def lelbm_set_timing(h, on: bool) -> None:
 def lelbm_last_error(h) -> str:
     m = load().lelbm_last_error(h)
     return m.decode() if m else ""
+
+
+def lelbm_step_noalloc(p: lelbm_params, m_in_ptr: int, m_out_ptr: int, stats: lelbm_stats | None = None,
+                       lengths=None, pads=None) -> int:
+    """One allocation-free step on caller-owned device buffers (returns the status code).
+
+    ``lengths``/``pads`` (1D batch) are host arrays kept alive for the call.
+    """
+    keep = []
+    if lengths is not None:
+        arr = np.ascontiguousarray(lengths, dtype=np.int32)
+        keep.append(arr)
+        p.lengths = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        p.n_batch = len(arr)
+    if pads is not None:
+        pa = np.ascontiguousarray(pads, dtype=np.int32)
+        keep.append(pa)
+        p.pads = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    sp = ctypes.byref(stats) if stats is not None else ctypes.POINTER(lelbm_stats)()
+    return load().lelbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(m_in_ptr), ctypes.c_void_p(m_out_ptr), sp)
