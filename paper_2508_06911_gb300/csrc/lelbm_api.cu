@@ -36,6 +36,7 @@ struct lelbm {
     long long* d_pad_src = nullptr;
     long long npad = 0;
     DevStats* d_stats = nullptr;
+    unsigned long long* d_work = nullptr;  // work counter of the cell-update kernel
     long long steps = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -153,6 +154,7 @@ static void free_all(lelbm* h) {
     cudaFree(h->d_pad_cell);
     cudaFree(h->d_pad_src);
     cudaFree(h->d_stats);
+    cudaFree(h->d_work);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -326,6 +328,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     if (!rc) rc = upload(h, &h->d_pad_cell, pad_cell);
     if (!rc) rc = upload(h, &h->d_pad_src, pad_src);
     if (!rc && cudaMalloc((void**)&h->d_stats, sizeof(DevStats)) != cudaSuccess) rc = LELBM_E_NOMEM;
+    if (!rc && cudaMalloc((void**)&h->d_work, sizeof(unsigned long long)) != cudaSuccess) rc = LELBM_E_NOMEM;
     if (!rc && (cudaMemset(h->M[0], 0, bytes) != cudaSuccess || cudaMemset(h->M[1], 0, bytes) != cudaSuccess))
         rc = LELBM_E_CUDA;
     if (!rc) rc = reset_stats_dev(h);
@@ -335,7 +338,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         delete h;
         return fail(nullptr, rc, "%s", e.empty() ? "device set-up failed" : e.c_str());
     }
-    h->blocks = cell_update_blocks(D, h->device) * 4;
+    h->blocks = cell_update_blocks(D, h->device);
     *out = h;
     return LELBM_OK;
 }
@@ -449,13 +452,14 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
         launch_fill_pads(h->D, h->model, h->p.inlet, Min, h->ncell, h->d_pad_cell, h->d_pad_src, h->npad,
                          h->stream);
         CUDA_TRY(h, cudaMemsetAsync(Mout, 0, bytes, h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
         std::pair<cudaEvent_t, cudaEvent_t> ev{};
         if (h->timing) {
             int rc = take_events(h, &ev);
             if (rc) return rc;
             CUDA_TRY(h, cudaEventRecord(ev.first, h->stream));
         }
-        launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->blocks, h->stream);
+        launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks, h->stream);
         if (h->timing) {
             CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
             h->ev_used.push_back(ev);

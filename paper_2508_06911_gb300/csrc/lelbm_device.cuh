@@ -240,6 +240,57 @@ struct Stencil {
         }
     }
 
+    // Row form of the same velocity set: row(cy, xa, xb) receives the level-0
+    // integer points cx = xa..xb of row cy (cy = 0 in 1D, dC = 1); leaf(c, dC)
+    // receives every refined point.  Membership is tested only at segment ends:
+    // the exact test is monotone along a row, so every segment is an interval.
+    template <class RowF, class LeafF>
+    __device__ __forceinline__ void for_each_row(RowF& row, LeafF& leaf) const {
+        const double rr = sqrt(rr2);
+        int y0 = 0, y1 = 0;
+        if constexpr (D == 2) {
+            y0 = (int)floor(u[1] - rr) - 1;
+            y1 = (int)ceil(u[1] + rr) + 1;
+        }
+        const double r1 = sqrt(rad2[1]);
+        for (int cy = y0; cy <= y1; cy++) {
+            double c[D];
+            double s = rr;
+            if constexpr (D == 2) {
+                c[1] = (double)cy;
+                const double dy = __dsub_rn((double)cy, u[1]);
+                const double dy2 = __dmul_rn(dy, dy);
+                if (dy2 > rr2) continue;
+                s = sqrt(fmax(rr2 - dy2, 0.0));
+            }
+            int x0 = (int)floor(u[0] - s) - 1, x1 = (int)ceil(u[0] + s) + 1;
+            c[0] = (double)x0;
+            while (x0 <= x1 && dist2(c) > rr2) c[0] = (double)(++x0);
+            c[0] = (double)x1;
+            while (x1 >= x0 && dist2(c) > rr2) c[0] = (double)(--x1);
+            if (x0 > x1) continue;
+            if (Nr > 0) {
+                int a = (int)floor(u[0] - r1) - 1, b = (int)ceil(u[0] + r1) + 1;
+                a = a < x0 ? x0 : a;
+                b = b > x1 ? x1 : b;
+                c[0] = (double)a;
+                while (a <= b && dist2(c) > rad2[1]) c[0] = (double)(++a);
+                c[0] = (double)b;
+                while (b >= a && dist2(c) > rad2[1]) c[0] = (double)(--b);
+                if (a <= b) {
+                    if (x0 <= a - 1) row(cy, x0, a - 1);
+                    for (int cx = a; cx <= b; cx++) {
+                        c[0] = (double)cx;
+                        visit0(c, leaf);
+                    }
+                    if (b + 1 <= x1) row(cy, b + 1, x1);
+                    continue;
+                }
+            }
+            row(cy, x0, x1);
+        }
+    }
+
     template <class F>
     __device__ __forceinline__ void for_each(F& f) const {
         const double rr = sqrt(rr2);
@@ -412,6 +463,230 @@ __device__ int epr_newton(const CellState<D>& c, const Stencil<D>& st, const dou
         for (int j = 0; j < N; j++) lam[j] += r[j];
         updates++;
         if (conv) polished = true;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// EPR Newton in moment form.  The fluon basis is every monomial x^a y^b of total
+// degree <= 3 and the phonon basis every monomial of degree <= 2 (Eq. IIB14-17 in
+// thermal units), so A_ij = sum_k T_i T_j f_k is the population moment of
+// x^(a_i + a_j) y^(b_i + b_j): degree <= 6 (fluons) or <= 4 (phonons).  Along a
+// stencil row (fixed y) those moments are y^b times the row sums S_a = sum x^a f,
+// so a point costs the powers of x and one FMA per row sum instead of the
+// N(N+1)/2 products of Eq. (IID11a).  The residual (IID11c) is the first column.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ constexpr int tix(int a, int b, int P) { return b * (P + 1) - b * (b - 1) / 2 + a; }
+
+template <int D>
+struct MomentSet {
+    static constexpr int PF = 6, PG = 4;
+    static constexpr int NF = D == 1 ? PF + 1 : (PF + 1) * (PF + 2) / 2;
+    static constexpr int NG = D == 1 ? PG + 1 : (PG + 1) * (PG + 2) / 2;
+};
+
+// exponents (a_j, b_j) of the basis entries, in the order of Basis<D, FLUON>::eval
+template <int D, bool FLUON>
+__device__ __forceinline__ constexpr int bx(int j) {
+    if constexpr (D == 1) {
+        return j;
+    } else {
+        constexpr int a[10] = {0, 1, 0, 2, 1, 0, 3, 1, 2, 0};
+        return a[j];
+    }
+}
+template <int D, bool FLUON>
+__device__ __forceinline__ constexpr int by(int j) {
+    if constexpr (D == 1) {
+        return 0;
+    } else {
+        constexpr int b[10] = {0, 0, 1, 0, 1, 2, 0, 2, 1, 3};
+        return b[j];
+    }
+}
+
+// Coefficients of the exponent 1 + sum_j lam_j T_j as a polynomial in x on the row y.
+template <int D>
+__device__ __forceinline__ void row_coeffs(const double* lf, const double* lg, double y, double* cf, double* cg) {
+    if constexpr (D == 1) {
+        cf[0] = 1.0 + lf[0];
+        cf[1] = lf[1];
+        cf[2] = lf[2];
+        cf[3] = lf[3];
+        cg[0] = 1.0 + lg[0];
+        cg[1] = lg[1];
+        cg[2] = lg[2];
+    } else {
+        cf[0] = 1.0 + lf[0] + y * (lf[2] + y * (lf[5] + y * lf[9]));
+        cf[1] = lf[1] + y * (lf[4] + y * lf[7]);
+        cf[2] = lf[3] + y * lf[8];
+        cf[3] = lf[6];
+        cg[0] = 1.0 + lg[0] + y * (lg[2] + y * lg[5]);
+        cg[1] = lg[1] + y * lg[4];
+        cg[2] = lg[3];
+    }
+}
+
+// One pass over the velocity set accumulating the population moments of f
+// (if doF) and g (if doG) for the multipliers lf, lg.  Returns the point count.
+template <int D>
+__device__ __forceinline__ unsigned long long moment_pass(const CellState<D>& c, const Stencil<D>& st,
+                                                          const double* lf, const double* lg, bool doF, bool doG,
+                                                          double* MF, double* MG) {
+    using MS = MomentSet<D>;
+#pragma unroll
+    for (int i = 0; i < MS::NF; i++) MF[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < MS::NG; i++) MG[i] = 0.0;
+    unsigned long long q = 0;
+    auto row = [&](int cy, int xa, int xb) {
+        double y = 0.0;
+        if constexpr (D == 2) y = ((double)cy - c.u[1]) * c.inv_sig;
+        double cf[4], cg[3];
+        row_coeffs<D>(lf, lg, y, cf, cg);
+        double SF[MS::PF + 1], SG[MS::PG + 1];
+#pragma unroll
+        for (int a = 0; a <= MS::PF; a++) SF[a] = 0.0;
+#pragma unroll
+        for (int a = 0; a <= MS::PG; a++) SG[a] = 0.0;
+        for (int cx = xa; cx <= xb; cx++) {
+            const double x = ((double)cx - c.u[0]) * c.inv_sig;
+            double p[MS::PF + 1];
+            p[0] = 1.0;
+#pragma unroll
+            for (int k = 1; k <= MS::PF; k++) p[k] = p[k - 1] * x;
+            if (doF) {
+                const double f = exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+#pragma unroll
+                for (int a = 0; a <= MS::PF; a++) SF[a] += p[a] * f;
+            }
+            if (doG) {
+                const double g = exp(-((cg[2] * x + cg[1]) * x + cg[0]));
+#pragma unroll
+                for (int a = 0; a <= MS::PG; a++) SG[a] += p[a] * g;
+            }
+        }
+        q += (unsigned long long)(xb - xa + 1);
+        if constexpr (D == 1) {
+#pragma unroll
+            for (int a = 0; a <= MS::PF; a++) MF[a] += SF[a];
+#pragma unroll
+            for (int a = 0; a <= MS::PG; a++) MG[a] += SG[a];
+        } else {
+            double yp[MS::PF + 1];
+            yp[0] = 1.0;
+#pragma unroll
+            for (int k = 1; k <= MS::PF; k++) yp[k] = yp[k - 1] * y;
+#pragma unroll
+            for (int b = 0; b <= MS::PF; b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += SF[a] * yp[b];
+#pragma unroll
+            for (int b = 0; b <= MS::PG; b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] += SG[a] * yp[b];
+        }
+    };
+    auto leaf = [&](const double* cp, double dC) {
+        const double x = (cp[0] - c.u[0]) * c.inv_sig;
+        double y = 0.0;
+        if constexpr (D == 2) y = (cp[1] - c.u[1]) * c.inv_sig;
+        double cf[4], cg[3];
+        row_coeffs<D>(lf, lg, y, cf, cg);
+        double px[MS::PF + 1], py[MS::PF + 1];
+        px[0] = py[0] = 1.0;
+#pragma unroll
+        for (int k = 1; k <= MS::PF; k++) {
+            px[k] = px[k - 1] * x;
+            py[k] = py[k - 1] * y;
+        }
+        if (doF) {
+            const double f = dC * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? MS::PF : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += px[a] * py[b] * f;
+        }
+        if (doG) {
+            const double g = dC * exp(-((cg[2] * x + cg[1]) * x + cg[0]));
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? MS::PG : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] += px[a] * py[b] * g;
+        }
+        q++;
+    };
+    st.for_each_row(row, leaf);
+    return q;
+}
+
+// Newton update from the moments of the current pass (Eq. IID8-IID11).
+// Returns 0 (updated), 1 (converged: the polishing update was applied),
+// -1 (non-finite residual or non-positive pivot), -2 (iteration cap).
+template <int D, bool FLUON>
+__device__ __forceinline__ int newton_step(const double* Mom, const double* con, double* lam, const Model& m, int it) {
+    constexpr int N = Basis<D, FLUON>::N;
+    constexpr int P = FLUON ? MomentSet<D>::PF : MomentSet<D>::PG;
+    double r[N];
+    double rmax = 0.0;
+    bool finite = true;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        r[j] = Mom[tix(bx<D, FLUON>(j), by<D, FLUON>(j), P)] - con[j];
+        finite = finite && isfinite(r[j]);
+        rmax = fmax(rmax, fabs(r[j]));
+    }
+    if (!finite) return -1;
+    const bool conv = rmax <= m.tol;
+    if (!conv && it >= m.max_iter) return -2;
+    double A[N * (N + 1) / 2];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++)
+            A[tri(i, j)] = Mom[tix(bx<D, FLUON>(i) + bx<D, FLUON>(j), by<D, FLUON>(i) + by<D, FLUON>(j), P)];
+    if (!chol_solve<N>(A, r)) return -1;
+#pragma unroll
+    for (int j = 0; j < N; j++) lam[j] += r[j];
+    return conv ? 1 : 0;
+}
+
+// Joint Newton iterations of the fluon and phonon multipliers: every pass
+// accumulates the moments of each population that is still iterating.
+// sf, sg: number of updates (>= 0) or failure (< 0).
+template <int D>
+__device__ __forceinline__ void solve_fg(const CellState<D>& c, const Stencil<D>& st, const double* conF,
+                                         const double* conG, bool has_g, double* lf, double* lg, const Model& m,
+                                         int& sf, int& sg, unsigned long long& npf, unsigned long long& npg) {
+    using MS = MomentSet<D>;
+    bool fa = true, ga = has_g;
+    sf = 0;
+    sg = 0;
+    for (int it = 0; fa || ga; it++) {
+        double MF[MS::NF], MG[MS::NG];
+        const unsigned long long q = moment_pass<D>(c, st, lf, lg, fa, ga, MF, MG);
+        // phonons first: their moments are dead before the larger fluon system is built
+        if (ga) {
+            npg += q;
+            const int r = newton_step<D, false>(MG, conG, lg, m, it);
+            if (r < 0) {
+                sg = r;
+                ga = false;
+            } else {
+                sg++;
+                if (r == 1) ga = false;
+            }
+        }
+        if (fa) {
+            npf += q;
+            const int r = newton_step<D, true>(MF, conF, lf, m, it);
+            if (r < 0) {
+                sf = r;
+                fa = false;
+            } else {
+                sf++;
+                if (r == 1) fa = false;
+            }
+        }
     }
 }
 

@@ -58,7 +58,7 @@ void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, l
                       const long long* pad_cell, const long long* pad_src, long long npad,
                       cudaStream_t s);
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min,
-                        double* Mout, DevStats* st, int grid_blocks, cudaStream_t s);
+                        double* Mout, DevStats* st, unsigned long long* work, int grid_blocks, cudaStream_t s);
 void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u,
                      const double* RT, double* M, long long ncell, cudaStream_t s);
 void launch_macros(int D, double K, const uint8_t* type, const double* M, double* rho, double* u,

@@ -26,20 +26,52 @@ namespace lbm {
 // ---------------------------------------------------------------------------
 struct LocalStats {
     unsigned long long q_max;
-    double disp_max;
+    double disp_max2;
     unsigned long long points;
 };
 
+// Landing cell of an integer displacement (dx, dy) from the emitting cell, or -1
+// when the population leaves the interior of its instance (Sec. III: discarded).
 template <int D>
-__device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, const uint8_t* type,
-                                             double* Mout, long long cell, const CellState<D>& c,
-                                             const Stencil<D>& st, const double* lf, const double* lg,
-                                             LocalStats& ls) {
-    constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
+__device__ __forceinline__ long long land(const Geometry& g, long long cell, long long lo, int n, int ix, int iy,
+                                          int dx, int dy) {
+    if constexpr (D == 1) {
+        long long x = cell + dx;
+        if (g.periodic[0]) {
+            long long r = (x - lo) % n;
+            if (r < 0) r += n;
+            return lo + r;
+        }
+        return (x < lo || x >= lo + n) ? -1 : x;
+    } else {
+        int tx = ix + dx, ty = iy + dy;
+        if (g.periodic[0]) {
+            tx %= g.nx;
+            if (tx < 0) tx += g.nx;
+        } else if (tx < g.pad || tx >= g.pad + g.nx) {
+            return -1;
+        }
+        if (g.periodic[1]) {
+            ty %= g.ny;
+            if (ty < 0) ty += g.ny;
+        } else if (ty < g.pad || ty >= g.pad + g.ny) {
+            return -1;
+        }
+        return (long long)ty * g.NX + tx;
+    }
+}
+
+// Moment streaming, Eq. (IIE3): T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i added at
+// x + c_i.  Level-0 points land on one cell; refined points are shared between the
+// cells they overlap (cloud-in-cell).
+template <int D>
+__device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                             long long cell, const CellState<D>& c, const Stencil<D>& st,
+                                             const double* lf, const double* lg, LocalStats& ls) {
+    constexpr int NM = Dim<D>::NM;
     const bool has_g = m.K > 0.0;
-    const double mfs = c.rho;                // rho dV f'   (Eq. IIE3a)
-    const double mgs = c.rho * m.K * c.RT;   // rho K RT dV g'
-    // position of the emitting cell
+    const double mfs = c.rho;               // rho dV f'
+    const double mgs = c.rho * m.K * c.RT;  // rho K RT dV g'
     long long lo = 0;
     int n = 0, ix = 0, iy = 0;
     if constexpr (D == 1) {
@@ -52,28 +84,11 @@ __device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, 
     }
     unsigned long long q = 0;
     double dmax2 = 0.0;
-    auto emit = [&](const double* cp, double dC) {
-        q++;
-        double t[D];
-#pragma unroll
-        for (int a = 0; a < D; a++) t[a] = (cp[a] - c.u[a]) * c.inv_sig;
-        double T[NF];
-        Basis<D, true>::eval(t, T);
-        double e = 1.0;
-#pragma unroll
-        for (int j = 0; j < NF; j++) e += lf[j] * T[j];
-        const double mf = mfs * dC * exp(-e);
-        double mg = 0.0;
-        if (has_g) {
-            double eg = 1.0;
-#pragma unroll
-            for (int j = 0; j < NG; j++) eg += lg[j] * T[j];
-            mg = mgs * dC * exp(-eg);
-        }
+    auto deposit = [&](long long tgt, const double* cp, double mf, double mg) {
+        if (tgt < 0 || type[tgt] != CELL_FLUID) return;
         double csq = 0.0;
 #pragma unroll
         for (int a = 0; a < D; a++) csq += cp[a] * cp[a];
-        dmax2 = fmax(dmax2, csq);
         double dM[NM];
         dM[0] = mf;
 #pragma unroll
@@ -87,76 +102,91 @@ __device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, 
         dM[iG0<D>()] = mg;
 #pragma unroll
         for (int gg = 0; gg < D; gg++) dM[iG1<D>(gg)] = cp[gg] * mg;
-        // cloud-in-cell split of the landing point x + c (exact for integer c)
+#pragma unroll
+        for (int mm = 0; mm < NM; mm++) atomicAdd(Mout + mm * g.ncell + tgt, dM[mm]);
+    };
+    auto row = [&](int cy, int xa, int xb) {
+        double y = 0.0;
+        if constexpr (D == 2) y = ((double)cy - c.u[1]) * c.inv_sig;
+        double cf[4], cg[3];
+        row_coeffs<D>(lf, lg, y, cf, cg);
+        for (int cx = xa; cx <= xb; cx++) {
+            const double x = ((double)cx - c.u[0]) * c.inv_sig;
+            const double mf = mfs * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+            const double mg = has_g ? mgs * exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+            double cp[D];
+            cp[0] = (double)cx;
+            if constexpr (D == 2) cp[1] = (double)cy;
+            deposit(land<D>(g, cell, lo, n, ix, iy, cx, cy), cp, mf, mg);
+        }
+        q += (unsigned long long)(xb - xa + 1);
+        const double ex = (double)(abs(xa) > abs(xb) ? xa : xb);
+        dmax2 = fmax(dmax2, ex * ex + (double)cy * (double)cy);
+    };
+    auto leaf = [&](const double* cp, double dC) {
+        const double x = (cp[0] - c.u[0]) * c.inv_sig;
+        double y = 0.0;
+        if constexpr (D == 2) y = (cp[1] - c.u[1]) * c.inv_sig;
+        double cf[4], cg[3];
+        row_coeffs<D>(lf, lg, y, cf, cg);
+        const double mf = mfs * dC * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+        const double mg = has_g ? mgs * dC * exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+        q++;
+        double csq = 0.0;
         int base[D];
         double w1[D];
 #pragma unroll
         for (int a = 0; a < D; a++) {
+            csq += cp[a] * cp[a];
             const double fl = floor(cp[a]);
             base[a] = (int)fl;
             w1[a] = cp[a] - fl;
         }
+        dmax2 = fmax(dmax2, csq);
         const int ncx = w1[0] > 0.0 ? 2 : 1;
         const int ncy = (D == 2 && w1[D - 1] > 0.0) ? 2 : 1;
         for (int sy = 0; sy < ncy; sy++)
             for (int sx = 0; sx < ncx; sx++) {
                 double w = sx ? w1[0] : 1.0 - w1[0];
-                long long tgt;
-                if constexpr (D == 1) {
-                    long long x = cell + base[0] + sx;
-                    if (g.periodic[0]) {
-                        long long r = (x - lo) % n;
-                        if (r < 0) r += n;
-                        x = lo + r;
-                    } else if (x < lo || x >= lo + n) {
-                        continue;
-                    }
-                    tgt = x;
-                } else {
-                    w *= sy ? w1[D - 1] : 1.0 - w1[D - 1];
-                    int tx = ix + base[0] + sx;
-                    int ty = iy + base[D - 1] + sy;
-                    if (g.periodic[0]) {
-                        tx %= g.nx;
-                        if (tx < 0) tx += g.nx;
-                    } else if (tx < g.pad || tx >= g.pad + g.nx) {
-                        continue;
-                    }
-                    if (g.periodic[1]) {
-                        ty %= g.ny;
-                        if (ty < 0) ty += g.ny;
-                    } else if (ty < g.pad || ty >= g.pad + g.ny) {
-                        continue;
-                    }
-                    tgt = (long long)ty * g.NX + tx;
-                }
-                if (type[tgt] != CELL_FLUID) continue;
-#pragma unroll
-                for (int mm = 0; mm < NM; mm++) atomicAdd(Mout + mm * g.ncell + tgt, w * dM[mm]);
+                if constexpr (D == 2) w *= sy ? w1[1] : 1.0 - w1[1];
+                deposit(land<D>(g, cell, lo, n, ix, iy, base[0] + sx, D == 2 ? base[D - 1] + sy : 0), cp, w * mf,
+                        w * mg);
             }
     };
-    st.for_each(emit);
+    st.for_each_row(row, leaf);
     if (q > ls.q_max) ls.q_max = q;
     ls.points += q;
-    ls.disp_max = fmax(ls.disp_max, sqrt(dmax2));
+    ls.disp_max2 = fmax(ls.disp_max2, dmax2);
 }
 
 template <int D>
 __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
-                                                          DevStats* stats) {
+                                                          DevStats* stats, unsigned long long* work) {
     constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ unsigned long long s_hist[64];
     __shared__ unsigned long long s_cells, s_feq, s_fmx, s_q;
     __shared__ unsigned long long s_dmax, s_pf, s_pg, s_pm;
+    // post-collision constraints of each thread's cell (kept out of registers)
+    __shared__ double s_con[128][NF + NG];
+    double* conF = s_con[threadIdx.x];
+    double* conG = conF + NF;
     for (int i = threadIdx.x; i < 64; i += blockDim.x) s_hist[i] = 0;
     if (threadIdx.x == 0) s_cells = s_feq = s_fmx = s_q = s_dmax = s_pf = s_pg = s_pm = 0;
     __syncthreads();
 
     LocalStats ls{0, 0.0, 0};
     unsigned long long my_cells = 0, my_pf = 0, my_pg = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell; cell += stride) {
+    const int lane = threadIdx.x & 31;
+    // Warps claim chunks of 32 consecutive cells: the cost of a cell varies with its
+    // temperature (q ~ (n sqrt RT)^D), so a static split leaves SMs idle at the end.
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(work, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)g.ncell) break;
+        const long long cell = (long long)base + lane;
+        if (cell >= g.ncell) continue;
         const uint8_t ty = type[cell];
         if (ty == CELL_SOLID) continue;
         double M[NM];
@@ -175,59 +205,41 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         const bool has_g = m.K > 0.0;
         double lf[NF], lg[NG];
         maxwell_start<D, NF>(c.RT, lf);
-        int sf = epr_newton<D, true>(c, st, c.cf, lf, m, my_pf);
-        int sg = 0;
-        if (has_g) {
-            maxwell_start<D, NG>(c.RT, lg);
-            sg = epr_newton<D, false>(c, st, c.cg, lg, m, my_pg);
-        } else {
+        maxwell_start<D, NG>(c.RT, lg);
 #pragma unroll
-            for (int j = 0; j < NG; j++) lg[j] = 0.0;
-        }
+        for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
+#pragma unroll
+        for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
+        int sf, sg;
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
         if (sf >= 0 && sg >= 0) {
             atomicAdd(&s_hist[sf < 63 ? sf : 63], 1ull);
             if (has_g) atomicAdd(&s_hist[sg < 63 ? sg : 63], 1ull);
         } else {
             // equilibrium constraints (omega = 1) for both populations
-            double ef[NF], eg[NG];
 #pragma unroll
-            for (int j = 0; j < NF; j++) ef[j] = 0.0;
+            for (int j = 0; j < NF; j++) conF[j] = 0.0;
 #pragma unroll
-            for (int j = 0; j < NG; j++) eg[j] = 0.0;
-            ef[0] = eg[0] = 1.0;
+            for (int j = 0; j < NG; j++) conG[j] = 0.0;
+            conF[0] = conG[0] = 1.0;
             int jj = 1 + D;
 #pragma unroll
             for (int a = 0; a < D; a++)
 #pragma unroll
                 for (int b = a; b < D; b++) {
-                    ef[jj] = eg[jj] = (a == b) ? 1.0 : 0.0;
+                    conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
                     jj++;
                 }
             maxwell_start<D, NF>(c.RT, lf);
-            sf = epr_newton<D, true>(c, st, ef, lf, m, my_pf);
-            sg = 0;
-            if (has_g) {
-                maxwell_start<D, NG>(c.RT, lg);
-                sg = epr_newton<D, false>(c, st, eg, lg, m, my_pg);
-            }
+            maxwell_start<D, NG>(c.RT, lg);
+            solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
             if (sf >= 0 && sg >= 0) {
                 atomicAdd(&s_feq, 1ull);
             } else {
-                // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S
-                double S = 0.0;
-                auto sum = [&](const double* cp, double dC) {
-                    double t2 = 0.0;
-#pragma unroll
-                    for (int a = 0; a < D; a++) {
-                        const double t = (cp[a] - c.u[a]) * c.inv_sig;
-                        t2 += t * t;
-                    }
-                    S += dC * exp(-0.5 * t2);
-                };
-                st.for_each(sum);
+                // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S (mass exact)
 #pragma unroll
                 for (int j = 0; j < NF; j++) lf[j] = 0.0;
-                lf[0] = log(S) - 1.0;
+                lf[0] = -1.0;
                 jj = 1 + D;
 #pragma unroll
                 for (int a = 0; a < D; a++)
@@ -236,6 +248,9 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
                         lf[jj] = (a == b) ? 0.5 : 0.0;
                         jj++;
                     }
+                double MF[MomentSet<D>::NF], MG[MomentSet<D>::NG];
+                moment_pass<D>(c, st, lf, lg, true, false, MF, MG);
+                lf[0] = log(MF[0]) - 1.0;
 #pragma unroll
                 for (int j = 0; j < NG; j++) lg[j] = lf[j];
                 atomicAdd(&s_fmx, 1ull);
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
     atomicAdd(&s_pg, my_pg);
     atomicAdd(&s_pm, ls.points);
     atomicMax(&s_q, ls.q_max);
-    atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(ls.disp_max));
+    atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(sqrt(ls.disp_max2)));
     __syncthreads();
     for (int i = threadIdx.x; i < 64; i += blockDim.x)
         if (s_hist[i]) atomicAdd(&stats->newton_hist[i], s_hist[i]);
@@ -370,14 +385,14 @@ int cell_update_blocks(int D, int device) {
 }
 
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, double* Mout,
-                        DevStats* st, int grid_blocks, cudaStream_t s) {
+                        DevStats* st, unsigned long long* work, int grid_blocks, cudaStream_t s) {
     long long need = (g.ncell + 127) / 128;
     int blocks = (int)(need < grid_blocks ? need : grid_blocks);
     if (blocks < 1) blocks = 1;
     if (g.D == 1)
-        cell_update_kernel<1><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st);
+        cell_update_kernel<1><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
     else
-        cell_update_kernel<2><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st);
+        cell_update_kernel<2><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
 }
 
 void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u, const double* RT,
