@@ -63,7 +63,11 @@ extern "C" {
 #define LELBM_BC_PERIODIC 2 /* wrap-around; must be set on both sides of an axis      */
 
 /* arithmetic of the step */
-#define LELBM_FP64 0 /* every operation in FP64                                     */
+#define LELBM_FP64 0  /* every operation in FP64                                     */
+#define LELBM_MIXED 1 /* EPR Newton passes in FP32, then one FP64 Newton pass; the
+                         streaming pass computes the populations in FP64 and checks
+                         their FP64 residual against tol (re-solving in FP64 on a
+                         miss); state, collision and accumulation in FP64          */
 
 typedef struct lelbm* lelbm_t;
 
@@ -89,7 +93,7 @@ typedef struct {
     int max_refine;      /* cap on N_r, 0..4                                           */
     double tol;          /* EPR residual tolerance in thermal units; paper: 1e-12      */
     int max_newton;      /* Newton update cap per solve, 1..60                         */
-    int precision;       /* LELBM_FP64                                                 */
+    int precision;       /* LELBM_FP64 or LELBM_MIXED                                  */
     const uint8_t* solid;/* host, one byte per padded cell, 1 = solid; NULL: none       */
     void* stream;        /* cudaStream_t to run on; NULL: a stream owned by the handle  */
 } lelbm_params;
@@ -109,6 +113,8 @@ typedef struct {
     long long points_f;           /* stencil points visited by fluon Newton passes  */
     long long points_g;           /* stencil points visited by phonon Newton passes */
     long long points_ms;          /* stencil points streamed (moment streaming)     */
+    long long points_32;          /* stencil points of FP32 Newton passes (mixed)   */
+    long long judge_redo;         /* mixed: cells re-solved in FP64 after the check */
 } lelbm_stats;
 
 /* Sizes of the structures this library was built with, so a binding can check

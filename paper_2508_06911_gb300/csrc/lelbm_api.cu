@@ -120,7 +120,8 @@ static int validate(const lelbm_params* p) {
     if (p->max_refine < 0 || p->max_refine > 4) return fail(nullptr, LELBM_E_INVAL, "max_refine must be 0..4");
     if (!(p->tol > 0.0)) return fail(nullptr, LELBM_E_INVAL, "tol must be > 0");
     if (p->max_newton < 1 || p->max_newton > 60) return fail(nullptr, LELBM_E_INVAL, "max_newton must be 1..60");
-    if (p->precision != LELBM_FP64) return fail(nullptr, LELBM_E_INVAL, "unknown precision");
+    if (p->precision != LELBM_FP64 && p->precision != LELBM_MIXED)
+        return fail(nullptr, LELBM_E_INVAL, "unknown precision");
     if (p->dims == 1 && p->n_batch > 1 && p->lengths)
         for (int b = 0; b < p->n_batch; b++)
             if (p->lengths[b] < 1) return fail(nullptr, LELBM_E_INVAL, "lengths[%d] < 1", b);
@@ -338,7 +339,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         delete h;
         return fail(nullptr, rc, "%s", e.empty() ? "device set-up failed" : e.c_str());
     }
-    h->blocks = cell_update_blocks(D, h->device);
+    h->blocks = cell_update_blocks(D, p->precision == LELBM_MIXED, h->device);
     *out = h;
     return LELBM_OK;
 }
@@ -459,7 +460,8 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
             if (rc) return rc;
             CUDA_TRY(h, cudaEventRecord(ev.first, h->stream));
         }
-        launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks, h->stream);
+        launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks,
+                           h->p.precision == LELBM_MIXED, h->stream);
         if (h->timing) {
             CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
             h->ev_used.push_back(ev);
@@ -494,6 +496,8 @@ static int read_stats(lelbm* h, lelbm_stats* s) {
         s->points_f = (long long)d.points_f;
         s->points_g = (long long)d.points_g;
         s->points_ms = (long long)d.points_ms;
+        s->points_32 = (long long)d.points_32;
+        s->judge_redo = (long long)d.judge_redo;
     }
     return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
 }

@@ -526,6 +526,63 @@ __device__ __forceinline__ void row_coeffs(const double* lf, const double* lg, d
     }
 }
 
+// Populations along one stencil row: x_k = x_a + k h (k = 0..n-1), f_k = exp(-e_f(x_k))
+// and g_k = exp(-e_g(x_k)) with e_f cubic and e_g quadratic in x (row_coeffs).  Short
+// rows call exp per point.  Long rows use multiplicative forward differences,
+// exp(-e(x + h)) = exp(-e(x)) exp(-d1), d1 <- d1 + d2, d2 <- d2 + d3 (d3 constant for
+// a cubic), with d1, d2, d3 taken from the exact difference polynomials; each row is
+// swept outwards from its centre so the rounding growth (~k^3/6 ulp after k steps)
+// stays far below the Newton tolerance where the populations matter.
+// point(k, x, f, g) is called once per point (in sweep order for long rows).
+constexpr int kRecurrenceMinRow = 12;
+
+template <class Pt>
+__device__ __forceinline__ void row_sweep(const double* cf, const double* cg, bool doF, bool doG, double x, double h,
+                                          int k0, int dir, int m, Pt& point) {
+    const double h2 = h * h, h3 = h2 * h;
+    double Ef = 0.0, R1f = 0.0, R2f = 0.0, R3f = 0.0, Eg = 0.0, R1g = 0.0, R2g = 0.0;
+    if (doF) {
+        const double d1 = cf[1] * h + cf[2] * (2.0 * x * h + h2) + cf[3] * (3.0 * x * x * h + 3.0 * x * h2 + h3);
+        const double d2 = 2.0 * cf[2] * h2 + cf[3] * (6.0 * x * h2 + 6.0 * h3);
+        Ef = exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+        R1f = exp(-d1);
+        R2f = exp(-d2);
+        R3f = exp(-6.0 * cf[3] * h3);
+    }
+    if (doG) {
+        const double d1 = cg[1] * h + cg[2] * (2.0 * x * h + h2);
+        Eg = exp(-((cg[2] * x + cg[1]) * x + cg[0]));
+        R1g = exp(-d1);
+        R2g = exp(-2.0 * cg[2] * h2);
+    }
+    for (int i = 0; i < m; i++) {
+        point(k0 + dir * i, x, Ef, Eg);
+        Ef *= R1f;
+        R1f *= R2f;
+        R2f *= R3f;
+        Eg *= R1g;
+        R1g *= R2g;
+        x += h;
+    }
+}
+
+template <class Pt>
+__device__ __forceinline__ void row_eval(const double* cf, const double* cg, bool doF, bool doG, double xa, double h,
+                                         int n, Pt& point) {
+    if (n < kRecurrenceMinRow) {
+        double x = xa;
+        for (int k = 0; k < n; k++, x += h) {
+            const double f = doF ? exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0])) : 0.0;
+            const double g = doG ? exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+            point(k, x, f, g);
+        }
+        return;
+    }
+    const int kc = n >> 1;
+    row_sweep(cf, cg, doF, doG, xa + kc * h, h, kc, 1, n - kc, point);
+    row_sweep(cf, cg, doF, doG, xa + (kc - 1) * h, -h, kc - 1, -1, kc, point);
+}
+
 // One pass over the velocity set accumulating the population moments of f
 // (if doF) and g (if doG) for the multipliers lf, lg.  Returns the point count.
 template <int D>
@@ -548,23 +605,21 @@ __device__ __forceinline__ unsigned long long moment_pass(const CellState<D>& c,
         for (int a = 0; a <= MS::PF; a++) SF[a] = 0.0;
 #pragma unroll
         for (int a = 0; a <= MS::PG; a++) SG[a] = 0.0;
-        for (int cx = xa; cx <= xb; cx++) {
-            const double x = ((double)cx - c.u[0]) * c.inv_sig;
+        auto point = [&](int, double x, double f, double g) {
             double p[MS::PF + 1];
             p[0] = 1.0;
 #pragma unroll
             for (int k = 1; k <= MS::PF; k++) p[k] = p[k - 1] * x;
             if (doF) {
-                const double f = exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
 #pragma unroll
                 for (int a = 0; a <= MS::PF; a++) SF[a] += p[a] * f;
             }
             if (doG) {
-                const double g = exp(-((cg[2] * x + cg[1]) * x + cg[0]));
 #pragma unroll
                 for (int a = 0; a <= MS::PG; a++) SG[a] += p[a] * g;
             }
-        }
+        };
+        row_eval(cf, cg, doF, doG, ((double)xa - c.u[0]) * c.inv_sig, c.inv_sig, xb - xa + 1, point);
         q += (unsigned long long)(xb - xa + 1);
         if constexpr (D == 1) {
 #pragma unroll
@@ -619,11 +674,50 @@ __device__ __forceinline__ unsigned long long moment_pass(const CellState<D>& c,
     return q;
 }
 
+// LDL^T factorisation of the packed lower triangle and solve A x = b: the same
+// SPD solve as Cholesky without square roots, one reciprocal per column.
+template <typename T, int N>
+__device__ __forceinline__ bool ldlt_solve(T* A, T* b) {
+    T inv[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        T d = A[tri(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; k++) d -= A[tri(j, k)] * A[tri(j, k)] * A[tri(k, k)];
+        if (!(d > T(0))) return false;
+        A[tri(j, j)] = d;
+        inv[j] = T(1) / d;
+#pragma unroll
+        for (int i = j + 1; i < N; i++) {
+            T t = A[tri(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; k++) t -= A[tri(i, k)] * A[tri(j, k)] * A[tri(k, k)];
+            A[tri(i, j)] = t * inv[j];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        T t = b[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) t -= A[tri(i, k)] * b[k];
+        b[i] = t;
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
+        T t = b[i] * inv[i];
+#pragma unroll
+        for (int k = i + 1; k < N; k++) t -= A[tri(k, i)] * b[k];
+        b[i] = t;
+    }
+    return true;
+}
+
 // Newton update from the moments of the current pass (Eq. IID8-IID11).
 // Returns 0 (updated), 1 (converged: the polishing update was applied),
 // -1 (non-finite residual or non-positive pivot), -2 (iteration cap).
 template <int D, bool FLUON>
-__device__ __forceinline__ int newton_step(const double* Mom, const double* con, double* lam, const Model& m, int it) {
+__device__ __forceinline__ int newton_step_tol(const double* Mom, const double* con, double* lam, double tol,
+                                               int max_iter, int it) {
     constexpr int N = Basis<D, FLUON>::N;
     constexpr int P = FLUON ? MomentSet<D>::PF : MomentSet<D>::PG;
     double r[N];
@@ -636,18 +730,53 @@ __device__ __forceinline__ int newton_step(const double* Mom, const double* con,
         rmax = fmax(rmax, fabs(r[j]));
     }
     if (!finite) return -1;
-    const bool conv = rmax <= m.tol;
-    if (!conv && it >= m.max_iter) return -2;
+    const bool conv = rmax <= tol;
+    if (!conv && it >= max_iter) return -2;
     double A[N * (N + 1) / 2];
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
         for (int j = 0; j <= i; j++)
             A[tri(i, j)] = Mom[tix(bx<D, FLUON>(i) + bx<D, FLUON>(j), by<D, FLUON>(i) + by<D, FLUON>(j), P)];
-    if (!chol_solve<N>(A, r)) return -1;
+    if (!ldlt_solve<double, N>(A, r)) return -1;
 #pragma unroll
     for (int j = 0; j < N; j++) lam[j] += r[j];
     return conv ? 1 : 0;
+}
+
+// The same update from FP32 moments with an FP32 solve (FP32 Newton phase).
+template <int D, bool FLUON>
+__device__ __forceinline__ int newton_step32(const float* Mom, const double* con, double* lam, float tol, int max_iter,
+                                             int it) {
+    constexpr int N = Basis<D, FLUON>::N;
+    constexpr int P = FLUON ? MomentSet<D>::PF : MomentSet<D>::PG;
+    float r[N];
+    float rmax = 0.f;
+    bool finite = true;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        r[j] = Mom[tix(bx<D, FLUON>(j), by<D, FLUON>(j), P)] - (float)con[j];
+        finite = finite && isfinite(r[j]);
+        rmax = fmaxf(rmax, fabsf(r[j]));
+    }
+    if (!finite) return -1;
+    const bool conv = rmax <= tol;
+    if (!conv && it >= max_iter) return -2;
+    float A[N * (N + 1) / 2];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++)
+            A[tri(i, j)] = Mom[tix(bx<D, FLUON>(i) + bx<D, FLUON>(j), by<D, FLUON>(i) + by<D, FLUON>(j), P)];
+    if (!ldlt_solve<float, N>(A, r)) return -1;
+#pragma unroll
+    for (int j = 0; j < N; j++) lam[j] += (double)r[j];
+    return conv ? 1 : 0;
+}
+
+template <int D, bool FLUON>
+__device__ __forceinline__ int newton_step(const double* Mom, const double* con, double* lam, const Model& m, int it) {
+    return newton_step_tol<D, FLUON>(Mom, con, lam, m.tol, m.max_iter, it);
 }
 
 // Joint Newton iterations of the fluon and phonon multipliers: every pass
@@ -688,6 +817,149 @@ __device__ __forceinline__ void solve_fg(const CellState<D>& c, const Stencil<D>
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: the Newton passes over the velocity set run in FP32 (FP32 is
+// about 60x the FP64 rate on GB300); the small Cholesky solves stay FP64.  The
+// FP32 iterate is then corrected by one full FP64 Newton pass, and the
+// streaming pass checks the FP64 residual of exactly the populations it
+// deposits against the same tolerance as the FP64 path.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& c, const Stencil<D>& st,
+                                                            const double* lf, const double* lg, bool doF, bool doG,
+                                                            float* MF, float* MG) {
+    using MS = MomentSet<D>;
+#pragma unroll
+    for (int i = 0; i < MS::NF; i++) MF[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < MS::NG; i++) MG[i] = 0.f;
+    unsigned long long q = 0;
+    const float s32 = (float)c.inv_sig;
+    auto row = [&](int cy, int xa, int xb) {
+        double y = 0.0;
+        if constexpr (D == 2) y = ((double)cy - c.u[1]) * c.inv_sig;
+        double cfd[4], cgd[3];
+        row_coeffs<D>(lf, lg, y, cfd, cgd);
+        const float cf0 = (float)cfd[0], cf1 = (float)cfd[1], cf2 = (float)cfd[2], cf3 = (float)cfd[3];
+        const float cg0 = (float)cgd[0], cg1 = (float)cgd[1], cg2 = (float)cgd[2];
+        const float x0 = (float)(((double)xa - c.u[0]) * c.inv_sig);
+        float SF[MS::PF + 1], SG[MS::PG + 1];
+#pragma unroll
+        for (int a = 0; a <= MS::PF; a++) SF[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a <= MS::PG; a++) SG[a] = 0.f;
+        for (int k = 0; k <= xb - xa; k++) {
+            const float x = fmaf((float)k, s32, x0);
+            float pw[MS::PF + 1];
+            pw[0] = 1.f;
+#pragma unroll
+            for (int e = 1; e <= MS::PF; e++) pw[e] = pw[e - 1] * x;
+            if (doF) {
+                const float f = __expf(-fmaf(fmaf(fmaf(cf3, x, cf2), x, cf1), x, cf0));
+#pragma unroll
+                for (int a = 0; a <= MS::PF; a++) SF[a] = fmaf(pw[a], f, SF[a]);
+            }
+            if (doG) {
+                const float g = __expf(-fmaf(fmaf(cg2, x, cg1), x, cg0));
+#pragma unroll
+                for (int a = 0; a <= MS::PG; a++) SG[a] = fmaf(pw[a], g, SG[a]);
+            }
+        }
+        q += (unsigned long long)(xb - xa + 1);
+        if constexpr (D == 1) {
+#pragma unroll
+            for (int a = 0; a <= MS::PF; a++) MF[a] += SF[a];
+#pragma unroll
+            for (int a = 0; a <= MS::PG; a++) MG[a] += SG[a];
+        } else {
+            const float yf = (float)y;
+            float yp[MS::PF + 1];
+            yp[0] = 1.f;
+#pragma unroll
+            for (int e = 1; e <= MS::PF; e++) yp[e] = yp[e - 1] * yf;
+#pragma unroll
+            for (int b = 0; b <= MS::PF; b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] = fmaf(SF[a], yp[b], MF[tix(a, b, MS::PF)]);
+#pragma unroll
+            for (int b = 0; b <= MS::PG; b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] = fmaf(SG[a], yp[b], MG[tix(a, b, MS::PG)]);
+        }
+    };
+    auto leaf = [&](const double* cp, double dC) {  // refined points, FP32 as well
+        const double yd = D == 2 ? (cp[D - 1] - c.u[D - 1]) * c.inv_sig : 0.0;
+        double cfd[4], cgd[3];
+        row_coeffs<D>(lf, lg, yd, cfd, cgd);
+        const float x = (float)((cp[0] - c.u[0]) * c.inv_sig), y = (float)yd, w = (float)dC;
+        float px[MS::PF + 1], py[MS::PF + 1];
+        px[0] = py[0] = 1.f;
+#pragma unroll
+        for (int k = 1; k <= MS::PF; k++) {
+            px[k] = px[k - 1] * x;
+            py[k] = py[k - 1] * y;
+        }
+        if (doF) {
+            const float f =
+                w * __expf(-fmaf(fmaf(fmaf((float)cfd[3], x, (float)cfd[2]), x, (float)cfd[1]), x, (float)cfd[0]));
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? MS::PF : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += px[a] * py[b] * f;
+        }
+        if (doG) {
+            const float g = w * __expf(-fmaf(fmaf((float)cgd[2], x, (float)cgd[1]), x, (float)cgd[0]));
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? MS::PG : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] += px[a] * py[b] * g;
+        }
+        q++;
+    };
+    st.for_each_row(row, leaf);
+    return q;
+}
+
+// FP32 Newton phase followed by one FP64 Newton pass.  Returns false when a
+// solve broke down (the caller then runs the plain FP64 solve).  sf, sg count
+// the FP64 updates; np32 counts the points of the FP32 passes.
+template <int D>
+__device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Stencil<D>& st, const double* conF,
+                                               const double* conG, bool has_g, double* lf, double* lg,
+                                               const Model& m, int& sf, int& sg, unsigned long long& npf,
+                                               unsigned long long& npg, unsigned long long& np32) {
+    using MS = MomentSet<D>;
+    constexpr float tol32 = 2e-5f;  // thermal units; the FP64 pass takes it to round-off
+    constexpr int max32 = 12;
+    bool fa = true, ga = has_g;
+    for (int it = 0; (fa || ga) && it < max32; it++) {
+        float MF32[MS::NF], MG32[MS::NG];
+        np32 += moment_pass32<D>(c, st, lf, lg, fa, ga, MF32, MG32);
+        if (ga) {
+            const int r = newton_step32<D, false>(MG32, conG, lg, tol32, max32, it);
+            if (r < 0) return false;
+            if (r == 1) ga = false;
+        }
+        if (fa) {
+            const int r = newton_step32<D, true>(MF32, conF, lf, tol32, max32, it);
+            if (r < 0) return false;
+            if (r == 1) fa = false;
+        }
+    }
+    double MF[MS::NF], MG[MS::NG];
+    const unsigned long long q = moment_pass<D>(c, st, lf, lg, true, has_g, MF, MG);
+    sg = 0;
+    if (has_g) {
+        npg += q;
+        if (newton_step_tol<D, false>(MG, conG, lg, m.tol, 1, 0) < 0) return false;
+        sg = 1;
+    }
+    npf += q;
+    if (newton_step_tol<D, true>(MF, conF, lf, m.tol, 1, 0) < 0) return false;
+    sf = 1;
+    return true;
 }
 
 template <int D>

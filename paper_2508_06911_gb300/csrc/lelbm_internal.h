@@ -52,17 +52,20 @@ struct DevStats {
     unsigned long long points_f;       // stencil points of fluon Newton passes
     unsigned long long points_g;       // stencil points of phonon Newton passes
     unsigned long long points_ms;      // stencil points streamed
+    unsigned long long points_32;      // stencil points of FP32 Newton passes (mixed path)
+    unsigned long long judge_redo;     // mixed path: cells whose FP64 check failed and were re-solved
 };
 
 void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, long long ncell,
                       const long long* pad_cell, const long long* pad_src, long long npad,
                       cudaStream_t s);
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min,
-                        double* Mout, DevStats* st, unsigned long long* work, int grid_blocks, cudaStream_t s);
+                        double* Mout, DevStats* st, unsigned long long* work, int grid_blocks, bool mixed,
+                        cudaStream_t s);
 void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u,
                      const double* RT, double* M, long long ncell, cudaStream_t s);
 void launch_macros(int D, double K, const uint8_t* type, const double* M, double* rho, double* u,
                    double* RT, long long ncell, cudaStream_t s);
-int cell_update_blocks(int D, int device);
+int cell_update_blocks(int D, bool mixed, int device);
 
 }  // namespace lbm

@@ -64,14 +64,28 @@ __device__ __forceinline__ long long land(const Geometry& g, long long cell, lon
 // Moment streaming, Eq. (IIE3): T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i added at
 // x + c_i.  Level-0 points land on one cell; refined points are shared between the
 // cells they overlap (cloud-in-cell).
-template <int D>
-__device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+//
+// With CHECK, the same pass also accumulates the moments of degree <= 3 (fluons)
+// and <= 2 (phonons) of the deposited populations and returns whether their
+// residual against conF / conG is within the tolerance (the FP64 judge of the
+// mixed path).  sign = -1 removes a previous deposit of the same populations.
+template <int D, bool CHECK>
+__device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                              long long cell, const CellState<D>& c, const Stencil<D>& st,
-                                             const double* lf, const double* lg, LocalStats& ls) {
+                                             const double* lf, const double* lg, LocalStats& ls, double sign = 1.0,
+                                             const double* conF = nullptr, const double* conG = nullptr) {
     constexpr int NM = Dim<D>::NM;
+    constexpr int RF = D == 1 ? 4 : 10, RG = D == 1 ? 3 : 6;  // monomials of degree <= 3 / <= 2
     const bool has_g = m.K > 0.0;
-    const double mfs = c.rho;               // rho dV f'
-    const double mgs = c.rho * m.K * c.RT;  // rho K RT dV g'
+    const double mfs = sign * c.rho;               // rho dV f'
+    const double mgs = sign * c.rho * m.K * c.RT;  // rho K RT dV g'
+    double RFm[RF], RGm[RG];
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int i = 0; i < RF; i++) RFm[i] = 0.0;
+#pragma unroll
+        for (int i = 0; i < RG; i++) RGm[i] = 0.0;
+    }
     long long lo = 0;
     int n = 0, ix = 0, iy = 0;
     if constexpr (D == 1) {
@@ -110,14 +124,36 @@ __device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, 
         if constexpr (D == 2) y = ((double)cy - c.u[1]) * c.inv_sig;
         double cf[4], cg[3];
         row_coeffs<D>(lf, lg, y, cf, cg);
-        for (int cx = xa; cx <= xb; cx++) {
-            const double x = ((double)cx - c.u[0]) * c.inv_sig;
-            const double mf = mfs * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
-            const double mg = has_g ? mgs * exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+        double SF[4] = {0.0, 0.0, 0.0, 0.0}, SG[3] = {0.0, 0.0, 0.0};
+        auto point = [&](int k, double x, double f, double gp) {
+            const int cx = xa + k;
+            if constexpr (CHECK) {
+                const double x2 = x * x;
+                SF[0] += f;
+                SF[1] += x * f;
+                SF[2] += x2 * f;
+                SF[3] += x2 * x * f;
+                SG[0] += gp;
+                SG[1] += x * gp;
+                SG[2] += x2 * gp;
+            }
             double cp[D];
             cp[0] = (double)cx;
             if constexpr (D == 2) cp[1] = (double)cy;
-            deposit(land<D>(g, cell, lo, n, ix, iy, cx, cy), cp, mf, mg);
+            deposit(land<D>(g, cell, lo, n, ix, iy, cx, cy), cp, mfs * f, mgs * gp);
+        };
+        row_eval(cf, cg, true, has_g, ((double)xa - c.u[0]) * c.inv_sig, c.inv_sig, xb - xa + 1, point);
+        if constexpr (CHECK) {
+            // fold y^b into the moments x^a y^b (a + b <= 3 / <= 2)
+            double yp[4] = {1.0, y, y * y, y * y * y};
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 3 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 3; a++) RFm[tix(a, b, 3)] += SF[a] * yp[b];
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 2 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 2; a++) RGm[tix(a, b, 2)] += SG[a] * yp[b];
         }
         q += (unsigned long long)(xb - xa + 1);
         const double ex = (double)(abs(xa) > abs(xb) ? xa : xb);
@@ -129,8 +165,20 @@ __device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, 
         if constexpr (D == 2) y = (cp[1] - c.u[1]) * c.inv_sig;
         double cf[4], cg[3];
         row_coeffs<D>(lf, lg, y, cf, cg);
-        const double mf = mfs * dC * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
-        const double mg = has_g ? mgs * dC * exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+        const double f = dC * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+        const double gp = has_g ? dC * exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+        const double mf = mfs * f, mg = mgs * gp;
+        if constexpr (CHECK) {
+            double px[4] = {1.0, x, x * x, x * x * x}, py[4] = {1.0, y, y * y, y * y * y};
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 3 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 3; a++) RFm[tix(a, b, 3)] += px[a] * py[b] * f;
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 2 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 2; a++) RGm[tix(a, b, 2)] += px[a] * py[b] * gp;
+        }
         q++;
         double csq = 0.0;
         int base[D];
@@ -157,26 +205,46 @@ __device__ __forceinline__ void scatter_cell(const Model& m, const Geometry& g, 
     if (q > ls.q_max) ls.q_max = q;
     ls.points += q;
     ls.disp_max2 = fmax(ls.disp_max2, dmax2);
+    if constexpr (CHECK) {
+        double rmax = 0.0;
+        bool finite = true;
+#pragma unroll
+        for (int j = 0; j < RF; j++) {
+            const double r = RFm[tix(bx<D, true>(j), by<D, true>(j), 3)] - conF[j];
+            finite = finite && isfinite(r);
+            rmax = fmax(rmax, fabs(r));
+        }
+        if (has_g) {
+#pragma unroll
+            for (int j = 0; j < RG; j++) {
+                const double r = RGm[tix(bx<D, false>(j), by<D, false>(j), 2)] - conG[j];
+                finite = finite && isfinite(r);
+                rmax = fmax(rmax, fabs(r));
+            }
+        }
+        return finite && rmax <= m.tol;
+    }
+    return true;
 }
 
-template <int D>
+template <int D, bool MIXED>
 __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
                                                           DevStats* stats, unsigned long long* work) {
     constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ unsigned long long s_hist[64];
     __shared__ unsigned long long s_cells, s_feq, s_fmx, s_q;
-    __shared__ unsigned long long s_dmax, s_pf, s_pg, s_pm;
+    __shared__ unsigned long long s_dmax, s_pf, s_pg, s_pm, s_p32, s_redo;
     // post-collision constraints of each thread's cell (kept out of registers)
     __shared__ double s_con[128][NF + NG];
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
     for (int i = threadIdx.x; i < 64; i += blockDim.x) s_hist[i] = 0;
-    if (threadIdx.x == 0) s_cells = s_feq = s_fmx = s_q = s_dmax = s_pf = s_pg = s_pm = 0;
+    if (threadIdx.x == 0) s_cells = s_feq = s_fmx = s_q = s_dmax = s_pf = s_pg = s_pm = s_p32 = s_redo = 0;
     __syncthreads();
 
     LocalStats ls{0, 0.0, 0};
-    unsigned long long my_cells = 0, my_pf = 0, my_pg = 0;
+    unsigned long long my_cells = 0, my_pf = 0, my_pg = 0, my_p32 = 0, my_redo = 0;
     const int lane = threadIdx.x & 31;
     // Warps claim chunks of 32 consecutive cells: the cost of a cell varies with its
     // temperature (q ~ (n sqrt RT)^D), so a static split leaves SMs idle at the end.
@@ -211,6 +279,23 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
 #pragma unroll
         for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
         int sf, sg;
+        bool mixed_ok = false;
+        if constexpr (MIXED) {
+            mixed_ok = solve_fg_mixed<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg, my_p32);
+            if (mixed_ok) {
+                // stream and judge in one FP64 pass; on a miss, take the deposit back and
+                // finish the solve in FP64 from the current multipliers
+                if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, ls, 1.0, conF, conG)) {
+                    atomicAdd(&s_hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
+                    continue;
+                }
+                scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls, -1.0);
+                my_redo++;
+            } else {
+                maxwell_start<D, NF>(c.RT, lf);
+                maxwell_start<D, NG>(c.RT, lg);
+            }
+        }
         solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
         if (sf >= 0 && sg >= 0) {
             atomicAdd(&s_hist[sf < 63 ? sf : 63], 1ull);
@@ -257,9 +342,11 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
                 atomicMin(&stats->first_fail, (unsigned long long)cell);
             }
         }
-        scatter_cell<D>(m, g, type, Mout, cell, c, st, lf, lg, ls);
+        scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls);
     }
     atomicAdd(&s_cells, my_cells);
+    atomicAdd(&s_p32, my_p32);
+    atomicAdd(&s_redo, my_redo);
     atomicAdd(&s_pf, my_pf);
     atomicAdd(&s_pg, my_pg);
     atomicAdd(&s_pm, ls.points);
@@ -273,6 +360,8 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         atomicAdd(&stats->points_f, s_pf);
         atomicAdd(&stats->points_g, s_pg);
         atomicAdd(&stats->points_ms, s_pm);
+        atomicAdd(&stats->points_32, s_p32);
+        if (s_redo) atomicAdd(&stats->judge_redo, s_redo);
         if (s_feq) atomicAdd(&stats->fallback_eq, s_feq);
         if (s_fmx) atomicAdd(&stats->fallback_mx, s_fmx);
         atomicMax(&stats->q_max, s_q);
@@ -371,28 +460,37 @@ void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, l
                                                    pad_src, npad);
 }
 
-int cell_update_blocks(int D, int device) {
+int cell_update_blocks(int D, bool mixed, int device) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     int per_sm = 0;
     if (D == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_update_kernel<1>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, mixed ? cell_update_kernel<1, true> : cell_update_kernel<1, false>, 128, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_update_kernel<2>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, mixed ? cell_update_kernel<2, true> : cell_update_kernel<2, false>, 128, 0);
     if (per_sm < 1) per_sm = 1;
     if (sms < 1) sms = 1;
     return sms * per_sm;
 }
 
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, double* Mout,
-                        DevStats* st, unsigned long long* work, int grid_blocks, cudaStream_t s) {
+                        DevStats* st, unsigned long long* work, int grid_blocks, bool mixed, cudaStream_t s) {
     long long need = (g.ncell + 127) / 128;
     int blocks = (int)(need < grid_blocks ? need : grid_blocks);
     if (blocks < 1) blocks = 1;
-    if (g.D == 1)
-        cell_update_kernel<1><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
-    else
-        cell_update_kernel<2><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+    if (g.D == 1) {
+        if (mixed)
+            cell_update_kernel<1, true><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+        else
+            cell_update_kernel<1, false><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+    } else {
+        if (mixed)
+            cell_update_kernel<2, true><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+        else
+            cell_update_kernel<2, false><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+    }
 }
 
 void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u, const double* RT,

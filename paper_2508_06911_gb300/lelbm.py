@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "liblelbm.so")
 LELBM_OK, LELBM_E_INVAL, LELBM_E_NOMEM, LELBM_E_CUDA, LELBM_E_EPR, LELBM_E_TIMEOUT, LELBM_E_STATE = range(7)
 LELBM_BC_OUTFLOW, LELBM_BC_INFLOW, LELBM_BC_PERIODIC = 0, 1, 2
 LELBM_FP64 = 0
+LELBM_MIXED = 1
 STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_EPR", 5: "E_TIMEOUT", 6: "E_STATE"}
 
 
@@ -64,6 +65,8 @@ class lelbm_stats(ctypes.Structure):
         ("points_f", ctypes.c_longlong),
         ("points_g", ctypes.c_longlong),
         ("points_ms", ctypes.c_longlong),
+        ("points_32", ctypes.c_longlong),
+        ("judge_redo", ctypes.c_longlong),
     ]
 
 
