@@ -117,7 +117,7 @@ __device__ __forceinline__ void collide(const double* M, const Model& m, CellSta
         const double k2 = s2 / ((D + K) * RT);
         const double k3 = s3 / ((D + K + 2) * RT * c.sig);
         const double Kn = fmax(k2, k3);
-        if (Kn > 0.0) {
+        if (Kn > 0.01) {  // below 0.01 the limiter leaves omega unchanged
             const double ks = log10(Kn);
             if (ks >= -1.0) {
                 wf = wb = wh = 1.0;
@@ -405,6 +405,25 @@ __device__ __forceinline__ void maxwell_start(double RT, double* lam) {
         for (int b = a; b < D; b++) lam[j++] = (a == b) ? 0.5 : 0.0;
 }
 
+// Eq. (IID13) for both populations with one logarithm.
+template <int D, int NFv, int NGv>
+__device__ __forceinline__ void maxwell_start_fg(double RT, double* lf, double* lg) {
+    const double l0 = -1.0 + 0.5 * D * log(2.0 * 3.14159265358979323846 * RT);
+#pragma unroll
+    for (int j = 0; j < NFv; j++) lf[j] = 0.0;
+#pragma unroll
+    for (int j = 0; j < NGv; j++) lg[j] = 0.0;
+    lf[0] = lg[0] = l0;
+    int j = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) {
+            lf[j] = lg[j] = (a == b) ? 0.5 : 0.0;
+            j++;
+        }
+}
+
 // Newton-Raphson on the multipliers (Eq. IID8-IID11): returns the number of
 // updates (converged, one polishing update included), -1 on a breakdown
 // (non-finite residual, non-positive pivot), -2 at the iteration cap.
@@ -527,14 +546,15 @@ __device__ __forceinline__ void row_coeffs(const double* lf, const double* lg, d
 }
 
 // Populations along one stencil row: x_k = x_a + k h (k = 0..n-1), f_k = exp(-e_f(x_k))
-// and g_k = exp(-e_g(x_k)) with e_f cubic and e_g quadratic in x (row_coeffs).  Short
-// rows call exp per point.  Long rows use multiplicative forward differences,
+// and g_k = exp(-e_g(x_k)) with e_f cubic and e_g quadratic in x (row_coeffs).  Rows
+// of fewer than 4 points call exp per point.  Longer rows use multiplicative forward
+// differences,
 // exp(-e(x + h)) = exp(-e(x)) exp(-d1), d1 <- d1 + d2, d2 <- d2 + d3 (d3 constant for
 // a cubic), with d1, d2, d3 taken from the exact difference polynomials; each row is
-// swept outwards from its centre so the rounding growth (~k^3/6 ulp after k steps)
-// stays far below the Newton tolerance where the populations matter.
+// swept in one pass when short and outwards from its centre when long, so the rounding
+// growth (~k^3/6 ulp after k steps) stays far below the Newton tolerance.
 // point(k, x, f, g) is called once per point (in sweep order for long rows).
-constexpr int kRecurrenceMinRow = 12;
+constexpr int kRecurrenceMinRow = 24;
 
 template <class Pt>
 __device__ __forceinline__ void row_sweep(const double* cf, const double* cg, bool doF, bool doG, double x, double h,
@@ -569,13 +589,17 @@ __device__ __forceinline__ void row_sweep(const double* cf, const double* cg, bo
 template <class Pt>
 __device__ __forceinline__ void row_eval(const double* cf, const double* cg, bool doF, bool doG, double xa, double h,
                                          int n, Pt& point) {
-    if (n < kRecurrenceMinRow) {
+    if (n < 4) {
         double x = xa;
         for (int k = 0; k < n; k++, x += h) {
             const double f = doF ? exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0])) : 0.0;
             const double g = doG ? exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
             point(k, x, f, g);
         }
+        return;
+    }
+    if (n < kRecurrenceMinRow) {  // one sweep: at most ~kRecurrenceMinRow^3/6 ulp at the far end
+        row_sweep(cf, cg, doF, doG, xa, h, 0, 1, n, point);
         return;
     }
     const int kc = n >> 1;
@@ -837,13 +861,37 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
     for (int i = 0; i < MS::NG; i++) MG[i] = 0.f;
     unsigned long long q = 0;
     const float s32 = (float)c.inv_sig;
+    float lf32[Basis<D, true>::N], lg32[Basis<D, false>::N];
+#pragma unroll
+    for (int j = 0; j < Basis<D, true>::N; j++) lf32[j] = (float)lf[j];
+#pragma unroll
+    for (int j = 0; j < Basis<D, false>::N; j++) lg32[j] = (float)lg[j];
+    auto coeffs32 = [&](float y, float* cf, float* cg) {
+        if constexpr (D == 1) {
+            cf[0] = 1.f + lf32[0];
+            cf[1] = lf32[1];
+            cf[2] = lf32[2];
+            cf[3] = lf32[3];
+            cg[0] = 1.f + lg32[0];
+            cg[1] = lg32[1];
+            cg[2] = lg32[2];
+        } else {
+            cf[0] = 1.f + lf32[0] + y * (lf32[2] + y * (lf32[5] + y * lf32[9]));
+            cf[1] = lf32[1] + y * (lf32[4] + y * lf32[7]);
+            cf[2] = lf32[3] + y * lf32[8];
+            cf[3] = lf32[6];
+            cg[0] = 1.f + lg32[0] + y * (lg32[2] + y * lg32[5]);
+            cg[1] = lg32[1] + y * lg32[4];
+            cg[2] = lg32[3];
+        }
+    };
     auto row = [&](int cy, int xa, int xb) {
-        double y = 0.0;
-        if constexpr (D == 2) y = ((double)cy - c.u[1]) * c.inv_sig;
-        double cfd[4], cgd[3];
-        row_coeffs<D>(lf, lg, y, cfd, cgd);
-        const float cf0 = (float)cfd[0], cf1 = (float)cfd[1], cf2 = (float)cfd[2], cf3 = (float)cfd[3];
-        const float cg0 = (float)cgd[0], cg1 = (float)cgd[1], cg2 = (float)cgd[2];
+        float y = 0.f;
+        if constexpr (D == 2) y = (float)(((double)cy - c.u[1]) * c.inv_sig);
+        float cfv[4], cgv[3];
+        coeffs32(y, cfv, cgv);
+        const float cf0 = cfv[0], cf1 = cfv[1], cf2 = cfv[2], cf3 = cfv[3];
+        const float cg0 = cgv[0], cg1 = cgv[1], cg2 = cgv[2];
         const float x0 = (float)(((double)xa - c.u[0]) * c.inv_sig);
         float SF[MS::PF + 1], SG[MS::PG + 1];
 #pragma unroll
@@ -874,11 +922,10 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
 #pragma unroll
             for (int a = 0; a <= MS::PG; a++) MG[a] += SG[a];
         } else {
-            const float yf = (float)y;
             float yp[MS::PF + 1];
             yp[0] = 1.f;
 #pragma unroll
-            for (int e = 1; e <= MS::PF; e++) yp[e] = yp[e - 1] * yf;
+            for (int e = 1; e <= MS::PF; e++) yp[e] = yp[e - 1] * y;
 #pragma unroll
             for (int b = 0; b <= MS::PF; b++)
 #pragma unroll
@@ -890,10 +937,10 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
         }
     };
     auto leaf = [&](const double* cp, double dC) {  // refined points, FP32 as well
-        const double yd = D == 2 ? (cp[D - 1] - c.u[D - 1]) * c.inv_sig : 0.0;
-        double cfd[4], cgd[3];
-        row_coeffs<D>(lf, lg, yd, cfd, cgd);
-        const float x = (float)((cp[0] - c.u[0]) * c.inv_sig), y = (float)yd, w = (float)dC;
+        const float y = D == 2 ? (float)((cp[D - 1] - c.u[D - 1]) * c.inv_sig) : 0.f;
+        float cfd[4], cgd[3];
+        coeffs32(y, cfd, cgd);
+        const float x = (float)((cp[0] - c.u[0]) * c.inv_sig), w = (float)dC;
         float px[MS::PF + 1], py[MS::PF + 1];
         px[0] = py[0] = 1.f;
 #pragma unroll
@@ -902,15 +949,14 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
             py[k] = py[k - 1] * y;
         }
         if (doF) {
-            const float f =
-                w * __expf(-fmaf(fmaf(fmaf((float)cfd[3], x, (float)cfd[2]), x, (float)cfd[1]), x, (float)cfd[0]));
+            const float f = w * __expf(-fmaf(fmaf(fmaf(cfd[3], x, cfd[2]), x, cfd[1]), x, cfd[0]));
 #pragma unroll
             for (int b = 0; b <= (D == 2 ? MS::PF : 0); b++)
 #pragma unroll
                 for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += px[a] * py[b] * f;
         }
         if (doG) {
-            const float g = w * __expf(-fmaf(fmaf((float)cgd[2], x, (float)cgd[1]), x, (float)cgd[0]));
+            const float g = w * __expf(-fmaf(fmaf(cgd[2], x, cgd[1]), x, cgd[0]));
 #pragma unroll
             for (int b = 0; b <= (D == 2 ? MS::PG : 0); b++)
 #pragma unroll

@@ -272,8 +272,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         st.init(c, m);
         const bool has_g = m.K > 0.0;
         double lf[NF], lg[NG];
-        maxwell_start<D, NF>(c.RT, lf);
-        maxwell_start<D, NG>(c.RT, lg);
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
 #pragma unroll
         for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
 #pragma unroll
@@ -292,8 +291,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
                 scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls, -1.0);
                 my_redo++;
             } else {
-                maxwell_start<D, NF>(c.RT, lf);
-                maxwell_start<D, NG>(c.RT, lg);
+                maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
             }
         }
         solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
@@ -315,8 +313,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
                     conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
                     jj++;
                 }
-            maxwell_start<D, NF>(c.RT, lf);
-            maxwell_start<D, NG>(c.RT, lg);
+            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
             solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
             if (sf >= 0 && sg >= 0) {
                 atomicAdd(&s_feq, 1ull);
