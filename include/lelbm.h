@@ -181,6 +181,35 @@ int lelbm_reset_stats(lelbm_t h);
 /* 1: time every cell-update kernel with CUDA events on its own stream. */
 int lelbm_set_timing(lelbm_t h, int on);
 
+/* ---- 1D batches: persistent execution ----------------------------------
+ * Per-instance step budgets for lelbm_run_batch (host array [n_batch]; NULL
+ * removes every budget).  An instance whose budget is spent is frozen. */
+int lelbm_set_steps(lelbm_t h, const int* steps);
+
+/* Launch shape of the persistent batch kernel. */
+typedef struct {
+    int threads;        /* threads per block: 64 or 128                          */
+    int blocks_per_sm;  /* resident blocks per SM (0: the occupancy maximum)     */
+    int order;          /* 0: instances in batch order, 1: longest first         */
+    double ms;          /* autotune: time of the trial, else 0                   */
+} lelbm_tuning;
+
+/* Advance every 1D instance by min(n, its budget) time steps in ONE persistent
+ * kernel launch, replayed from a CUDA graph captured on the first call with
+ * this n.  A block claims a whole instance and runs its steps with block-level
+ * barriers (instances share no cells); results equal n calls of lelbm_step
+ * when no budget is set.  1D handles only (E_INVAL otherwise); asynchronous. */
+int lelbm_run_batch(lelbm_t h, int n);
+
+/* Time every candidate launch shape (threads 64/128, 1, 2 or the maximum of
+ * blocks per SM, batch or longest-first order) for trial_steps steps on the
+ * current state, restore the state and budgets after each trial, keep the
+ * fastest for lelbm_run_batch and return it in *best (may be NULL).  Syncs. */
+int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best);
+
+/* Set the launch shape of lelbm_run_batch explicitly. */
+int lelbm_set_tuning(lelbm_t h, const lelbm_tuning* t);
+
 /* Message of the last failure of h ("" if none; h may be NULL for create). */
 const char* lelbm_last_error(lelbm_t h);
 

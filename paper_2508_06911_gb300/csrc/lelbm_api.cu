@@ -37,6 +37,17 @@ struct lelbm {
     long long npad = 0;
     DevStats* d_stats = nullptr;
     unsigned long long* d_work = nullptr;  // work counter of the cell-update kernel
+    // persistent 1D batch
+    int* d_order[2] = {nullptr, nullptr};  // batch order, longest first
+    long long* d_inst_first = nullptr;     // first cell of each instance block (pads included)
+    int* d_inst_pad = nullptr;
+    int* d_steps_left = nullptr;
+    bool budgets = false;
+    lelbm_tuning tuning{128, 0, 0, 0.0};
+    cudaGraphExec_t graph = nullptr;  // captured lelbm_run_batch launch
+    int graph_n = -1, graph_cur = -1;
+    bool graph_budgets = false;
+    lelbm_tuning graph_tuning{0, 0, 0, 0.0};
     long long steps = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -156,6 +167,12 @@ static void free_all(lelbm* h) {
     cudaFree(h->d_pad_src);
     cudaFree(h->d_stats);
     cudaFree(h->d_work);
+    cudaFree(h->d_order[0]);
+    cudaFree(h->d_order[1]);
+    cudaFree(h->d_inst_first);
+    cudaFree(h->d_inst_pad);
+    cudaFree(h->d_steps_left);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -264,6 +281,20 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         rc = upload(h, &h->d_inst, inst);
         if (!rc) rc = upload(h, &h->d_inst_lo, h->inst_lo_h);
         if (!rc) rc = upload(h, &h->d_inst_n, h->inst_n_h);
+        std::vector<long long> firsts;
+        std::vector<int> pads_v, ord0(nb), ord1(nb);
+        for (int b = 0; b < nb; b++) {
+            const int pb = g.periodic[0] ? 0 : ((p->n_batch > 1 && p->pads) ? p->pads[b] : p->pad);
+            pads_v.push_back(pb);
+            firsts.push_back(h->inst_lo_h[b] - pb);
+            ord0[b] = ord1[b] = b;
+        }
+        std::stable_sort(ord1.begin(), ord1.end(),
+                         [&](int x, int y) { return h->inst_n_h[x] > h->inst_n_h[y]; });
+        if (!rc) rc = upload(h, &h->d_inst_first, firsts);
+        if (!rc) rc = upload(h, &h->d_inst_pad, pads_v);
+        if (!rc) rc = upload(h, &h->d_order[0], ord0);
+        if (!rc) rc = upload(h, &h->d_order[1], ord1);
         if (rc) {
             std::string e = h->err;
             free_all(h);
@@ -560,6 +591,152 @@ extern "C" int lelbm_reset_stats(lelbm_t h) {
 extern "C" int lelbm_set_timing(lelbm_t h, int on) {
     if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
     h->timing = on != 0;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_set_steps(lelbm_t h, const int* steps) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (h->D != 1) return fail(h, LELBM_E_INVAL, "step budgets are for 1D batches");
+    const int nb = (int)h->inst_n_h.size();
+    if (!steps) {
+        h->budgets = false;
+        return LELBM_OK;
+    }
+    for (int b = 0; b < nb; b++)
+        if (steps[b] < 0) return fail(h, LELBM_E_INVAL, "steps[%d] < 0", b);
+    if (!h->d_steps_left) CUDA_TRY(h, cudaMalloc((void**)&h->d_steps_left, sizeof(int) * nb));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_steps_left, steps, sizeof(int) * nb, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->budgets = true;
+    return LELBM_OK;
+}
+
+static int tuned_blocks(lelbm* h, const lelbm_tuning& t) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int mx = batch_persistent_max_blocks_per_sm(h->p.precision == LELBM_MIXED, t.threads);
+    const int per = (t.blocks_per_sm <= 0 || t.blocks_per_sm > mx) ? mx : t.blocks_per_sm;
+    return sms * per;
+}
+
+// Enqueue one persistent launch (work-counter reset + kernel) on the handle's stream.
+static int enqueue_batch(lelbm* h, int n, const lelbm_tuning& t) {
+    CUDA_TRY(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
+    launch_batch_persistent(h->model, h->geo, h->p.inlet, h->p.bc[0] == LELBM_BC_INFLOW,
+                            h->p.bc[1] == LELBM_BC_INFLOW, h->d_type, h->M[h->cur], h->M[1 - h->cur], h->d_stats,
+                            h->d_work, h->d_order[t.order ? 1 : 0], h->d_inst_first, h->d_inst_pad,
+                            h->budgets ? h->d_steps_left : nullptr, n, tuned_blocks(h, t), t.threads,
+                            h->p.precision == LELBM_MIXED, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_run_batch(lelbm_t h, int n) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (h->D != 1) return fail(h, LELBM_E_INVAL, "lelbm_run_batch needs a 1D handle");
+    if (n < 0) return fail(h, LELBM_E_INVAL, "n must be >= 0");
+    if (n == 0) return LELBM_OK;
+    const lelbm_tuning& t = h->tuning;
+    // the graph holds the buffer pointers, the launch shape, n and the budget pointer
+    const bool same = h->graph && h->graph_n == n && h->graph_cur == h->cur && h->graph_budgets == h->budgets &&
+                      h->graph_tuning.threads == t.threads && h->graph_tuning.blocks_per_sm == t.blocks_per_sm &&
+                      h->graph_tuning.order == t.order;
+    if (!same) {
+        if (h->graph) cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        cudaGraph_t gr = nullptr;
+        CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_batch(h, n, t);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &gr);
+        if (rc) return rc;
+        if (e != cudaSuccess) return fail(h, LELBM_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return fail(h, LELBM_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        h->graph_n = n;
+        h->graph_cur = h->cur;
+        h->graph_budgets = h->budgets;
+        h->graph_tuning = t;
+    }
+    std::pair<cudaEvent_t, cudaEvent_t> ev{};
+    if (h->timing) {
+        int rc = take_events(h, &ev);
+        if (rc) return rc;
+        CUDA_TRY(h, cudaEventRecord(ev.first, h->stream));
+    }
+    CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+    if (h->timing) {
+        CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
+        h->ev_used.push_back(ev);
+    }
+    h->steps += n;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_set_tuning(lelbm_t h, const lelbm_tuning* t) {
+    if (!h || !t) return fail(h, LELBM_E_INVAL, "NULL argument");
+    if ((t->threads != 64 && t->threads != 128) || t->blocks_per_sm < 0 || (t->order != 0 && t->order != 1))
+        return fail(h, LELBM_E_INVAL, "bad tuning");
+    h->tuning = *t;
+    h->tuning.ms = 0.0;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (h->D != 1) return fail(h, LELBM_E_INVAL, "lelbm_autotune needs a 1D handle");
+    if (trial_steps < 1) return fail(h, LELBM_E_INVAL, "trial_steps must be >= 1");
+    const size_t bytes = sizeof(double) * (size_t)h->nmom * (size_t)h->ncell;
+    const int nb = (int)h->inst_n_h.size();
+    double* save = nullptr;
+    int* save_steps = nullptr;
+    CUDA_TRY(h, cudaMalloc((void**)&save, bytes));
+    if (h->budgets && cudaMalloc((void**)&save_steps, sizeof(int) * nb) != cudaSuccess) {
+        cudaFree(save);
+        return fail(h, LELBM_E_NOMEM, "autotune backup");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int mx128 = batch_persistent_max_blocks_per_sm(h->p.precision == LELBM_MIXED, 128);
+    std::vector<lelbm_tuning> cand;
+    for (int threads : {64, 128})
+        for (int per : {1, 2, 0})
+            for (int order : {0, 1}) {
+                if (threads == 128 && per == 2 && mx128 < 2) continue;
+                cand.push_back({threads, per, order, 0.0});
+            }
+    lelbm_tuning win{128, 0, 0, 1e300};
+    int rc = LELBM_OK;
+    cudaMemcpyAsync(save, h->M[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (save_steps) cudaMemcpyAsync(save_steps, h->d_steps_left, sizeof(int) * nb, cudaMemcpyDeviceToDevice, h->stream);
+    for (auto& t : cand) {
+        cudaEventRecord(e0, h->stream);
+        rc = enqueue_batch(h, trial_steps, t);
+        if (rc) break;
+        cudaEventRecord(e1, h->stream);
+        cudaMemcpyAsync(h->M[h->cur], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (save_steps)
+            cudaMemcpyAsync(h->d_steps_left, save_steps, sizeof(int) * nb, cudaMemcpyDeviceToDevice, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(h, LELBM_E_CUDA, "autotune trial failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t.ms = ms;
+        if (ms < win.ms) win = t;
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save);
+    cudaFree(save_steps);
+    if (rc) return rc;
+    h->tuning = win;
+    int r2 = reset_stats_dev(h);
+    if (r2) return r2;
+    if (best) *best = win;
     return LELBM_OK;
 }
 

@@ -67,5 +67,11 @@ void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, co
 void launch_macros(int D, double K, const uint8_t* type, const double* M, double* rho, double* u,
                    double* RT, long long ncell, cudaStream_t s);
 int cell_update_blocks(int D, bool mixed, int device);
+void launch_batch_persistent(const Model& m, const Geometry& g, const double inlet[4], int bc_left_inflow,
+                             int bc_right_inflow, const uint8_t* type, double* A, double* B, DevStats* st,
+                             unsigned long long* work, const int* order, const long long* inst_first,
+                             const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, bool mixed,
+                             cudaStream_t s);
+int batch_persistent_max_blocks_per_sm(bool mixed, int threads);
 
 }  // namespace lbm

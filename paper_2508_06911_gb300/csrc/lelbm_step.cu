@@ -227,143 +227,282 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
     return true;
 }
 
+// Per-block counters in shared memory, flushed to DevStats once per block.
+struct BlockCounters {
+    unsigned long long hist[64];
+    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo;
+};
+
+// Per-thread tallies.
+struct ThreadCounters {
+    unsigned long long cells, pf, pg, p32, redo;
+    LocalStats ls;
+};
+
+__device__ __forceinline__ void counters_init(BlockCounters& bc) {
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
+    if (threadIdx.x == 0) bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = 0;
+}
+
+// Adds the thread tallies to the block counters, then (after a barrier) the block
+// counters to the device counters.  Every thread of the block must call it.
+__device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCounters& tc, DevStats* stats) {
+    atomicAdd(&bc.cells, tc.cells);
+    atomicAdd(&bc.p32, tc.p32);
+    atomicAdd(&bc.redo, tc.redo);
+    atomicAdd(&bc.pf, tc.pf);
+    atomicAdd(&bc.pg, tc.pg);
+    atomicAdd(&bc.pm, tc.ls.points);
+    atomicMax(&bc.q, tc.ls.q_max);
+    atomicMax(&bc.dmax, (unsigned long long)__double_as_longlong(sqrt(tc.ls.disp_max2)));
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        if (bc.hist[i]) atomicAdd(&stats->newton_hist[i], bc.hist[i]);
+    if (threadIdx.x == 0) {
+        atomicAdd(&stats->cells, bc.cells);
+        atomicAdd(&stats->points_f, bc.pf);
+        atomicAdd(&stats->points_g, bc.pg);
+        atomicAdd(&stats->points_ms, bc.pm);
+        atomicAdd(&stats->points_32, bc.p32);
+        if (bc.redo) atomicAdd(&stats->judge_redo, bc.redo);
+        if (bc.feq) atomicAdd(&stats->fallback_eq, bc.feq);
+        if (bc.fmx) atomicAdd(&stats->fallback_mx, bc.fmx);
+        atomicMax(&stats->q_max, bc.q);
+        atomicMax(&stats->disp_max_bits, bc.dmax);
+    }
+}
+
+// The whole single-cell operation of Fig. 5 for one (non-solid) cell: collision,
+// LAS, EPR (with the fallbacks) and moment streaming into Mout.
+template <int D, bool MIXED>
+__device__ __forceinline__ void process_cell(const Model& m, const Geometry& g, const uint8_t* type,
+                                             const double* __restrict__ Min, double* Mout, DevStats* stats,
+                                             long long cell, BlockCounters& bc, ThreadCounters& tc, double* conF,
+                                             double* conG) {
+    constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
+    double M[NM];
+#pragma unroll
+    for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
+    CellState<D> c;
+    collide<D>(M, m, c);
+    if (!c.ok) {  // non-physical cell: nothing can be reconstructed
+        atomicAdd(&bc.fmx, 1ull);
+        atomicMin(&stats->first_fail, (unsigned long long)cell);
+        return;
+    }
+    tc.cells++;
+    Stencil<D> st;
+    st.init(c, m);
+    const bool has_g = m.K > 0.0;
+    double lf[NF], lg[NG];
+    maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+#pragma unroll
+    for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
+#pragma unroll
+    for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
+    int sf, sg;
+    if constexpr (MIXED) {
+        if (solve_fg_mixed<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
+            // stream and judge in one FP64 pass; on a miss, take the deposit back and
+            // finish the solve in FP64 from the current multipliers
+            if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
+                atomicAdd(&bc.hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
+                return;
+            }
+            scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
+            tc.redo++;
+        } else {
+            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        }
+    }
+    solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+    if (sf >= 0 && sg >= 0) {
+        atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
+        if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+    } else {
+        // equilibrium constraints (omega = 1) for both populations
+#pragma unroll
+        for (int j = 0; j < NF; j++) conF[j] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NG; j++) conG[j] = 0.0;
+        conF[0] = conG[0] = 1.0;
+        int jj = 1 + D;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++) {
+                conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
+                jj++;
+            }
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+        if (sf >= 0 && sg >= 0) {
+            atomicAdd(&bc.feq, 1ull);
+        } else {
+            // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S (mass exact)
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf[j] = 0.0;
+            lf[0] = -1.0;
+            jj = 1 + D;
+#pragma unroll
+            for (int a = 0; a < D; a++)
+#pragma unroll
+                for (int b = a; b < D; b++) {
+                    lf[jj] = (a == b) ? 0.5 : 0.0;
+                    jj++;
+                }
+            double MF[MomentSet<D>::NF], MG[MomentSet<D>::NG];
+            moment_pass<D>(c, st, lf, lg, true, false, MF, MG);
+            lf[0] = log(MF[0]) - 1.0;
+#pragma unroll
+            for (int j = 0; j < NG; j++) lg[j] = lf[j];
+            atomicAdd(&bc.fmx, 1ull);
+            atomicMin(&stats->first_fail, (unsigned long long)cell);
+        }
+    }
+    scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls);
+}
+
+// One time step of the whole padded grid: warps claim chunks of 32 consecutive cells
+// from a global counter (the cost of a cell varies with its temperature, q ~
+// (n sqrt RT)^D, so a static split leaves SMs idle at the end).
 template <int D, bool MIXED>
 __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
                                                           DevStats* stats, unsigned long long* work) {
-    constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
-    __shared__ unsigned long long s_hist[64];
-    __shared__ unsigned long long s_cells, s_feq, s_fmx, s_q;
-    __shared__ unsigned long long s_dmax, s_pf, s_pg, s_pm, s_p32, s_redo;
-    // post-collision constraints of each thread's cell (kept out of registers)
-    __shared__ double s_con[128][NF + NG];
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    __shared__ BlockCounters bc;
+    __shared__ double s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) s_hist[i] = 0;
-    if (threadIdx.x == 0) s_cells = s_feq = s_fmx = s_q = s_dmax = s_pf = s_pg = s_pm = s_p32 = s_redo = 0;
+    counters_init(bc);
     __syncthreads();
-
-    LocalStats ls{0, 0.0, 0};
-    unsigned long long my_cells = 0, my_pf = 0, my_pg = 0, my_p32 = 0, my_redo = 0;
+    ThreadCounters tc{0, 0, 0, 0, 0, {0, 0.0, 0}};
     const int lane = threadIdx.x & 31;
-    // Warps claim chunks of 32 consecutive cells: the cost of a cell varies with its
-    // temperature (q ~ (n sqrt RT)^D), so a static split leaves SMs idle at the end.
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(work, 32ull);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= (unsigned long long)g.ncell) break;
         const long long cell = (long long)base + lane;
-        if (cell >= g.ncell) continue;
-        const uint8_t ty = type[cell];
-        if (ty == CELL_SOLID) continue;
-        double M[NM];
-#pragma unroll
-        for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
-        CellState<D> c;
-        collide<D>(M, m, c);
-        if (!c.ok) {  // non-physical cell: nothing can be reconstructed
-            atomicAdd(&s_fmx, 1ull);
-            atomicMin(&stats->first_fail, (unsigned long long)cell);
-            continue;
-        }
-        my_cells++;
-        Stencil<D> st;
-        st.init(c, m);
-        const bool has_g = m.K > 0.0;
-        double lf[NF], lg[NG];
-        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-#pragma unroll
-        for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
-#pragma unroll
-        for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
-        int sf, sg;
-        bool mixed_ok = false;
-        if constexpr (MIXED) {
-            mixed_ok = solve_fg_mixed<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg, my_p32);
-            if (mixed_ok) {
-                // stream and judge in one FP64 pass; on a miss, take the deposit back and
-                // finish the solve in FP64 from the current multipliers
-                if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, ls, 1.0, conF, conG)) {
-                    atomicAdd(&s_hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
-                    continue;
-                }
-                scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls, -1.0);
-                my_redo++;
-            } else {
-                maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-            }
-        }
-        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
-        if (sf >= 0 && sg >= 0) {
-            atomicAdd(&s_hist[sf < 63 ? sf : 63], 1ull);
-            if (has_g) atomicAdd(&s_hist[sg < 63 ? sg : 63], 1ull);
-        } else {
-            // equilibrium constraints (omega = 1) for both populations
-#pragma unroll
-            for (int j = 0; j < NF; j++) conF[j] = 0.0;
-#pragma unroll
-            for (int j = 0; j < NG; j++) conG[j] = 0.0;
-            conF[0] = conG[0] = 1.0;
-            int jj = 1 + D;
-#pragma unroll
-            for (int a = 0; a < D; a++)
-#pragma unroll
-                for (int b = a; b < D; b++) {
-                    conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
-                    jj++;
-                }
-            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-            solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, my_pf, my_pg);
-            if (sf >= 0 && sg >= 0) {
-                atomicAdd(&s_feq, 1ull);
-            } else {
-                // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S (mass exact)
-#pragma unroll
-                for (int j = 0; j < NF; j++) lf[j] = 0.0;
-                lf[0] = -1.0;
-                jj = 1 + D;
-#pragma unroll
-                for (int a = 0; a < D; a++)
-#pragma unroll
-                    for (int b = a; b < D; b++) {
-                        lf[jj] = (a == b) ? 0.5 : 0.0;
-                        jj++;
-                    }
-                double MF[MomentSet<D>::NF], MG[MomentSet<D>::NG];
-                moment_pass<D>(c, st, lf, lg, true, false, MF, MG);
-                lf[0] = log(MF[0]) - 1.0;
-#pragma unroll
-                for (int j = 0; j < NG; j++) lg[j] = lf[j];
-                atomicAdd(&s_fmx, 1ull);
-                atomicMin(&stats->first_fail, (unsigned long long)cell);
-            }
-        }
-        scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls);
+        if (cell >= g.ncell || type[cell] == CELL_SOLID) continue;
+        process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG);
     }
-    atomicAdd(&s_cells, my_cells);
-    atomicAdd(&s_p32, my_p32);
-    atomicAdd(&s_redo, my_redo);
-    atomicAdd(&s_pf, my_pf);
-    atomicAdd(&s_pg, my_pg);
-    atomicAdd(&s_pm, ls.points);
-    atomicMax(&s_q, ls.q_max);
-    atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(sqrt(ls.disp_max2)));
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64; i += blockDim.x)
-        if (s_hist[i]) atomicAdd(&stats->newton_hist[i], s_hist[i]);
-    if (threadIdx.x == 0) {
-        atomicAdd(&stats->cells, s_cells);
-        atomicAdd(&stats->points_f, s_pf);
-        atomicAdd(&stats->points_g, s_pg);
-        atomicAdd(&stats->points_ms, s_pm);
-        atomicAdd(&stats->points_32, s_p32);
-        if (s_redo) atomicAdd(&stats->judge_redo, s_redo);
-        if (s_feq) atomicAdd(&stats->fallback_eq, s_feq);
-        if (s_fmx) atomicAdd(&stats->fallback_mx, s_fmx);
-        atomicMax(&stats->q_max, s_q);
-        atomicMax(&stats->disp_max_bits, s_dmax);
+    counters_flush(bc, tc, stats);
+}
+
+// Persistent 1D batch: a block claims a whole instance from the queue (order[]) and
+// runs all of its steps with block barriers only -- instances share no cells, so no
+// grid-wide barrier is needed.  Each step fills the instance's pads (Sec. III.A),
+// zeroes its block of the next buffer, then lets its warps claim 32-cell chunks from
+// a shared counter.  An instance that ends on an odd step copies its block back, so
+// every instance finishes in buffer A.  steps_left[] (may be null: unlimited) caps
+// each instance and is decremented.
+template <bool MIXED>
+__global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry g, double in0, double in1,
+                                                               double in3, int bc_left_inflow, int bc_right_inflow,
+                                                               const uint8_t* __restrict__ type, double* A, double* B,
+                                                               DevStats* stats, unsigned long long* work,
+                                                               const int* order, const long long* inst_first,
+                                                               const int* inst_pad, int* steps_left, int nsteps) {
+    constexpr int D = 1, NM = Dim<1>::NM, NF = Dim<1>::NF, NG = Dim<1>::NG;
+    __shared__ BlockCounters bc;
+    __shared__ double s_con[128][NF + NG];
+    __shared__ unsigned int s_next;
+    __shared__ int s_inst;
+    double* conF = s_con[threadIdx.x];
+    double* conG = conF + NF;
+    counters_init(bc);
+    ThreadCounters tc{0, 0, 0, 0, 0, {0, 0.0, 0}};
+    const int lane = threadIdx.x & 31;
+    double Meq[NM];
+    {
+        const double uin[1] = {in1};
+        eq_moments<1>(m.K, in0, uin, in3, Meq);
     }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned long long k = atomicAdd(work, 1ull);
+            s_inst = k < (unsigned long long)g.n_inst ? order[k] : -1;
+        }
+        __syncthreads();
+        const int b = s_inst;
+        if (b < 0) break;
+        const int n = g.inst_n[b];
+        const int pad = inst_pad[b];
+        const long long lo = g.inst_lo[b];
+        const long long first = inst_first[b];
+        const int nblk = n + 2 * pad;
+        int k = nsteps;
+        if (steps_left) k = min(k, steps_left[b]);
+        for (int s = 0; s < k; s++) {
+            const double* Min = (s & 1) ? B : A;
+            double* Mout = (s & 1) ? A : B;
+            // pads, then a zeroed output block
+            for (int i = threadIdx.x; i < 2 * pad; i += blockDim.x) {
+                const bool left = i < pad;
+                const long long cell = left ? first + i : lo + n + (i - pad);
+                double* Mw = const_cast<double*>(Min);
+                if (left ? bc_left_inflow : bc_right_inflow) {
+#pragma unroll
+                    for (int q = 0; q < NM; q++) Mw[q * g.ncell + cell] = Meq[q];
+                } else {
+                    const long long src = left ? lo : lo + n - 1;
+#pragma unroll
+                    for (int q = 0; q < NM; q++) Mw[q * g.ncell + cell] = Min[q * g.ncell + src];
+                }
+            }
+            for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+#pragma unroll
+                for (int q = 0; q < NM; q++) Mout[q * g.ncell + first + i] = 0.0;
+            if (threadIdx.x == 0) s_next = 0;
+            __syncthreads();
+            for (;;) {
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(&s_next, 32u);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= (unsigned int)nblk) break;
+                const int i = (int)base + lane;
+                if (i >= nblk) continue;
+                const long long cell = first + i;
+                if (type[cell] == CELL_SOLID) continue;
+                process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG);
+            }
+            __syncthreads();
+        }
+        if (k & 1) {  // the result is in B: copy the block back to A
+            for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+#pragma unroll
+                for (int q = 0; q < NM; q++) A[q * g.ncell + first + i] = B[q * g.ncell + first + i];
+        }
+        if (steps_left && threadIdx.x == 0) steps_left[b] -= k;
+    }
+    counters_flush(bc, tc, stats);
+}
+
+void launch_batch_persistent(const Model& m, const Geometry& g, const double inlet[4], int bc_left_inflow,
+                             int bc_right_inflow, const uint8_t* type, double* A, double* B, DevStats* st,
+                             unsigned long long* work, const int* order, const long long* inst_first,
+                             const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, bool mixed,
+                             cudaStream_t s) {
+    if (mixed)
+        batch_persistent_kernel<true><<<blocks, threads, 0, s>>>(m, g, inlet[0], inlet[1], inlet[3], bc_left_inflow,
+                                                                 bc_right_inflow, type, A, B, st, work, order,
+                                                                 inst_first, inst_pad, steps_left, nsteps);
+    else
+        batch_persistent_kernel<false><<<blocks, threads, 0, s>>>(m, g, inlet[0], inlet[1], inlet[3], bc_left_inflow,
+                                                                  bc_right_inflow, type, A, B, st, work, order,
+                                                                  inst_first, inst_pad, steps_left, nsteps);
+}
+
+int batch_persistent_max_blocks_per_sm(bool mixed, int threads) {
+    int per_sm = 0;
+    if (mixed)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<true>, threads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<false>, threads, 0);
+    return per_sm < 1 ? 1 : per_sm;
 }
 
 // ---------------------------------------------------------------------------

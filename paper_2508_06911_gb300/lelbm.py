@@ -50,6 +50,11 @@ class lelbm_params(ctypes.Structure):
     ]
 
 
+class lelbm_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("order", ctypes.c_int),
+                ("ms", ctypes.c_double)]
+
+
 class lelbm_stats(ctypes.Structure):
     _fields_ = [
         ("steps", ctypes.c_longlong),
@@ -75,7 +80,7 @@ EXPORTS = [
     "lelbm_set_state", "lelbm_set_moments", "lelbm_set_moments_device", "lelbm_step",
     "lelbm_synchronize", "lelbm_get_moments", "lelbm_get_moments_device", "lelbm_get_macros",
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
-    "lelbm_step_noalloc",
+    "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -124,6 +129,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
         L.lelbm_last_error.argtypes = [_H]
         L.lelbm_last_error.restype = ctypes.c_char_p
+        L.lelbm_set_steps.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
+        L.lelbm_run_batch.argtypes = [_H, ctypes.c_int]
+        L.lelbm_autotune.argtypes = [_H, ctypes.c_int, ctypes.POINTER(lelbm_tuning)]
+        L.lelbm_set_tuning.argtypes = [_H, ctypes.POINTER(lelbm_tuning)]
         L.lelbm_step_noalloc.argtypes = [ctypes.POINTER(lelbm_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.POINTER(lelbm_stats)]
         _lib = L
@@ -242,6 +251,30 @@ def lelbm_reset_stats(h) -> None:
 
 def lelbm_set_timing(h, on: bool) -> None:
     _check(load().lelbm_set_timing(h, int(on)), h)
+
+
+def lelbm_set_steps(h, steps) -> None:
+    """Per-instance step budgets of a 1D batch (None removes them)."""
+    if steps is None:
+        _check(load().lelbm_set_steps(h, ctypes.POINTER(ctypes.c_int)()), h)
+        return
+    arr = np.ascontiguousarray(steps, dtype=np.int32)
+    _check(load().lelbm_set_steps(h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), h)
+
+
+def lelbm_run_batch(h, n: int) -> None:
+    _check(load().lelbm_run_batch(h, n), h)
+
+
+def lelbm_autotune(h, trial_steps: int = 1) -> lelbm_tuning:
+    t = lelbm_tuning()
+    _check(load().lelbm_autotune(h, trial_steps, ctypes.byref(t)), h)
+    return t
+
+
+def lelbm_set_tuning(h, threads: int = 128, blocks_per_sm: int = 0, order: int = 0) -> None:
+    t = lelbm_tuning(threads, blocks_per_sm, order, 0.0)
+    _check(load().lelbm_set_tuning(h, ctypes.byref(t)), h)
 
 
 def lelbm_last_error(h) -> str:

@@ -64,6 +64,16 @@ class Solver:
     def step(self, n: int = 1) -> None:
         L.lelbm_step(self.h, n)
 
+    def run_batch(self, n: int) -> None:
+        """n steps of every 1D instance in one persistent launch (CUDA graph)."""
+        L.lelbm_run_batch(self.h, n)
+
+    def set_steps(self, steps) -> None:
+        L.lelbm_set_steps(self.h, steps)
+
+    def autotune(self, trial_steps: int = 1):
+        return L.lelbm_autotune(self.h, trial_steps)
+
     def synchronize(self) -> int:
         return L.lelbm_synchronize(self.h)
 
