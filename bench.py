@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
+    ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell"],
+                    help="EPR Newton start of the timed path: the trained MLP or Eq. (IID13)")
     ap.add_argument("--per-step", action="store_true", help="1D batch: one launch per step instead of the "
                     "persistent batch kernel")
     ap.add_argument("--no-e2e", action="store_true")
@@ -240,9 +242,26 @@ def run_ours(args):
     interior = desc["interior_cells"]
     prec = {"mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
 
-    def make(precision):
+    weights = None
+    wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", f"warmstart_{D}d.npy")
+    if args.warmstart == "learned":
+        if os.path.exists(wpath):
+            weights = np.load(wpath)
+        else:  # no trained network shipped: train one on pairs recorded by the plain solver
+            from paper_2508_06911_gb300 import warmstart as WS
+            from paper_2508_06911_gb300 import workloads as W
+            src = (Solver.riemann1d(W.riemann_1d_batch(n_batch=1024, seed_index=11)) if D == 1
+                   else Solver.grid2d(W.riemann_2d(n=512, seed_index=12)))
+            X, Y = WS.record_pairs(src, steps=2)
+            weights, _ = WS.train(D, X, Y)
+            src.close()
+
+    def make(precision, learned=True):
         kw = dict(stream=stream.cuda_stream, precision=prec[precision])
-        return Solver.riemann1d(w, **kw) if D == 1 else Solver.grid2d(w, **kw)
+        s_ = Solver.riemann1d(w, **kw) if D == 1 else Solver.grid2d(w, **kw)
+        if learned and weights is not None:
+            L.lelbm_set_mlp(s_.h, weights)
+        return s_
 
     persistent = D == 1 and not args.per_step
 
@@ -282,9 +301,10 @@ def run_ours(args):
     value = interior * args.steps * world / (ms / 1e3) / 1e6
 
     compare = None
+    ablation = None
     if not args.no_compare:
         other = "fp64" if args.precision == "mixed" else "mixed"
-        s2 = make(other)
+        s2 = make(other, learned=False)  # the plain path: Eq. (IID13) start
         ms2, st2, _, _ = timed(s2, False)
         r1 = s.get_moments()[0]
         r2 = s2.get_moments()[0]
@@ -292,8 +312,18 @@ def run_ours(args):
         compare = {"precision": other, "value": interior * args.steps * world / (ms2 / 1e3) / 1e6,
                    "ms_per_step": ms2 / args.steps,
                    "kernel_ms": st2.cell_kernel_ms / max(st2.cell_kernel_launches, 1),
-                   "l1_density_rel": l1, "note": "both runs from the same state, warmup + steps each"}
+                   "l1_density_rel": l1, "warmstart": "maxwell",
+                   "note": "both runs from the same state, warmup + steps each"}
         s2.close()
+        if weights is not None:  # what the trained network gains on the timed path
+            s3 = make(args.precision, learned=False)
+            ms3, st3, _, _ = timed(s3, False)
+            h3 = list(st3.newton_hist)
+            ablation = {"warmstart": "maxwell", "value": interior * args.steps * world / (ms3 / 1e3) / 1e6,
+                        "ms_per_step": ms3 / args.steps, "points_fp32": st3.points_32,
+                        "points_fp64_newton": st3.points_f + st3.points_g,
+                        "newton_mean_updates": sum(i * x for i, x in enumerate(h3)) / max(sum(h3), 1)}
+            s3.close()
 
     # dominant kernel: the fused cell update, FP64-ALU bound
     # one timed launch covers args.steps steps on the persistent path; work per launch
@@ -360,6 +390,9 @@ def run_ours(args):
                 "data": "synthetic (seeded)",
                 "config": desc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
                 "speedup_vs_fp64": (value / compare["value"]) if (compare and args.precision == "mixed") else None,
+                "warmstart": "learned" if weights is not None else "maxwell",
+                "ablation_no_mlp": ablation, "points_fp32": st.points_32,
+                "points_fp64_newton": st.points_f + st.points_g, "mlp_retry": st.mlp_retry,
                 "gpu_launches": 1 if persistent else int(args.steps * (2 if s.n_cells > interior else 1)),
                 "clocks": clocks, "status": L.STATUS.get(status, status),
                 "newton_mean_updates": mean_updates, "fallback_eq": st.fallback_eq,

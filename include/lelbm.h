@@ -115,6 +115,7 @@ typedef struct {
     long long points_ms;          /* stencil points streamed (moment streaming)     */
     long long points_32;          /* stencil points of FP32 Newton passes (mixed)   */
     long long judge_redo;         /* mixed: cells re-solved in FP64 after the check */
+    long long mlp_retry;          /* learned start failed; re-solved from Eq. IID13 */
 } lelbm_stats;
 
 /* Sizes of the structures this library was built with, so a binding can check
@@ -209,6 +210,46 @@ int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best);
 
 /* Set the launch shape of lelbm_run_batch explicitly. */
 int lelbm_set_tuning(lelbm_t h, const lelbm_tuning* t);
+
+/* ---- Learned warm start of the EPR Newton -----------------------------------
+ * The Newton of Sec. II.D starts from the Maxwellian multipliers of Eq. (IID13);
+ * with a network set, it starts from those plus a correction predicted by an MLP
+ * (2 x 64 hidden units, SiLU, BF16 weights, FP32 accumulation) from the cell's
+ * normalised post-collision constraints and stencil geometry.  The plain start
+ * stays the fallback (a failed learned solve is redone from Eq. IID13) and the
+ * same residual tolerance is the judge, so results do not depend on the network.
+ * Features: 8 (1D) / 15 (2D); targets: converged multipliers minus Eq. (IID13)
+ * in thermal units, fluons then phonons, 7 (1D) / 16 (2D).  Parameters: FP32
+ * vector W1 b1 W2 b2 W3 b3 followed by the input/output means and standard
+ * deviations (n_params in total, the first n_weights trained). */
+int lelbm_mlp_size(int dims, int* n_in, int* n_out, long long* n_params, long long* n_weights);
+
+/* Initial parameters into the HOST array params[n_params]: He-uniform weights
+ * (seeded) and the normalisation from n training pairs X_dev[n][n_in],
+ * Y_dev[n][n_out] on the device (n = 0: unit normalisation).  Syncs. */
+int lelbm_mlp_init(int dims, unsigned long long seed, const float* X_dev, const float* Y_dev, long long n,
+                   float* params);
+
+/* Mean-squared loss (standardised targets) and its gradient with respect to the
+ * n_weights trained parameters, at the BF16-rounded weights, over all n pairs;
+ * params_dev, X_dev, Y_dev, grad_dev are device arrays; *loss is host.  Syncs. */
+int lelbm_mlp_loss_grad(int dims, const float* params_dev, const float* X_dev, const float* Y_dev, long long n,
+                        float* grad_dev, double* loss, void* stream);
+
+/* Train params_dev in place: epochs of shuffled minibatches, Adam (lr, beta
+ * 0.9/0.999) on FP32 master weights, BF16 forward/backward with FP32
+ * accumulation.  epoch_loss (host, may be NULL) gets the mean loss of each epoch. */
+int lelbm_mlp_train(int dims, float* params_dev, const float* X_dev, const float* Y_dev, long long n, int epochs,
+                    int batch, float lr, unsigned long long seed, double* epoch_loss, void* stream);
+
+/* One time step that also writes, for every cell solved without fallback, its
+ * features to x_dev[cell][n_in] and its targets to y_dev[cell][n_out] (device
+ * arrays over the padded cells; other rows are left untouched). */
+int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev);
+
+/* Use the network params (host, n_params floats) as warm start; NULL: the plain
+ * Maxwellian start. */
+int lelbm_set_mlp(lelbm_t h, const float* params);
 
 /* Message of the last failure of h ("" if none; h may be NULL for create). */
 const char* lelbm_last_error(lelbm_t h);

@@ -9,8 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblelbm.so")
-SOURCES = ["lelbm_step.cu", "lelbm_api.cu", "lelbm_noalloc.cu"]
-HEADERS = ["lelbm_internal.h", "lelbm_device.cuh", os.path.join("..", "..", "include", "lelbm.h")]
+SOURCES = ["lelbm_step.cu", "lelbm_api.cu", "lelbm_noalloc.cu", "lelbm_mlp.cu"]
+HEADERS = ["lelbm_internal.h", "lelbm_device.cuh", "lelbm_mlp.cuh", os.path.join("..", "..", "include", "lelbm.h")]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/lelbm.h"
 #include "lelbm_internal.h"
 
@@ -44,6 +46,8 @@ struct lelbm {
     int* d_steps_left = nullptr;
     bool budgets = false;
     lelbm_tuning tuning{128, 0, 0, 0.0};
+    __nv_bfloat16* d_mlp_w = nullptr;  // learned warm start: BF16 weights
+    float* d_mlp_nrm = nullptr;        // and normalisation
     cudaGraphExec_t graph = nullptr;  // captured lelbm_run_batch launch
     int graph_n = -1, graph_cur = -1;
     bool graph_budgets = false;
@@ -173,6 +177,8 @@ static void free_all(lelbm* h) {
     cudaFree(h->d_inst_pad);
     cudaFree(h->d_steps_left);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    cudaFree(h->d_mlp_w);
+    cudaFree(h->d_mlp_nrm);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -529,6 +535,7 @@ static int read_stats(lelbm* h, lelbm_stats* s) {
         s->points_ms = (long long)d.points_ms;
         s->points_32 = (long long)d.points_32;
         s->judge_redo = (long long)d.judge_redo;
+        s->mlp_retry = (long long)d.mlp_retry;
     }
     return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
 }
@@ -737,6 +744,44 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
     int r2 = reset_stats_dev(h);
     if (r2) return r2;
     if (best) *best = win;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!x_dev || !y_dev) return fail(h, LELBM_E_INVAL, "NULL record buffer");
+    h->model.rec_x = x_dev;
+    h->model.rec_y = y_dev;
+    const int rc = lelbm_step(h, 1);
+    h->model.rec_x = nullptr;
+    h->model.rec_y = nullptr;
+    return rc;
+}
+
+extern "C" int lelbm_set_mlp(lelbm_t h, const float* params) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    int nin, nout;
+    long long ntot, nw;
+    if (lelbm_mlp_size(h->D, &nin, &nout, &ntot, &nw) != LELBM_OK) return fail(h, LELBM_E_INVAL, "bad dims");
+    if (!params) {
+        h->model.mlp_w = nullptr;
+        h->model.mlp_nrm = nullptr;
+        if (h->graph) cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        return LELBM_OK;
+    }
+    for (long long i = 0; i < ntot; i++)
+        if (!std::isfinite(params[i])) return fail(h, LELBM_E_INVAL, "non-finite MLP parameter %lld", i);
+    std::vector<__nv_bfloat16> w(nw);
+    for (long long i = 0; i < nw; i++) w[i] = __float2bfloat16(params[i]);
+    if (!h->d_mlp_w) CUDA_TRY(h, cudaMalloc((void**)&h->d_mlp_w, sizeof(__nv_bfloat16) * nw));
+    if (!h->d_mlp_nrm) CUDA_TRY(h, cudaMalloc((void**)&h->d_mlp_nrm, sizeof(float) * (ntot - nw)));
+    CUDA_TRY(h, cudaMemcpy(h->d_mlp_w, w.data(), sizeof(__nv_bfloat16) * nw, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_mlp_nrm, params + nw, sizeof(float) * (ntot - nw), cudaMemcpyHostToDevice));
+    h->model.mlp_w = h->d_mlp_w;
+    h->model.mlp_nrm = h->d_mlp_nrm;
+    if (h->graph) cudaGraphExecDestroy(h->graph);  // the captured launch holds the old model
+    h->graph = nullptr;
     return LELBM_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -24,6 +25,10 @@ struct Model {
     int max_refine;     // cap on N_r (<= 4)
     double tol;         // EPR tolerance, thermal units
     int max_iter;       // Newton update cap
+    float* rec_x;                  // record mode: per-cell features, or null
+    float* rec_y;                  // record mode: per-cell targets, or null
+    const __nv_bfloat16* mlp_w;    // learned warm start: BF16 weights, or null
+    const float* mlp_nrm;          // learned warm start: normalisation
 };
 
 // Padded-grid geometry.  2D: one instance, cell = iy * NX + ix.
@@ -54,6 +59,7 @@ struct DevStats {
     unsigned long long points_ms;      // stencil points streamed
     unsigned long long points_32;      // stencil points of FP32 Newton passes (mixed path)
     unsigned long long judge_redo;     // mixed path: cells whose FP64 check failed and were re-solved
+    unsigned long long mlp_retry;      // cells whose learned start failed and were re-solved from Eq. IID13
 };
 
 void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, long long ncell,

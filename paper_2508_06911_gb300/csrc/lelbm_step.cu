@@ -18,6 +18,7 @@
 
 #include "lelbm_device.cuh"
 #include "lelbm_internal.h"
+#include "lelbm_mlp.cuh"
 
 namespace lbm {
 
@@ -230,18 +231,33 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
 // Per-block counters in shared memory, flushed to DevStats once per block.
 struct BlockCounters {
     unsigned long long hist[64];
-    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo;
+    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry;
 };
 
 // Per-thread tallies.
 struct ThreadCounters {
-    unsigned long long cells, pf, pg, p32, redo;
+    unsigned long long cells, pf, pg, p32, redo, retry;
     LocalStats ls;
 };
 
+// BF16 weights and FP32 normalisation of the warm-start MLP in shared memory.
+template <int D>
+struct MlpShared {
+    __nv_bfloat16 w[MlpLayout<D>::NW];
+    float nrm[2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT)];
+};
+
+template <int D>
+__device__ __forceinline__ void mlp_stage(const Model& m, MlpShared<D>& sm) {
+    if (!m.mlp_w) return;
+    for (int i = threadIdx.x; i < MlpLayout<D>::NW; i += blockDim.x) sm.w[i] = m.mlp_w[i];
+    for (int i = threadIdx.x; i < 2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT); i += blockDim.x) sm.nrm[i] = m.mlp_nrm[i];
+}
+
 __device__ __forceinline__ void counters_init(BlockCounters& bc) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
-    if (threadIdx.x == 0) bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = 0;
+    if (threadIdx.x == 0)
+        bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = bc.retry = 0;
 }
 
 // Adds the thread tallies to the block counters, then (after a barrier) the block
@@ -250,6 +266,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
     atomicAdd(&bc.cells, tc.cells);
     atomicAdd(&bc.p32, tc.p32);
     atomicAdd(&bc.redo, tc.redo);
+    atomicAdd(&bc.retry, tc.retry);
     atomicAdd(&bc.pf, tc.pf);
     atomicAdd(&bc.pg, tc.pg);
     atomicAdd(&bc.pm, tc.ls.points);
@@ -265,6 +282,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
         atomicAdd(&stats->points_ms, bc.pm);
         atomicAdd(&stats->points_32, bc.p32);
         if (bc.redo) atomicAdd(&stats->judge_redo, bc.redo);
+        if (bc.retry) atomicAdd(&stats->mlp_retry, bc.retry);
         if (bc.feq) atomicAdd(&stats->fallback_eq, bc.feq);
         if (bc.fmx) atomicAdd(&stats->fallback_mx, bc.fmx);
         atomicMax(&stats->q_max, bc.q);
@@ -278,7 +296,7 @@ template <int D, bool MIXED>
 __device__ __forceinline__ void process_cell(const Model& m, const Geometry& g, const uint8_t* type,
                                              const double* __restrict__ Min, double* Mout, DevStats* stats,
                                              long long cell, BlockCounters& bc, ThreadCounters& tc, double* conF,
-                                             double* conG) {
+                                             double* conG, const MlpShared<D>* mlp) {
     constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
     double M[NM];
 #pragma unroll
@@ -296,6 +314,24 @@ __device__ __forceinline__ void process_cell(const Model& m, const Geometry& g, 
     const bool has_g = m.K > 0.0;
     double lf[NF], lg[NG];
     maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+    bool learned = false;
+    if (mlp) {  // learned correction of the Maxwellian start
+        float xin[MlpDims<D>::NIN], yout[MlpDims<D>::NOUT];
+        mlp_features<D>(c, st, xin);
+        mlp_forward<D>(mlp->w, mlp->nrm, xin, yout);
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < MlpDims<D>::NOUT; k++) ok = ok && isfinite(yout[k]);
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf[j] += (double)yout[j];
+            if (has_g) {
+#pragma unroll
+                for (int j = 0; j < NG; j++) lg[j] += (double)yout[NF + j];
+            }
+            learned = true;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
 #pragma unroll
@@ -312,13 +348,32 @@ __device__ __forceinline__ void process_cell(const Model& m, const Geometry& g, 
             scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
             tc.redo++;
         } else {
+            if (learned) tc.retry++;
             maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+            learned = false;
         }
     }
     solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+    if ((sf < 0 || sg < 0) && learned) {  // the plain EPR is the fallback of the learned start
+        tc.retry++;
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+    }
     if (sf >= 0 && sg >= 0) {
         atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
         if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+        if (m.rec_x) {  // training pairs: features and converged multipliers minus Eq. (IID13)
+            float xin[MlpDims<D>::NIN];
+            mlp_features<D>(c, st, xin);
+            double mf[NF], mg[NG];
+            maxwell_start_fg<D, NF, NG>(c.RT, mf, mg);
+#pragma unroll
+            for (int k = 0; k < MlpDims<D>::NIN; k++) m.rec_x[cell * MlpDims<D>::NIN + k] = xin[k];
+#pragma unroll
+            for (int j = 0; j < NF; j++) m.rec_y[cell * MlpDims<D>::NOUT + j] = (float)(lf[j] - mf[j]);
+#pragma unroll
+            for (int j = 0; j < NG; j++) m.rec_y[cell * MlpDims<D>::NOUT + NF + j] = has_g ? (float)(lg[j] - mg[j]) : 0.f;
+        }
     } else {
         // equilibrium constraints (omega = 1) for both populations
 #pragma unroll
@@ -373,11 +428,14 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ BlockCounters bc;
     __shared__ double s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
+    __shared__ MlpShared<D> s_mlp;
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
     counters_init(bc);
+    mlp_stage<D>(m, s_mlp);
     __syncthreads();
-    ThreadCounters tc{0, 0, 0, 0, 0, {0, 0.0, 0}};
+    const MlpShared<D>* mlp = m.mlp_w ? &s_mlp : nullptr;
+    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0}};
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -386,7 +444,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         if (base >= (unsigned long long)g.ncell) break;
         const long long cell = (long long)base + lane;
         if (cell >= g.ncell || type[cell] == CELL_SOLID) continue;
-        process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG);
+        process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, mlp);
     }
     counters_flush(bc, tc, stats);
 }
@@ -410,10 +468,13 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
     __shared__ double s_con[128][NF + NG];
     __shared__ unsigned int s_next;
     __shared__ int s_inst;
+    __shared__ MlpShared<1> s_mlp;
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
     counters_init(bc);
-    ThreadCounters tc{0, 0, 0, 0, 0, {0, 0.0, 0}};
+    mlp_stage<1>(m, s_mlp);
+    const MlpShared<1>* mlp = m.mlp_w ? &s_mlp : nullptr;
+    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0}};
     const int lane = threadIdx.x & 31;
     double Meq[NM];
     {
@@ -467,7 +528,7 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
                 if (i >= nblk) continue;
                 const long long cell = first + i;
                 if (type[cell] == CELL_SOLID) continue;
-                process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG);
+                process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, mlp);
             }
             __syncthreads();
         }

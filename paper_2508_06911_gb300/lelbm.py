@@ -72,6 +72,7 @@ class lelbm_stats(ctypes.Structure):
         ("points_ms", ctypes.c_longlong),
         ("points_32", ctypes.c_longlong),
         ("judge_redo", ctypes.c_longlong),
+        ("mlp_retry", ctypes.c_longlong),
     ]
 
 
@@ -81,6 +82,8 @@ EXPORTS = [
     "lelbm_synchronize", "lelbm_get_moments", "lelbm_get_moments_device", "lelbm_get_macros",
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
     "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
+    "lelbm_mlp_size", "lelbm_mlp_init", "lelbm_mlp_loss_grad", "lelbm_mlp_train", "lelbm_step_record",
+    "lelbm_set_mlp",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -133,6 +136,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_run_batch.argtypes = [_H, ctypes.c_int]
         L.lelbm_autotune.argtypes = [_H, ctypes.c_int, ctypes.POINTER(lelbm_tuning)]
         L.lelbm_set_tuning.argtypes = [_H, ctypes.POINTER(lelbm_tuning)]
+        L.lelbm_mlp_size.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+        L.lelbm_mlp_init.argtypes = [ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_longlong, ctypes.POINTER(ctypes.c_float)]
+        L.lelbm_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_longlong, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p]
+        L.lelbm_mlp_train.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                      ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        L.lelbm_step_record.argtypes = [_H, ctypes.c_void_p, ctypes.c_void_p]
+        L.lelbm_set_mlp.argtypes = [_H, ctypes.POINTER(ctypes.c_float)]
         L.lelbm_step_noalloc.argtypes = [ctypes.POINTER(lelbm_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.POINTER(lelbm_stats)]
         _lib = L
@@ -275,6 +290,51 @@ def lelbm_autotune(h, trial_steps: int = 1) -> lelbm_tuning:
 def lelbm_set_tuning(h, threads: int = 128, blocks_per_sm: int = 0, order: int = 0) -> None:
     t = lelbm_tuning(threads, blocks_per_sm, order, 0.0)
     _check(load().lelbm_set_tuning(h, ctypes.byref(t)), h)
+
+
+def lelbm_mlp_size(dims: int):
+    """(n_in, n_out, n_params, n_weights) of the warm-start network."""
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().lelbm_mlp_size(dims, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def lelbm_mlp_init(dims: int, seed: int, X_ptr: int, Y_ptr: int, n: int) -> np.ndarray:
+    _, _, ntot, _ = lelbm_mlp_size(dims)
+    out = np.zeros(ntot, dtype=np.float32)
+    _check(load().lelbm_mlp_init(dims, seed, ctypes.c_void_p(X_ptr), ctypes.c_void_p(Y_ptr), n,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def lelbm_mlp_loss_grad(dims: int, params_ptr: int, X_ptr: int, Y_ptr: int, n: int, grad_ptr: int,
+                        stream: int | None = None) -> float:
+    loss = ctypes.c_double()
+    _check(load().lelbm_mlp_loss_grad(dims, ctypes.c_void_p(params_ptr), ctypes.c_void_p(X_ptr),
+                                      ctypes.c_void_p(Y_ptr), n, ctypes.c_void_p(grad_ptr), ctypes.byref(loss),
+                                      ctypes.c_void_p(stream)))
+    return loss.value
+
+
+def lelbm_mlp_train(dims: int, params_ptr: int, X_ptr: int, Y_ptr: int, n: int, epochs: int, batch: int,
+                    lr: float, seed: int = 0, stream: int | None = None) -> np.ndarray:
+    losses = np.zeros(epochs)
+    _check(load().lelbm_mlp_train(dims, ctypes.c_void_p(params_ptr), ctypes.c_void_p(X_ptr), ctypes.c_void_p(Y_ptr),
+                                  n, epochs, batch, lr, seed, losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.c_void_p(stream)))
+    return losses
+
+
+def lelbm_step_record(h, x_ptr: int, y_ptr: int) -> None:
+    _check(load().lelbm_step_record(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr)), h)
+
+
+def lelbm_set_mlp(h, params) -> None:
+    if params is None:
+        _check(load().lelbm_set_mlp(h, ctypes.POINTER(ctypes.c_float)()), h)
+        return
+    arr = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().lelbm_set_mlp(h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), h)
 
 
 def lelbm_last_error(h) -> str:

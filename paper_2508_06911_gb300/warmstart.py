@@ -1,0 +1,89 @@
+"""Training driver of the learned EPR warm start (the kernels are in csrc/lelbm_mlp.cu).
+
+Pairs (features -> converged multipliers minus the Maxwellian start of Eq. IID13) are
+recorded by the plain solver during ordinary time steps (lelbm_step_record); the network is
+initialised and trained by the library's own BF16/FP32 kernels (lelbm_mlp_init,
+lelbm_mlp_train).  PyTorch only provides device buffers here.
+
+  python -m paper_2508_06911_gb300.warmstart --dims 1 --out warm1d.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import lelbm as L
+
+
+def record_pairs(solver, steps: int = 1, max_pairs: int | None = None):
+    """(X, Y) float32 CUDA tensors of the pairs recorded over `steps` time steps."""
+    import torch
+
+    nin, nout, _, _ = L.lelbm_mlp_size(solver.dims)
+    xs, ys = [], []
+    total = 0
+    for _ in range(steps):
+        x = torch.full((solver.n_cells, nin), float("nan"), dtype=torch.float32, device="cuda")
+        y = torch.full((solver.n_cells, nout), float("nan"), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        L.lelbm_step_record(solver.h, x.data_ptr(), y.data_ptr())
+        solver.synchronize()
+        ok = torch.isfinite(x).all(1) & torch.isfinite(y).all(1)
+        xs.append(x[ok])
+        ys.append(y[ok])
+        total += int(ok.sum())
+        if max_pairs is not None and total >= max_pairs:
+            break
+    X = torch.cat(xs).contiguous()
+    Y = torch.cat(ys).contiguous()
+    if max_pairs is not None:
+        X, Y = X[:max_pairs].contiguous(), Y[:max_pairs].contiguous()
+    return X, Y
+
+
+def train(dims: int, X, Y, epochs: int = 4, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
+    """Initialise (normalisation from the data) and train; returns (params float32, epoch losses)."""
+    import torch
+
+    n = X.shape[0]
+    p0 = L.lelbm_mlp_init(dims, seed, X.data_ptr(), Y.data_ptr(), n)
+    P = torch.from_numpy(p0).cuda()
+    torch.cuda.synchronize()
+    losses = L.lelbm_mlp_train(dims, P.data_ptr(), X.data_ptr(), Y.data_ptr(), n, epochs, batch, lr, seed)
+    return P.cpu().numpy(), losses
+
+
+def main():
+    import torch
+
+    from . import build, workloads as W
+    from .solver import Solver
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, default=1)
+    ap.add_argument("--pairs", type=int, default=10_000_000)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args()
+    build.build()
+    torch.cuda.init()
+    t0 = time.time()
+    if a.dims == 1:  # pairs from the 4096-instance batch (seed index 11: not the benchmark's)
+        s = Solver.riemann1d(W.riemann_1d_batch(n_batch=4096, seed_index=11))
+        X, Y = record_pairs(s, steps=4, max_pairs=a.pairs)
+    else:  # pairs from the 2D four-quadrant problem (seed index 12)
+        s = Solver.grid2d(W.riemann_2d(n=1024, seed_index=12))
+        X, Y = record_pairs(s, steps=12, max_pairs=a.pairs)
+    t1 = time.time()
+    params, losses = train(a.dims, X, Y, epochs=a.epochs)
+    t2 = time.time()
+    np.save(a.out, params)
+    print(json.dumps({"dims": a.dims, "pairs": int(X.shape[0]), "record_s": round(t1 - t0, 2),
+                      "train_s": round(t2 - t1, 2), "epoch_loss": [float(v) for v in losses]}))
+
+
+if __name__ == "__main__":
+    main()
