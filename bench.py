@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default persistent launch shape")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell"],
                     help="EPR Newton start of the timed path: the trained MLP or Eq. (IID13)")
     ap.add_argument("--per-step", action="store_true", help="1D batch: one launch per step instead of the "
@@ -272,7 +273,7 @@ def run_ours(args):
             s.step(n)
 
     def timed(s, sample_clocks):
-        if persistent:
+        if persistent and not args.no_autotune:
             s.autotune(1)
         advance(s, args.warmup)
         torch.cuda.synchronize()
@@ -324,6 +325,16 @@ def run_ours(args):
                         "points_fp64_newton": st3.points_f + st3.points_g,
                         "newton_mean_updates": sum(i * x for i, x in enumerate(h3)) / max(sum(h3), 1)}
             s3.close()
+            # and on the other precision: what the network gains there
+            s4 = make(other, learned=True)
+            ms4, st4, _, _ = timed(s4, False)
+            h4 = list(st4.newton_hist)
+            compare["learned"] = {"value": interior * args.steps * world / (ms4 / 1e3) / 1e6,
+                                  "ms_per_step": ms4 / args.steps,
+                                  "points_fp64_newton": st4.points_f + st4.points_g,
+                                  "newton_mean_updates": sum(i * x for i, x in enumerate(h4)) / max(sum(h4), 1)}
+            compare["points_fp64_newton"] = st2.points_f + st2.points_g
+            s4.close()
 
     # dominant kernel: the fused cell update, FP64-ALU bound
     # one timed launch covers args.steps steps on the persistent path; work per launch

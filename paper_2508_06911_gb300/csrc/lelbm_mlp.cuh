@@ -52,6 +52,8 @@ struct MlpLayout {
 };
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// inference-only SiLU with the fast reciprocal (BF16 activations follow anyway)
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z) {
     const float s = 1.f / (1.f + __expf(-z));
     return s * (1.f + z * (1.f - s));
@@ -117,6 +119,189 @@ __device__ __forceinline__ void mlp_forward(const __nv_bfloat16* W, const float*
     }
 #pragma unroll
     for (int k = 0; k < Md::NOUT; k++) y[k] = out[k] * nrm[2 * Md::NIN + Md::NOUT + k] + nrm[2 * Md::NIN + k];
+}
+
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores.  A warp evaluates the network for its 32 cells at
+// once as three small GEMMs (32 x 16 x 64, 32 x 64 x 64, 32 x 64 x NOUT) with
+// mma.sync m16n8k16 BF16 -> FP32: 88 MMAs per 32 cells instead of ~5000 FMAs per
+// cell.  The weights sit in shared memory in padded rows (stride 24 / 72 BF16) so
+// the fragment loads of the 8 row groups hit distinct banks.
+// ---------------------------------------------------------------------------
+template <int D>
+struct MlpMma {
+    static constexpr int S1 = 24;                  // row stride of W1 (inputs padded to 16)
+    static constexpr int S2 = 72;                  // row stride of W2, W3 and of activations
+    static constexpr int N3 = D == 1 ? 8 : 16;     // outputs padded to whole n-tiles
+    static constexpr int W1 = 0;
+    static constexpr int W2 = W1 + 64 * S1;
+    static constexpr int W3 = W2 + 64 * S2;
+    static constexpr int NWS = W3 + N3 * S2;       // BF16 elements of the staged weights
+    static constexpr int WARPS = 4;                // warps per block (128 threads)
+    // dynamic shared memory: weights | b1 b2 b3 | normalisation | per-warp X | per-warp H | per-warp O
+    static constexpr size_t OFF_B = ((size_t)NWS * 2 + 15) & ~(size_t)15;
+    static constexpr size_t OFF_N = OFF_B + sizeof(float) * (64 + 64 + 16);
+    static constexpr size_t OFF_X = (OFF_N + sizeof(float) * 2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT) + 15) & ~(size_t)15;
+    static constexpr size_t OFF_H = OFF_X + (size_t)WARPS * 32 * S1 * 2;
+    static constexpr size_t OFF_O = OFF_H + (size_t)WARPS * 32 * S2 * 2;
+    static constexpr size_t BYTES = OFF_O + (size_t)WARPS * 32 * 16 * sizeof(float);
+};
+
+// Stage the weights of the FP32-layout BF16 copy (W) and the FP32 normalisation into
+// the padded shared-memory layout; every thread of the block must call it.
+template <int D>
+__device__ __forceinline__ void mlp_stage_mma(unsigned char* smem, const __nv_bfloat16* W, const float* nrm) {
+    using Md = MlpDims<D>;
+    using Ly = MlpLayout<D>;
+    using Mm = MlpMma<D>;
+    __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(smem);
+    float* b = reinterpret_cast<float*>(smem + Mm::OFF_B);
+    float* nr = reinterpret_cast<float*>(smem + Mm::OFF_N);
+    const __nv_bfloat16 z = __float2bfloat16(0.f);
+    for (int i = threadIdx.x; i < 64 * Mm::S1; i += blockDim.x) {
+        const int n = i / Mm::S1, k = i % Mm::S1;
+        w[Mm::W1 + i] = k < Md::NIN ? W[Ly::W1 + n * Md::NIN + k] : z;
+    }
+    for (int i = threadIdx.x; i < 64 * Mm::S2; i += blockDim.x) {
+        const int n = i / Mm::S2, k = i % Mm::S2;
+        w[Mm::W2 + i] = k < 64 ? W[Ly::W2 + n * 64 + k] : z;
+    }
+    for (int i = threadIdx.x; i < Mm::N3 * Mm::S2; i += blockDim.x) {
+        const int n = i / Mm::S2, k = i % Mm::S2;
+        w[Mm::W3 + i] = (n < Md::NOUT && k < 64) ? W[Ly::W3 + n * 64 + k] : z;
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        b[i] = __bfloat162float(W[Ly::B1 + i]);
+        b[64 + i] = __bfloat162float(W[Ly::B2 + i]);
+    }
+    for (int i = threadIdx.x; i < 16; i += blockDim.x) b[128 + i] = i < Md::NOUT ? __bfloat162float(W[Ly::B3 + i]) : 0.f;
+    for (int i = threadIdx.x; i < 2 * (Md::NIN + Md::NOUT); i += blockDim.x) nr[i] = nrm[i];
+}
+
+__device__ __forceinline__ void mma_bf16_16x8x16(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                                 unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned ld_b32(const __nv_bfloat16* p) { return *reinterpret_cast<const unsigned*>(p); }
+
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float lo, float hi) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+}
+
+// Whole-warp inference: lane i supplies the raw features x of its cell (ignored when
+// !valid) and receives the raw prediction y.  All 32 lanes must call it.
+template <int D>
+__device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bool valid, float* y) {
+    using Md = MlpDims<D>;
+    using Mm = MlpMma<D>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(smem);
+    const float* b = reinterpret_cast<const float*>(smem + Mm::OFF_B);
+    const float* nr = reinterpret_cast<const float*>(smem + Mm::OFF_N);
+    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + Mm::OFF_X) + warp * 32 * Mm::S1;
+    __nv_bfloat16* Hh = reinterpret_cast<__nv_bfloat16*>(smem + Mm::OFF_H) + warp * 32 * Mm::S2;
+    float* O = reinterpret_cast<float*>(smem + Mm::OFF_O) + warp * 32 * 16;
+    // standardised inputs, one row per lane, zero padded to 16
+#pragma unroll
+    for (int m = 0; m < 16; m += 2) {
+        const float v0 = (valid && m < Md::NIN) ? __fdividef(x[m] - nr[m], nr[Md::NIN + m]) : 0.f;
+        const float v1 = (valid && m + 1 < Md::NIN) ? __fdividef(x[m + 1] - nr[m + 1], nr[Md::NIN + m + 1]) : 0.f;
+        st_pair(X + lane * Mm::S1 + m, v0, v1);
+    }
+    __syncwarp();
+    // layer 1: H = silu(X W1^T + b1)
+    unsigned a[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+        const __nv_bfloat16* r0 = X + (mt * 16 + gid) * Mm::S1 + tig * 2;
+        const __nv_bfloat16* r1 = r0 + 8 * Mm::S1;
+        a[mt][0][0] = ld_b32(r0);
+        a[mt][0][1] = ld_b32(r1);
+        a[mt][0][2] = ld_b32(r0 + 8);
+        a[mt][0][3] = ld_b32(r1 + 8);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+        const __nv_bfloat16* wb = w + Mm::W1 + (nt * 8 + gid) * Mm::S1 + tig * 2;
+        const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
+        const int col = nt * 8 + tig * 2;
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16_16x8x16(d, a[mt][0][0], a[mt][0][1], a[mt][0][2], a[mt][0][3], b0, b1);
+            const int row = mt * 16 + gid;
+            st_pair(Hh + row * Mm::S2 + col, silu_fast(d[0] + b[col]), silu_fast(d[1] + b[col + 1]));
+            st_pair(Hh + (row + 8) * Mm::S2 + col, silu_fast(d[2] + b[col]), silu_fast(d[3] + b[col + 1]));
+        }
+    }
+    __syncwarp();
+    // layers 2 and 3 read the whole previous activation into fragments first, so the
+    // result can overwrite it in place
+    auto load_h = [&]() {
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+            for (int kt = 0; kt < 4; kt++) {
+                const __nv_bfloat16* r0 = Hh + (mt * 16 + gid) * Mm::S2 + kt * 16 + tig * 2;
+                const __nv_bfloat16* r1 = r0 + 8 * Mm::S2;
+                a[mt][kt][0] = ld_b32(r0);
+                a[mt][kt][1] = ld_b32(r1);
+                a[mt][kt][2] = ld_b32(r0 + 8);
+                a[mt][kt][3] = ld_b32(r1 + 8);
+            }
+    };
+    load_h();
+    __syncwarp();
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+        float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int kt = 0; kt < 4; kt++) {
+            const __nv_bfloat16* wb = w + Mm::W2 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
+            const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) mma_bf16_16x8x16(d[mt], a[mt][kt][0], a[mt][kt][1], a[mt][kt][2], a[mt][kt][3], b0, b1);
+        }
+        const int col = nt * 8 + tig * 2;
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            const int row = mt * 16 + gid;
+            st_pair(Hh + row * Mm::S2 + col, silu_fast(d[mt][0] + b[64 + col]), silu_fast(d[mt][1] + b[64 + col + 1]));
+            st_pair(Hh + (row + 8) * Mm::S2 + col, silu_fast(d[mt][2] + b[64 + col]), silu_fast(d[mt][3] + b[64 + col + 1]));
+        }
+    }
+    __syncwarp();
+    load_h();
+#pragma unroll
+    for (int nt = 0; nt < Mm::N3 / 8; nt++) {
+        float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int kt = 0; kt < 4; kt++) {
+            const __nv_bfloat16* wb = w + Mm::W3 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
+            const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) mma_bf16_16x8x16(d[mt], a[mt][kt][0], a[mt][kt][1], a[mt][kt][2], a[mt][kt][3], b0, b1);
+        }
+        const int col = nt * 8 + tig * 2;
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            const int row = mt * 16 + gid;
+            O[row * 16 + col] = d[mt][0] + b[128 + col];
+            O[row * 16 + col + 1] = d[mt][1] + b[128 + col + 1];
+            O[(row + 8) * 16 + col] = d[mt][2] + b[128 + col];
+            O[(row + 8) * 16 + col + 1] = d[mt][3] + b[128 + col + 1];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < Md::NOUT; k++) y[k] = O[lane * 16 + k] * nr[2 * Md::NIN + Md::NOUT + k] + nr[2 * Md::NIN + k];
+    __syncwarp();
 }
 
 }  // namespace lbm

@@ -240,20 +240,6 @@ struct ThreadCounters {
     LocalStats ls;
 };
 
-// BF16 weights and FP32 normalisation of the warm-start MLP in shared memory.
-template <int D>
-struct MlpShared {
-    __nv_bfloat16 w[MlpLayout<D>::NW];
-    float nrm[2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT)];
-};
-
-template <int D>
-__device__ __forceinline__ void mlp_stage(const Model& m, MlpShared<D>& sm) {
-    if (!m.mlp_w) return;
-    for (int i = threadIdx.x; i < MlpLayout<D>::NW; i += blockDim.x) sm.w[i] = m.mlp_w[i];
-    for (int i = threadIdx.x; i < 2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT); i += blockDim.x) sm.nrm[i] = m.mlp_nrm[i];
-}
-
 __device__ __forceinline__ void counters_init(BlockCounters& bc) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
     if (threadIdx.x == 0)
@@ -290,44 +276,49 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
     }
 }
 
-// The whole single-cell operation of Fig. 5 for one (non-solid) cell: collision,
-// LAS, EPR (with the fallbacks) and moment streaming into Mout.
-template <int D, bool MIXED>
-__device__ __forceinline__ void process_cell(const Model& m, const Geometry& g, const uint8_t* type,
-                                             const double* __restrict__ Min, double* Mout, DevStats* stats,
-                                             long long cell, BlockCounters& bc, ThreadCounters& tc, double* conF,
-                                             double* conG, const MlpShared<D>* mlp) {
-    constexpr int NM = Dim<D>::NM, NF = Dim<D>::NF, NG = Dim<D>::NG;
+// The single-cell operation of Fig. 5 in two halves around the (warp-wide) warm-start
+// network: prepare_cell loads the moments, runs the collision module and sets up the
+// stencil; finish_cell runs EPR (with the fallbacks) and moment streaming into Mout.
+template <int D>
+__device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, const double* __restrict__ Min,
+                                             DevStats* stats, long long cell, BlockCounters& bc, CellState<D>& c,
+                                             Stencil<D>& st) {
+    constexpr int NM = Dim<D>::NM;
     double M[NM];
 #pragma unroll
     for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
-    CellState<D> c;
     collide<D>(M, m, c);
     if (!c.ok) {  // non-physical cell: nothing can be reconstructed
         atomicAdd(&bc.fmx, 1ull);
         atomicMin(&stats->first_fail, (unsigned long long)cell);
-        return;
+        return false;
     }
-    tc.cells++;
-    Stencil<D> st;
     st.init(c, m);
+    return true;
+}
+
+// dl: the learned correction of the Maxwellian start (fluons then phonons), or null.
+template <int D, bool MIXED>
+__device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                            DevStats* stats, long long cell, BlockCounters& bc, ThreadCounters& tc,
+                                            double* conF, double* conG, const CellState<D>& c, const Stencil<D>& st,
+                                            const float* dl) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    tc.cells++;
     const bool has_g = m.K > 0.0;
     double lf[NF], lg[NG];
     maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
     bool learned = false;
-    if (mlp) {  // learned correction of the Maxwellian start
-        float xin[MlpDims<D>::NIN], yout[MlpDims<D>::NOUT];
-        mlp_features<D>(c, st, xin);
-        mlp_forward<D>(mlp->w, mlp->nrm, xin, yout);
+    if (dl) {
         bool ok = true;
 #pragma unroll
-        for (int k = 0; k < MlpDims<D>::NOUT; k++) ok = ok && isfinite(yout[k]);
+        for (int k = 0; k < MlpDims<D>::NOUT; k++) ok = ok && isfinite(dl[k]);
         if (ok) {
 #pragma unroll
-            for (int j = 0; j < NF; j++) lf[j] += (double)yout[j];
+            for (int j = 0; j < NF; j++) lf[j] += (double)dl[j];
             if (has_g) {
 #pragma unroll
-                for (int j = 0; j < NG; j++) lg[j] += (double)yout[NF + j];
+                for (int j = 0; j < NG; j++) lg[j] += (double)dl[NF + j];
             }
             learned = true;
         }
@@ -428,13 +419,13 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ BlockCounters bc;
     __shared__ double s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
-    __shared__ MlpShared<D> s_mlp;
+    extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
     counters_init(bc);
-    mlp_stage<D>(m, s_mlp);
+    const bool mlp = m.mlp_w != nullptr;
+    if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
     __syncthreads();
-    const MlpShared<D>* mlp = m.mlp_w ? &s_mlp : nullptr;
     ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0}};
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -443,8 +434,18 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= (unsigned long long)g.ncell) break;
         const long long cell = (long long)base + lane;
-        if (cell >= g.ncell || type[cell] == CELL_SOLID) continue;
-        process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, mlp);
+        const bool active = cell < g.ncell && type[cell] != CELL_SOLID;
+        CellState<D> c;
+        Stencil<D> st;
+        bool ok = false;
+        if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
+        float dl[MlpDims<D>::NOUT];
+        if (mlp) {  // warp-uniform: every lane takes part in the tensor-core inference
+            float xin[MlpDims<D>::NIN];
+            if (ok) mlp_features<D>(c, st, xin);
+            warp_mlp<D>(s_mlp, xin, ok, dl);
+        }
+        if (ok) finish_cell<D, MIXED>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
     }
     counters_flush(bc, tc, stats);
 }
@@ -468,12 +469,12 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
     __shared__ double s_con[128][NF + NG];
     __shared__ unsigned int s_next;
     __shared__ int s_inst;
-    __shared__ MlpShared<1> s_mlp;
+    extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
     counters_init(bc);
-    mlp_stage<1>(m, s_mlp);
-    const MlpShared<1>* mlp = m.mlp_w ? &s_mlp : nullptr;
+    const bool mlp = m.mlp_w != nullptr;
+    if (mlp) mlp_stage_mma<1>(s_mlp, m.mlp_w, m.mlp_nrm);
     ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0}};
     const int lane = threadIdx.x & 31;
     double Meq[NM];
@@ -525,10 +526,20 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (base >= (unsigned int)nblk) break;
                 const int i = (int)base + lane;
-                if (i >= nblk) continue;
                 const long long cell = first + i;
-                if (type[cell] == CELL_SOLID) continue;
-                process_cell<D, MIXED>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, mlp);
+                const bool active = i < nblk && type[cell] != CELL_SOLID;
+                CellState<D> c;
+                Stencil<D> st;
+                bool ok = false;
+                if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
+                float dl[MlpDims<D>::NOUT];
+                if (mlp) {
+                    float xin[MlpDims<D>::NIN];
+                    if (ok) mlp_features<D>(c, st, xin);
+                    warp_mlp<D>(s_mlp, xin, ok, dl);
+                }
+                if (ok)
+                    finish_cell<D, MIXED>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
             }
             __syncthreads();
         }
@@ -547,14 +558,16 @@ void launch_batch_persistent(const Model& m, const Geometry& g, const double inl
                              unsigned long long* work, const int* order, const long long* inst_first,
                              const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, bool mixed,
                              cudaStream_t s) {
+    const size_t sm = m.mlp_w ? MlpMma<1>::BYTES : 0;
+    auto go = [&](auto kern) {
+        if (sm) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<blocks, threads, sm, s>>>(m, g, inlet[0], inlet[1], inlet[3], bc_left_inflow, bc_right_inflow, type, A,
+                                         B, st, work, order, inst_first, inst_pad, steps_left, nsteps);
+    };
     if (mixed)
-        batch_persistent_kernel<true><<<blocks, threads, 0, s>>>(m, g, inlet[0], inlet[1], inlet[3], bc_left_inflow,
-                                                                 bc_right_inflow, type, A, B, st, work, order,
-                                                                 inst_first, inst_pad, steps_left, nsteps);
+        go(batch_persistent_kernel<true>);
     else
-        batch_persistent_kernel<false><<<blocks, threads, 0, s>>>(m, g, inlet[0], inlet[1], inlet[3], bc_left_inflow,
-                                                                  bc_right_inflow, type, A, B, st, work, order,
-                                                                  inst_first, inst_pad, steps_left, nsteps);
+        go(batch_persistent_kernel<false>);
 }
 
 int batch_persistent_max_blocks_per_sm(bool mixed, int threads) {
@@ -677,16 +690,21 @@ void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, 
     long long need = (g.ncell + 127) / 128;
     int blocks = (int)(need < grid_blocks ? need : grid_blocks);
     if (blocks < 1) blocks = 1;
+    const size_t sm = m.mlp_w ? (g.D == 1 ? MlpMma<1>::BYTES : MlpMma<2>::BYTES) : 0;
+    auto go = [&](auto kern) {
+        if (sm) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<blocks, 128, sm, s>>>(m, g, type, Min, Mout, st, work);
+    };
     if (g.D == 1) {
         if (mixed)
-            cell_update_kernel<1, true><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+            go(cell_update_kernel<1, true>);
         else
-            cell_update_kernel<1, false><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+            go(cell_update_kernel<1, false>);
     } else {
         if (mixed)
-            cell_update_kernel<2, true><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+            go(cell_update_kernel<2, true>);
         else
-            cell_update_kernel<2, false><<<blocks, 128, 0, s>>>(m, g, type, Min, Mout, st, work);
+            go(cell_update_kernel<2, false>);
     }
 }
 
