@@ -79,6 +79,7 @@ class Stats(ctypes.Structure):
         ("fallback_mx", ctypes.c_longlong),
         ("q_max", ctypes.c_longlong),
         ("disp_max", ctypes.c_double),
+        ("wall_hits", ctypes.c_longlong),
     ]
 
 
@@ -130,6 +131,9 @@ def lib():
                                                ctypes.POINTER(Point), _DP, _DP, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]
             L.orc_fill_pads.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), _DP]
+            L.orc_trace_path.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), _DP, _DP]
             L.orc_step.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), _DP, _DP,
                                    ctypes.POINTER(Stats)]
             _lib = L
@@ -340,6 +344,23 @@ def fill_pads(g: Grid, p: Params, M: np.ndarray) -> np.ndarray:
     W = np.ascontiguousarray(M, dtype=np.float64).copy()
     lib().orc_fill_pads(ctypes.byref(g), ctypes.byref(p), _dp(W))
     return W
+
+
+def trace_path(g: Grid, ix: int, iy: int, c):
+    """Path of one population from padded cell (ix, iy) with velocity c past the
+    solid cells of ``g``, Sec. III.B (specular reflection at slip walls).
+
+    Returns (touched, (fi, fj), offset[2], c_star[2]): the final cell, the landing
+    point's offset from that cell's centre and the reflected velocity.
+    """
+    NY, NX = padded_shape(g)
+    cc = np.zeros(2)
+    cc[:g.D] = np.asarray(c, dtype=np.float64).reshape(-1)[:g.D]
+    fi, fj = ctypes.c_int(), ctypes.c_int()
+    off, cs = np.zeros(2), np.zeros(2)
+    t = lib().orc_trace_path(ctypes.byref(g), NX, NY, ix, iy, _dp(cc), ctypes.byref(fi), ctypes.byref(fj),
+                             _dp(off), _dp(cs))
+    return bool(t), (fi.value, fj.value), off, cs
 
 
 def step(g: Grid, p: Params, M: np.ndarray, stats: Stats | None = None) -> np.ndarray:

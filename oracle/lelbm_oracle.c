@@ -23,6 +23,7 @@
  *   EPR Newton, Maxwellian start ..... Eq. (IID7)-(IID13)
  *   moment streaming ................. Eq. (IIE3)
  *   fluid boundaries ................. Sec. III.A
+ *   solid boundaries (slip wall) ..... Sec. III.B, Eq. (IIIB10)-(IIIB15)
  * Readings of passages the paper leaves open are marked "reading:" below.
  *
  * Build with -ffp-contract=off: every operation then rounds once, on x86-64
@@ -76,6 +77,7 @@ typedef struct {
     long long fallback_mx;   /* solves that fell back to Maxwellian weights */
     long long q_max;         /* largest stencil                             */
     double disp_max;         /* largest |c_i| (lattice Courant, Eq. IIC3)   */
+    long long wall_hits;     /* populations reflected at solid faces        */
 } orc_stats;
 
 typedef struct {
@@ -666,6 +668,93 @@ static int land_axis(int i, int n, int pad, int periodic)
     return i;
 }
 
+/* Sec. III.B: is padded cell (i, j) a solid cell?  Cells outside the array are
+ * not (their populations are discarded later). */
+static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
+{
+    if (!g->solid) return 0;
+    if (g->periodic[0]) i = ((i % NX) + NX) % NX;
+    if (g->D == 2 && g->periodic[1]) j = ((j % NY) + NY) % NY;
+    if (i < 0 || i >= NX || j < 0 || j >= NY) return 0;
+    return g->solid[(long)j * NX + i] != 0;
+}
+
+/* Sec. III.B, first step of the extended bounce-back: the path x -> x + c is
+ * followed cell by cell, and at a face of a solid cell the population is
+ * specularly reflected (the normal component of its velocity flips) until the
+ * whole displacement is used.  reading: for a stationary adiabatic slip wall the
+ * image populations of Eq. (IIIB10)-(IIIB15) are built from the cell's own
+ * post-collision moments (u_n = u, Eq. IIIB11-12), so they are the reflected
+ * real populations and the mass ratio of Eq. (IIIB15) is one.  Face crossings
+ * are ordered exactly in integer units of 1/64 cell.  reading: a path through a
+ * cell corner whose diagonal cell is solid reflects only the component normal
+ * to a flat wall (one of the two side cells solid, the other fluid) and both
+ * components otherwise; with the diagonal cell fluid it passes the corner.
+ * Returns 1 if the population touched a wall; *fi, *fj receive the final cell,
+ * off[] the final offset from its centre, cs[] the reflected velocity c*. */
+int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const double* c, int* fi, int* fj,
+                      double* off, double* cs)
+{
+    const long S = 64;
+    int D = g->D;
+    long qx = lround(S * c[0]), qy = D == 2 ? lround(S * c[1]) : 0;
+    int sx = qx > 0 ? 1 : (qx < 0 ? -1 : 0), sy = qy > 0 ? 1 : (qy < 0 ? -1 : 0);
+    long ax = labs(qx), ay = labs(qy);
+    int i = ix, j = iy, touched = 0;
+    long kx = 0, ky = 0;
+    for (;;) {
+        long Xn = S / 2 + S * kx, Yn = S / 2 + S * ky;
+        int hx = ax > 0 && Xn < ax, hy = ay > 0 && Yn < ay;
+        if (!hx && !hy) break;
+        int stx = hx, sty = hy;
+        if (hx && hy) {
+            long l = Xn * ay, r = Yn * ax;
+            stx = l <= r;
+            sty = r <= l;
+        }
+        if (stx && sty) {
+            /* through a cell corner: a flat wall along one axis reflects only
+             * that component, a corner of solid cells reflects both */
+            if (!solid_at(g, NX, NY, i + sx, j + sy)) {
+                i += sx;
+                j += sy;
+            } else {
+                int sa = solid_at(g, NX, NY, i + sx, j), sb = solid_at(g, NX, NY, i, j + sy);
+                touched = 1;
+                if (sa && !sb) {
+                    sx = -sx;
+                    j += sy;
+                } else if (sb && !sa) {
+                    sy = -sy;
+                    i += sx;
+                } else {
+                    sx = -sx;
+                    sy = -sy;
+                }
+            }
+        } else {
+            int ti = i + (stx ? sx : 0), tj = j + (sty ? sy : 0);
+            if (solid_at(g, NX, NY, ti, tj)) {
+                if (stx) sx = -sx;
+                if (sty) sy = -sy;
+                touched = 1;
+            } else {
+                i = ti;
+                j = tj;
+            }
+        }
+        if (stx) kx++;
+        if (sty) ky++;
+    }
+    *fi = i;
+    *fj = j;
+    off[0] = sx * (double)(ax - S * kx) / S;
+    off[1] = sy * (double)(ay - S * ky) / S;
+    cs[0] = sx * fabs(c[0]);
+    cs[1] = D == 2 ? sy * fabs(c[1]) : 0.0;
+    return touched;
+}
+
 /* One time step over a padded grid: fill the pads, then for every non-solid
  * cell run collision, LAS and EPR and stream the moment fractions
  * T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i to x + c_i (Eq. IIE3).
@@ -719,15 +808,27 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
                     double cm = sqrt(dist2(D, c, (double[2]){0.0, 0.0}));
                     if (cm > st->disp_max) st->disp_max = cm;
                 }
-                double dM[ORC_MAXM];
-                raw_contrib(D, c, mscale * popf[k], p->K > 0.0 ? gscale * popg[k] : 0.0, dM);
-                /* cloud-in-cell split of the landing position x + c */
+                /* landing point: x + c, or the end of the reflected path (Sec. III.B) */
+                double cl[2] = {c[0], D == 2 ? c[1] : 0.0}, pos[2];
+                int fi = ix, fj = iy;
+                if (g->solid) {
+                    double off[2];
+                    int touched = orc_trace_path(g, NX, NY, ix, iy, c, &fi, &fj, off, cl);
+                    if (st && touched) st->wall_hits++;
+                    pos[0] = fi + off[0];
+                    pos[1] = fj + off[1];
+                } else {
+                    pos[0] = ix + c[0];
+                    pos[1] = iy + (D == 2 ? c[1] : 0.0);
+                }
+                double mf = mscale * popf[k], mg = p->K > 0.0 ? gscale * popg[k] : 0.0;
+                /* cloud-in-cell split of the landing position */
                 int i0[2] = {0, 0};
                 double w1[2] = {0.0, 0.0};
                 for (int a = 0; a < D; a++) {
-                    double fl = floor(c[a]);
+                    double fl = floor(pos[a]);
                     i0[a] = (int)fl;
-                    w1[a] = c[a] - fl;
+                    w1[a] = pos[a] - fl;
                 }
                 int ncx = w1[0] > 0.0 ? 2 : 1;
                 int ncy = (D == 2 && w1[1] > 0.0) ? 2 : 1;
@@ -735,13 +836,41 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
                     for (int sx = 0; sx < ncx; sx++) {
                         double w = (sx ? w1[0] : 1.0 - w1[0]);
                         if (D == 2) w *= (sy ? w1[1] : 1.0 - w1[1]);
+                        int cx_ = i0[0] + sx, cy_ = D == 2 ? i0[1] + sy : 0;
+                        double cw[2] = {cl[0], cl[1]};
+                        /* reading: a share that would fall on a solid cell is the mirror
+                         * image of one arriving from the image lattice, so it is mirrored
+                         * back across the wall with the normal velocity component reversed
+                         * (exact for flat walls, Sec. III.B).  A diagonal share behind a
+                         * flat wall (one side cell fluid) goes to that side cell; behind a
+                         * corner of solid cells it goes to the final cell, both reversed. */
+                        if (solid_at(g, NX, NY, cx_, cy_)) {
+                            int ox = cx_ != fi, oy = cy_ != fj;
+                            if (ox && oy) {
+                                int sa = solid_at(g, NX, NY, cx_, fj), sb = solid_at(g, NX, NY, fi, cy_);
+                                if (!sa && sb) {
+                                    ox = 0; /* keep x: mirror across the y wall */
+                                } else if (sa && !sb) {
+                                    oy = 0; /* keep y: mirror across the x wall */
+                                }
+                            }
+                            if (ox) {
+                                cw[0] = -cw[0];
+                                cx_ = fi;
+                            }
+                            if (oy) {
+                                cw[1] = -cw[1];
+                                cy_ = fj;
+                            }
+                        }
+                        double dM[ORC_MAXM];
+                        raw_contrib(D, cw, mf, mg, dM);
                         /* px = 0 on a periodic axis, py likewise */
-                        int tx = land_axis(ix + i0[0] + sx, g->nx, px, g->periodic[0]);
+                        int tx = land_axis(cx_, g->nx, px, g->periodic[0]);
                         int ty = 0;
-                        if (D == 2) ty = land_axis(iy + i0[1] + sy, ny, py, g->periodic[1]);
+                        if (D == 2) ty = land_axis(cy_, ny, py, g->periodic[1]);
                         if (tx < 0 || ty < 0) continue;
                         long tgt = (long)ty * NX + tx;
-                        if (g->solid && g->solid[tgt]) continue;
                         for (int m = 0; m < nm; m++) Mout[m * ncell + tgt] += w * dM[m];
                     }
             }
