@@ -7,7 +7,7 @@ one time step of every instance (fluid-boundary fill, collision, LAS, EPR, momen
 streaming).  MLUPS = interior cell updates per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload batch1d|hotbox2d|riemann2d]
+                  [--workload batch1d|hotbox2d|riemann2d|cylinder2d]
 
 --impl reference times the plain FP64 CPU oracle (the correctness reference) on a
 bounded sample of the same workload.  Under torchrun each rank runs its own batch
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch1d", choices=["batch1d", "hotbox2d", "riemann2d"])
+    ap.add_argument("--workload", default="batch1d", choices=["batch1d", "hotbox2d", "riemann2d", "cylinder2d"])
     ap.add_argument("--n-batch", type=int, default=4096)
     ap.add_argument("--n", type=int, default=1024, help="2D grid size")
     ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
@@ -86,6 +86,12 @@ def make_workload(args, rank):
         w = W.hot_box(2, args.n, args.rt)
         return w, {"workload": f"hotbox2d_{args.n}x{args.n}_RT{args.rt}", "dims": 2, "u": [10, 10],
                    "interior_cells": args.n * args.n}
+    if args.workload == "cylinder2d":
+        # Mach-3 slip-wall cylinder, 2n x n cells, diameter n/8 (2048 x 1024, D = 128 at n = 1024)
+        w = W.cylinder_2d(nx=2 * args.n, ny=args.n, diameter=args.n // 8)
+        fluid = int((w.solid == 0).sum())
+        return w, {"workload": w.name, "dims": 2, "interior_cells": fluid, "solid_cells": int(w.solid.sum()),
+                   "mach": 3.0, "boundary": "inflow x-, outflow elsewhere, slip-wall cylinder"}
     w = W.riemann_2d(n=args.n, seed_index=2 + 1000 * rank)
     return w, {"workload": f"riemann2d_{args.n}x{args.n}", "dims": 2, "interior_cells": args.n * args.n}
 
@@ -132,6 +138,18 @@ def clock_sampler_stop(state, gpu_index=0):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def small_2d(args, n):
+    """An n x n (cylinder: 2n x n) instance of the 2D workload for the CPU oracle."""
+    from paper_2508_06911_gb300 import workloads as W
+
+    if args.workload == "hotbox2d":
+        return W.hot_box(2, n, args.rt), n * n
+    if args.workload == "cylinder2d":
+        w = W.cylinder_2d(nx=2 * n, ny=n, diameter=max(n // 8, 2))
+        return w, int((w.solid == 0).sum())
+    return W.riemann_2d(n=n, seed_index=2), n * n
+
+
 def cpu_baseline(args, budget_s=15.0):
     """The CPU oracle, as it stands (serial FP64 C), on a bounded sample of the workload."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -152,13 +170,13 @@ def cpu_baseline(args, budget_s=15.0):
         sample = f"first {b} instances of the batch ({cells} interior cells), one time step each"
     else:
         n = 64
-        w = W.hot_box(2, n, args.rt) if args.workload == "hotbox2d" else W.riemann_2d(n=n, seed_index=2)
+        w, nc = small_2d(args, n)
         steps = 0
         while time.perf_counter() - t0 < budget_s:
             oracle_2d(w, 1)
-            cells += n * n
+            cells += nc
             steps += 1
-        sample = f"{n}x{n} crop-size instance of the workload, {steps} time steps"
+        sample = f"{w.nx}x{w.ny} small instance of the workload, {steps} time steps"
     dt = time.perf_counter() - t0
     return {"value": cells / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
             "seconds": round(dt, 2)}
@@ -188,9 +206,8 @@ def run_reference(args):
                 oracle_1d_instance(w, b, 1)
                 c += int(w.lengths[b])
         else:
-            small = W.hot_box(2, 48, args.rt) if args.workload == "hotbox2d" else W.riemann_2d(n=48, seed_index=2)
+            small, c = small_2d(args, 48)
             oracle_2d(small, 1)
-            c = 48 * 48
         cells_step = c
         return c
 
@@ -205,7 +222,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = tot / dt / 1e6
     sample = (f"first 16 instances of the batch ({cells_step} interior cells) per step"
-              if args.workload == "batch1d" else "48x48 instance of the workload per step")
+              if args.workload == "batch1d" else f"small instance of the workload ({cells_step} cells) per step")
     line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",

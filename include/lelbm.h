@@ -94,7 +94,13 @@ typedef struct {
     double tol;          /* EPR residual tolerance in thermal units; paper: 1e-12      */
     int max_newton;      /* Newton update cap per solve, 1..60                         */
     int precision;       /* LELBM_FP64 or LELBM_MIXED                                  */
-    const uint8_t* solid;/* host, one byte per padded cell, 1 = solid; NULL: none       */
+    const uint8_t* solid;/* host, one byte per padded cell, 1 = solid; NULL: none.
+                            2D interior cells only (flags on pads and in 1D are
+                            ignored).  Solid cells are stationary adiabatic slip
+                            walls (Sec. III.B): a population whose path crosses a
+                            solid face is specularly reflected, exactly traced in
+                            1/64-cell units; a cloud-in-cell share that would fall
+                            on a solid cell is mirrored back across the wall.    */
     void* stream;        /* cudaStream_t to run on; NULL: a stream owned by the handle  */
 } lelbm_params;
 
@@ -116,6 +122,8 @@ typedef struct {
     long long points_32;          /* stencil points of FP32 Newton passes (mixed)   */
     long long judge_redo;         /* mixed: cells re-solved in FP64 after the check */
     long long mlp_retry;          /* learned start failed; re-solved from Eq. IID13 */
+    long long wall_hits;          /* populations specularly reflected at a solid
+                                     face while streaming (Sec. III.B)              */
 } lelbm_stats;
 
 /* Sizes of the structures this library was built with, so a binding can check

@@ -31,6 +31,7 @@ struct lelbm {
     double* M[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t* d_type = nullptr;
+    uint8_t* d_wall_dist = nullptr;  // 2D with solids: Chebyshev distance to a solid cell
     int* d_inst = nullptr;
     long long* d_inst_lo = nullptr;
     int* d_inst_n = nullptr;
@@ -164,6 +165,7 @@ static void free_all(lelbm* h) {
     cudaFree(h->M[0]);
     cudaFree(h->M[1]);
     cudaFree(h->d_type);
+    cudaFree(h->d_wall_dist);
     cudaFree(h->d_inst);
     cudaFree(h->d_inst_lo);
     cudaFree(h->d_inst_n);
@@ -180,6 +182,42 @@ static void free_all(lelbm* h) {
     cudaFree(h->d_mlp_w);
     cudaFree(h->d_mlp_nrm);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// Chebyshev distance (in cells, capped at 255) from every padded cell to the nearest
+// solid cell: a breadth-first search over the 8-neighbourhood from all solid cells,
+// wrapping periodic axes.  The streaming pass traces paths past solid faces only in
+// cells whose populations can reach that far.
+static std::vector<uint8_t> wall_distance(const std::vector<uint8_t>& type, int NX, int NY, bool per_x,
+                                          bool per_y) {
+    const long long n = (long long)NX * NY;
+    std::vector<uint8_t> dist(n, 255);
+    std::vector<long long> frontier, next;
+    for (long long i = 0; i < n; i++)
+        if (type[i] == CELL_SOLID) {
+            dist[i] = 0;
+            frontier.push_back(i);
+        }
+    for (int d = 1; d < 255 && !frontier.empty(); d++) {
+        next.clear();
+        for (long long c : frontier) {
+            const int y = (int)(c / NX), x = (int)(c - (long long)y * NX);
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int tx = x + dx, ty = y + dy;
+                    if (per_x) tx = (tx + NX) % NX;
+                    if (per_y) ty = (ty + NY) % NY;
+                    if (tx < 0 || tx >= NX || ty < 0 || ty >= NY) continue;
+                    const long long t = (long long)ty * NX + tx;
+                    if (dist[t] == 255) {
+                        dist[t] = (uint8_t)d;
+                        next.push_back(t);
+                    }
+                }
+        }
+        frontier.swap(next);
+    }
+    return dist;
 }
 
 template <class T>
@@ -363,6 +401,10 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         return fail(nullptr, LELBM_E_NOMEM, "cudaMalloc of %zu bytes failed", 2 * bytes);
     }
     rc = upload(h, &h->d_type, type);
+    if (!rc && D == 2 && std::find(type.begin(), type.end(), (uint8_t)CELL_SOLID) != type.end()) {
+        rc = upload(h, &h->d_wall_dist, wall_distance(type, h->NX, h->NY, g.periodic[0], g.periodic[1]));
+        g.wall_dist = h->d_wall_dist;
+    }
     if (!rc) rc = upload(h, &h->d_pad_cell, pad_cell);
     if (!rc) rc = upload(h, &h->d_pad_src, pad_src);
     if (!rc && cudaMalloc((void**)&h->d_stats, sizeof(DevStats)) != cudaSuccess) rc = LELBM_E_NOMEM;
@@ -536,6 +578,7 @@ static int read_stats(lelbm* h, lelbm_stats* s) {
         s->points_32 = (long long)d.points_32;
         s->judge_redo = (long long)d.judge_redo;
         s->mlp_retry = (long long)d.mlp_retry;
+        s->wall_hits = (long long)d.wall_hits;
     }
     return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
 }

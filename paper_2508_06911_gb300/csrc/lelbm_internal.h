@@ -1,5 +1,6 @@
-// Internal declarations shared by the two translation units of liblelbm:
-// lelbm_step.cu (device code) and lelbm_api.cu (the C ABI, host side).
+// Internal declarations shared by the translation units of liblelbm: the device
+// code (lelbm_step.cu, lelbm_cell.cu, lelbm_batch.cu, lelbm_noalloc.cu,
+// lelbm_mlp.cu) and the C ABI (lelbm_api.cu, host side).
 #pragma once
 
 #include <cstdint>
@@ -43,6 +44,8 @@ struct Geometry {
     const int* inst_of_cell;     // 1D: instance of every cell
     const long long* inst_lo;    // 1D: first interior cell of each instance
     const int* inst_n;           // 1D: interior length of each instance
+    const uint8_t* wall_dist;    // 2D with solids: Chebyshev distance (cells) from each
+                                 // cell to the nearest solid cell, capped at 255; else null
 };
 
 // Device-side counters (all 64-bit, updated with atomics).
@@ -60,6 +63,7 @@ struct DevStats {
     unsigned long long points_32;      // stencil points of FP32 Newton passes (mixed path)
     unsigned long long judge_redo;     // mixed path: cells whose FP64 check failed and were re-solved
     unsigned long long mlp_retry;      // cells whose learned start failed and were re-solved from Eq. IID13
+    unsigned long long wall_hits;      // streamed populations reflected at a solid face (Sec. III.B)
 };
 
 void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, long long ncell,
@@ -79,5 +83,22 @@ void launch_batch_persistent(const Model& m, const Geometry& g, const double inl
                              const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, bool mixed,
                              cudaStream_t s);
 int batch_persistent_max_blocks_per_sm(bool mixed, int threads);
+
+// One object file per kernel variant (lelbm_cell.cu, lelbm_batch.cu).
+template <int D, bool MIXED>
+struct CellVariant {
+    static void launch(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, double* Mout,
+                       DevStats* st, unsigned long long* work, int blocks, size_t smem, cudaStream_t s);
+    static int blocks_per_sm();
+};
+
+template <bool MIXED>
+struct BatchVariant {
+    static void launch(const Model& m, const Geometry& g, const double inlet[4], int bc_left_inflow,
+                       int bc_right_inflow, const uint8_t* type, double* A, double* B, DevStats* st,
+                       unsigned long long* work, const int* order, const long long* inst_first, const int* inst_pad,
+                       int* steps_left, int nsteps, int blocks, int threads, size_t smem, cudaStream_t s);
+    static int blocks_per_sm(int threads);
+};
 
 }  // namespace lbm

@@ -1,0 +1,737 @@
+// Device code of the LELBM time step (arXiv:2508.06911) for sm_103a: the fused
+// single-cell kernel templates.  Each (dimension, precision) variant of the
+// cell-update kernel and each precision of the persistent 1D batch kernel is
+// instantiated in its own object (lelbm_cell.cu, lelbm_batch.cu) so that the
+// variants compile in parallel.
+//
+// One thread owns one cell for the whole single-cell operation (Fig. 5):
+// collision module -> LAS module -> EPR module -> MS module.  The velocity set
+// is never stored: it is re-enumerated row by row for every Newton pass and for
+// the streaming pass, so a cell needs registers only, whatever its temperature
+// (the memory-constant property of moment streaming, Sec. II.E).
+//
+// The EPR Newton works in thermal units t = (c - u) / sqrt(RT): the monomials
+// T_j(t) are O(1) at any temperature, the Jacobian is well scaled, and the
+// residual tested against the tolerance is the paper's residual divided by
+// sqrt(RT)^order.  Rounding-sensitive decisions (macroscopic variables,
+// acoustic radius, refinement levels, stencil membership) use explicitly
+// rounded operations so they do not depend on FMA contraction.
+
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "lelbm_device.cuh"
+#include "lelbm_internal.h"
+#include "lelbm_mlp.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// The fused single-cell kernel.
+// ---------------------------------------------------------------------------
+struct LocalStats {
+    unsigned long long q_max;
+    double disp_max2;
+    unsigned long long points;
+    long long walls;  // populations reflected at solid faces (an undone deposit counts -1)
+};
+
+// Landing cell of an integer displacement (dx, dy) from the emitting cell, or -1
+// when the population leaves the interior of its instance (Sec. III: discarded).
+template <int D>
+__device__ __forceinline__ long long land(const Geometry& g, long long cell, long long lo, int n, int ix, int iy,
+                                          int dx, int dy) {
+    if constexpr (D == 1) {
+        long long x = cell + dx;
+        if (g.periodic[0]) {
+            long long r = (x - lo) % n;
+            if (r < 0) r += n;
+            return lo + r;
+        }
+        return (x < lo || x >= lo + n) ? -1 : x;
+    } else {
+        int tx = ix + dx, ty = iy + dy;
+        if (g.periodic[0]) {
+            tx %= g.nx;
+            if (tx < 0) tx += g.nx;
+        } else if (tx < g.pad || tx >= g.pad + g.nx) {
+            return -1;
+        }
+        if (g.periodic[1]) {
+            ty %= g.ny;
+            if (ty < 0) ty += g.ny;
+        } else if (ty < g.pad || ty >= g.pad + g.ny) {
+            return -1;
+        }
+        return (long long)ty * g.NX + tx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Solid boundary, Sec. III.B (stationary adiabatic slip wall, 2D).
+// ---------------------------------------------------------------------------
+// Is padded cell (i, j) solid?  Periodic axes wrap; cells off the array are not.
+__device__ __forceinline__ bool solid_at(const Geometry& g, const uint8_t* type, int i, int j) {
+    if (g.periodic[0]) {
+        i %= g.NX;
+        if (i < 0) i += g.NX;
+    }
+    if (g.periodic[1]) {
+        j %= g.NY;
+        if (j < 0) j += g.NY;
+    }
+    if (i < 0 || i >= g.NX || j < 0 || j >= g.NY) return false;
+    return type[(long long)j * g.NX + i] == CELL_SOLID;
+}
+
+// End of the path x -> x + c past solid cells: the path is walked face by face and at
+// a face of a solid cell the velocity component normal to it is reversed (specular
+// reflection), until the displacement |c| is used up.  Positions are exact integers in
+// units of 1/64 cell: along each axis the faces lie at unfolded distances 32 + 64 k,
+// and which of two faces comes first is decided by cross-multiplication, so ties (a
+// path through a cell corner) are exact.  Through a corner whose diagonal cell is
+// solid, only the normal of a flat wall (exactly one side cell solid) is reversed,
+// otherwise both.  The walk ends after at most |c_x| + |c_y| + 2 face events.
+struct WallLanding {
+    int i, j;        // final (fluid) cell, unwrapped padded coordinates
+    double off[2];   // landing point relative to its centre, each in (-1/2, 1/2]
+    double cs[2];    // reflected velocity c*
+    bool touched;    // reflected at least once
+};
+
+__device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8_t* type, int ix, int iy,
+                                                  const double* c) {
+    constexpr long long S = 64;
+    const long long qx = llround((double)S * c[0]), qy = llround((double)S * c[1]);
+    int sx = (qx > 0) - (qx < 0), sy = (qy > 0) - (qy < 0);
+    const long long ax = qx < 0 ? -qx : qx, ay = qy < 0 ? -qy : qy;
+    int i = ix, j = iy;
+    bool touched = false;
+    long long kx = 0, ky = 0;
+    while (true) {
+        const long long Xn = S / 2 + S * kx, Yn = S / 2 + S * ky;
+        const bool hx = ax > 0 && Xn < ax, hy = ay > 0 && Yn < ay;
+        if (!hx && !hy) break;
+        bool stx = hx, sty = hy;
+        if (hx && hy) {
+            const long long l = Xn * ay, r = Yn * ax;
+            stx = l <= r;
+            sty = r <= l;
+        }
+        if (stx && sty) {
+            if (!solid_at(g, type, i + sx, j + sy)) {
+                i += sx;
+                j += sy;
+            } else {
+                const bool sa = solid_at(g, type, i + sx, j), sb = solid_at(g, type, i, j + sy);
+                touched = true;
+                if (sa && !sb) {
+                    sx = -sx;
+                    j += sy;
+                } else if (sb && !sa) {
+                    sy = -sy;
+                    i += sx;
+                } else {
+                    sx = -sx;
+                    sy = -sy;
+                }
+            }
+        } else {
+            const int ti = i + (stx ? sx : 0), tj = j + (sty ? sy : 0);
+            if (solid_at(g, type, ti, tj)) {
+                if (stx) sx = -sx;
+                if (sty) sy = -sy;
+                touched = true;
+            } else {
+                i = ti;
+                j = tj;
+            }
+        }
+        kx += stx;
+        ky += sty;
+    }
+    WallLanding L;
+    L.i = i;
+    L.j = j;
+    L.off[0] = (double)sx * (double)(ax - S * kx) * (1.0 / S);
+    L.off[1] = (double)sy * (double)(ay - S * ky) * (1.0 / S);
+    L.cs[0] = (double)sx * fabs(c[0]);
+    L.cs[1] = (double)sy * fabs(c[1]);
+    L.touched = touched;
+    return L;
+}
+
+// Adds the raw moments T_N(cp) mf and T_N(cp) mg (2D) to cell tgt of Mout.
+__device__ __forceinline__ void add_moments_2d(double* Mout, long long ncell, long long tgt, const double* cp,
+                                               double mf, double mg) {
+    const double csq = cp[0] * cp[0] + cp[1] * cp[1];
+    const double dM[11] = {mf,           cp[0] * mf,          cp[1] * mf,          cp[0] * cp[0] * mf,
+                           cp[0] * cp[1] * mf, cp[1] * cp[1] * mf, csq * cp[0] * mf, csq * cp[1] * mf,
+                           mg,           cp[0] * mg,          cp[1] * mg};
+#pragma unroll
+    for (int mm = 0; mm < 11; mm++) atomicAdd(Mout + mm * ncell + tgt, dM[mm]);
+}
+
+// Streams one population of cell (ix, iy) with velocity cp past the solid cells (2D):
+// its path is traced, the landing point is shared between cells by cloud-in-cell
+// weights, and a share that would fall on a solid cell is mirrored back across the wall
+// with the normal component of its velocity reversed (into the side cell behind a flat
+// wall, into the final cell behind a corner of solid cells).  Returns whether the path
+// was reflected.  Kept out of line: only cells near a solid cell take this path.
+static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8_t* type, double* Mout, int ix, int iy,
+                                           const double* cp, double mf, double mg) {
+    const WallLanding L = trace_path(g, type, ix, iy, cp);
+    const double pos[2] = {(double)L.i + L.off[0], (double)L.j + L.off[1]};
+    int base[2];
+    double w1[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const double fl = floor(pos[a]);
+        base[a] = (int)fl;
+        w1[a] = pos[a] - fl;
+    }
+    const int ncx = w1[0] > 0.0 ? 2 : 1, ncy = w1[1] > 0.0 ? 2 : 1;
+    for (int sy = 0; sy < ncy; sy++)
+        for (int sx = 0; sx < ncx; sx++) {
+            const double w = (sx ? w1[0] : 1.0 - w1[0]) * (sy ? w1[1] : 1.0 - w1[1]);
+            int tx = base[0] + sx, ty = base[1] + sy;
+            double cw[2] = {L.cs[0], L.cs[1]};
+            if (solid_at(g, type, tx, ty)) {
+                bool ox = tx != L.i, oy = ty != L.j;
+                if (ox && oy) {
+                    const bool sa = solid_at(g, type, tx, L.j), sb = solid_at(g, type, L.i, ty);
+                    if (!sa && sb) ox = false;
+                    else if (sa && !sb) oy = false;
+                }
+                if (ox) {
+                    cw[0] = -cw[0];
+                    tx = L.i;
+                }
+                if (oy) {
+                    cw[1] = -cw[1];
+                    ty = L.j;
+                }
+            }
+            const long long tgt = land<2>(g, 0, 0, 0, ix, iy, tx - ix, ty - iy);
+            if (tgt >= 0 && type[tgt] == CELL_FLUID) add_moments_2d(Mout, g.ncell, tgt, cw, w * mf, w * mg);
+        }
+    return L.touched;
+}
+
+// Moment streaming, Eq. (IIE3): T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i added at
+// x + c_i.  Level-0 points land on one cell; refined points are shared between the
+// cells they overlap (cloud-in-cell).
+//
+// With CHECK, the same pass also accumulates the moments of degree <= 3 (fluons)
+// and <= 2 (phonons) of the deposited populations and returns whether their
+// residual against conF / conG is within the tolerance (the FP64 judge of the
+// mixed path).  sign = -1 removes a previous deposit of the same populations.
+template <int D, bool CHECK>
+__device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                             long long cell, const CellState<D>& c, const Stencil<D>& st,
+                                             const double* lf, const double* lg, LocalStats& ls, double sign = 1.0,
+                                             const double* conF = nullptr, const double* conG = nullptr) {
+    constexpr int NM = Dim<D>::NM;
+    constexpr int RF = D == 1 ? 4 : 10, RG = D == 1 ? 3 : 6;  // monomials of degree <= 3 / <= 2
+    const bool has_g = m.K > 0.0;
+    const double mfs = sign * c.rho;               // rho dV f'
+    const double mgs = sign * c.rho * m.K * c.RT;  // rho K RT dV g'
+    double RFm[RF], RGm[RG];
+    if constexpr (CHECK) {
+#pragma unroll
+        for (int i = 0; i < RF; i++) RFm[i] = 0.0;
+#pragma unroll
+        for (int i = 0; i < RG; i++) RGm[i] = 0.0;
+    }
+    long long lo = 0;
+    int n = 0, ix = 0, iy = 0;
+    if constexpr (D == 1) {
+        const int b = g.inst_of_cell[cell];
+        lo = g.inst_lo[b];
+        n = g.inst_n[b];
+    } else {
+        iy = (int)(cell / g.NX);
+        ix = (int)(cell - (long long)iy * g.NX);
+    }
+    unsigned long long q = 0;
+    long long walls = 0;
+    double dmax2 = 0.0;
+    // Sec. III.B: paths are traced past solid faces only where a solid cell lies within
+    // reach: a path or a cloud-in-cell share touches cells at Chebyshev distance at
+    // most max_a |c_a| + 1, and |c_a| <= |u_a| + R_ac + 1/2.
+    bool near_wall = false;
+    if constexpr (D == 2) {
+        if (g.wall_dist)
+            near_wall = (double)g.wall_dist[cell] <= fmax(fabs(c.u[0]), fabs(c.u[1])) + (double)st.R + 1.5;
+    }
+    auto deposit = [&](long long tgt, const double* cp, double mf, double mg) {
+        if (tgt < 0 || type[tgt] != CELL_FLUID) return;
+        double csq = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) csq += cp[a] * cp[a];
+        double dM[NM];
+        dM[0] = mf;
+#pragma unroll
+        for (int a = 0; a < D; a++) dM[1 + a] = cp[a] * mf;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++) dM[iM2<D>(a, b)] = cp[a] * cp[b] * mf;
+#pragma unroll
+        for (int gg = 0; gg < D; gg++) dM[iMD<D>(gg)] = csq * cp[gg] * mf;
+        dM[iG0<D>()] = mg;
+#pragma unroll
+        for (int gg = 0; gg < D; gg++) dM[iG1<D>(gg)] = cp[gg] * mg;
+#pragma unroll
+        for (int mm = 0; mm < NM; mm++) atomicAdd(Mout + mm * g.ncell + tgt, dM[mm]);
+    };
+    auto deposit_traced = [&](const double* cp, double mf, double mg) {
+        if constexpr (D == 2) walls += stream_traced(g, type, Mout, ix, iy, cp, mf, mg) ? (sign > 0.0 ? 1 : -1) : 0;
+    };
+    auto row = [&](int cy, int xa, int xb) {
+        double y = 0.0;
+        if constexpr (D == 2) y = ((double)cy - c.u[1]) * c.inv_sig;
+        double cf[4], cg[3];
+        row_coeffs<D>(lf, lg, y, cf, cg);
+        double SF[4] = {0.0, 0.0, 0.0, 0.0}, SG[3] = {0.0, 0.0, 0.0};
+        auto point = [&](int k, double x, double f, double gp) {
+            const int cx = xa + k;
+            if constexpr (CHECK) {
+                const double x2 = x * x;
+                SF[0] += f;
+                SF[1] += x * f;
+                SF[2] += x2 * f;
+                SF[3] += x2 * x * f;
+                SG[0] += gp;
+                SG[1] += x * gp;
+                SG[2] += x2 * gp;
+            }
+            double cp[D];
+            cp[0] = (double)cx;
+            if constexpr (D == 2) cp[1] = (double)cy;
+            if (near_wall)
+                deposit_traced(cp, mfs * f, mgs * gp);
+            else
+                deposit(land<D>(g, cell, lo, n, ix, iy, cx, cy), cp, mfs * f, mgs * gp);
+        };
+        row_eval(cf, cg, true, has_g, ((double)xa - c.u[0]) * c.inv_sig, c.inv_sig, xb - xa + 1, point);
+        if constexpr (CHECK) {
+            // fold y^b into the moments x^a y^b (a + b <= 3 / <= 2)
+            double yp[4] = {1.0, y, y * y, y * y * y};
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 3 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 3; a++) RFm[tix(a, b, 3)] += SF[a] * yp[b];
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 2 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 2; a++) RGm[tix(a, b, 2)] += SG[a] * yp[b];
+        }
+        q += (unsigned long long)(xb - xa + 1);
+        const double ex = (double)(abs(xa) > abs(xb) ? xa : xb);
+        dmax2 = fmax(dmax2, ex * ex + (double)cy * (double)cy);
+    };
+    auto leaf = [&](const double* cp, double dC) {
+        const double x = (cp[0] - c.u[0]) * c.inv_sig;
+        double y = 0.0;
+        if constexpr (D == 2) y = (cp[1] - c.u[1]) * c.inv_sig;
+        double cf[4], cg[3];
+        row_coeffs<D>(lf, lg, y, cf, cg);
+        const double f = dC * exp(-(((cf[3] * x + cf[2]) * x + cf[1]) * x + cf[0]));
+        const double gp = has_g ? dC * exp(-((cg[2] * x + cg[1]) * x + cg[0])) : 0.0;
+        const double mf = mfs * f, mg = mgs * gp;
+        if constexpr (CHECK) {
+            double px[4] = {1.0, x, x * x, x * x * x}, py[4] = {1.0, y, y * y, y * y * y};
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 3 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 3; a++) RFm[tix(a, b, 3)] += px[a] * py[b] * f;
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? 2 : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= 2; a++) RGm[tix(a, b, 2)] += px[a] * py[b] * gp;
+        }
+        q++;
+        double csq = 0.0;
+        int base[D];
+        double w1[D];
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            csq += cp[a] * cp[a];
+            const double fl = floor(cp[a]);
+            base[a] = (int)fl;
+            w1[a] = cp[a] - fl;
+        }
+        dmax2 = fmax(dmax2, csq);
+        if (near_wall) {
+            deposit_traced(cp, mf, mg);
+            return;
+        }
+        const int ncx = w1[0] > 0.0 ? 2 : 1;
+        const int ncy = (D == 2 && w1[D - 1] > 0.0) ? 2 : 1;
+        for (int sy = 0; sy < ncy; sy++)
+            for (int sx = 0; sx < ncx; sx++) {
+                double w = sx ? w1[0] : 1.0 - w1[0];
+                if constexpr (D == 2) w *= sy ? w1[1] : 1.0 - w1[1];
+                deposit(land<D>(g, cell, lo, n, ix, iy, base[0] + sx, D == 2 ? base[D - 1] + sy : 0), cp, w * mf,
+                        w * mg);
+            }
+    };
+    st.for_each_row(row, leaf);
+    if (q > ls.q_max) ls.q_max = q;
+    ls.points += q;
+    ls.walls += walls;
+    ls.disp_max2 = fmax(ls.disp_max2, dmax2);
+    if constexpr (CHECK) {
+        double rmax = 0.0;
+        bool finite = true;
+#pragma unroll
+        for (int j = 0; j < RF; j++) {
+            const double r = RFm[tix(bx<D, true>(j), by<D, true>(j), 3)] - conF[j];
+            finite = finite && isfinite(r);
+            rmax = fmax(rmax, fabs(r));
+        }
+        if (has_g) {
+#pragma unroll
+            for (int j = 0; j < RG; j++) {
+                const double r = RGm[tix(bx<D, false>(j), by<D, false>(j), 2)] - conG[j];
+                finite = finite && isfinite(r);
+                rmax = fmax(rmax, fabs(r));
+            }
+        }
+        return finite && rmax <= m.tol;
+    }
+    return true;
+}
+
+// Per-block counters in shared memory, flushed to DevStats once per block.
+struct BlockCounters {
+    unsigned long long hist[64];
+    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls;
+};
+
+// Per-thread tallies.
+struct ThreadCounters {
+    unsigned long long cells, pf, pg, p32, redo, retry;
+    LocalStats ls;
+};
+
+__device__ __forceinline__ void counters_init(BlockCounters& bc) {
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
+    if (threadIdx.x == 0)
+        bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = bc.retry =
+            bc.walls = 0;
+}
+
+// Adds the thread tallies to the block counters, then (after a barrier) the block
+// counters to the device counters.  Every thread of the block must call it.
+__device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCounters& tc, DevStats* stats) {
+    atomicAdd(&bc.cells, tc.cells);
+    atomicAdd(&bc.p32, tc.p32);
+    atomicAdd(&bc.redo, tc.redo);
+    atomicAdd(&bc.retry, tc.retry);
+    atomicAdd(&bc.pf, tc.pf);
+    atomicAdd(&bc.pg, tc.pg);
+    atomicAdd(&bc.pm, tc.ls.points);
+    if (tc.ls.walls) atomicAdd(&bc.walls, (unsigned long long)tc.ls.walls);
+    atomicMax(&bc.q, tc.ls.q_max);
+    atomicMax(&bc.dmax, (unsigned long long)__double_as_longlong(sqrt(tc.ls.disp_max2)));
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        if (bc.hist[i]) atomicAdd(&stats->newton_hist[i], bc.hist[i]);
+    if (threadIdx.x == 0) {
+        atomicAdd(&stats->cells, bc.cells);
+        atomicAdd(&stats->points_f, bc.pf);
+        atomicAdd(&stats->points_g, bc.pg);
+        atomicAdd(&stats->points_ms, bc.pm);
+        atomicAdd(&stats->points_32, bc.p32);
+        if (bc.redo) atomicAdd(&stats->judge_redo, bc.redo);
+        if (bc.retry) atomicAdd(&stats->mlp_retry, bc.retry);
+        if (bc.walls) atomicAdd(&stats->wall_hits, bc.walls);
+        if (bc.feq) atomicAdd(&stats->fallback_eq, bc.feq);
+        if (bc.fmx) atomicAdd(&stats->fallback_mx, bc.fmx);
+        atomicMax(&stats->q_max, bc.q);
+        atomicMax(&stats->disp_max_bits, bc.dmax);
+    }
+}
+
+// The single-cell operation of Fig. 5 in two halves around the (warp-wide) warm-start
+// network: prepare_cell loads the moments, runs the collision module and sets up the
+// stencil; finish_cell runs EPR (with the fallbacks) and moment streaming into Mout.
+template <int D>
+__device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, const double* __restrict__ Min,
+                                             DevStats* stats, long long cell, BlockCounters& bc, CellState<D>& c,
+                                             Stencil<D>& st) {
+    constexpr int NM = Dim<D>::NM;
+    double M[NM];
+#pragma unroll
+    for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
+    collide<D>(M, m, c);
+    if (!c.ok) {  // non-physical cell: nothing can be reconstructed
+        atomicAdd(&bc.fmx, 1ull);
+        atomicMin(&stats->first_fail, (unsigned long long)cell);
+        return false;
+    }
+    st.init(c, m);
+    return true;
+}
+
+// dl: the learned correction of the Maxwellian start (fluons then phonons), or null.
+template <int D, bool MIXED>
+__device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                            DevStats* stats, long long cell, BlockCounters& bc, ThreadCounters& tc,
+                                            double* conF, double* conG, const CellState<D>& c, const Stencil<D>& st,
+                                            const float* dl) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    tc.cells++;
+    const bool has_g = m.K > 0.0;
+    double lf[NF], lg[NG];
+    maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+    bool learned = false;
+    if (dl) {
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < MlpDims<D>::NOUT; k++) ok = ok && isfinite(dl[k]);
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf[j] += (double)dl[j];
+            if (has_g) {
+#pragma unroll
+                for (int j = 0; j < NG; j++) lg[j] += (double)dl[NF + j];
+            }
+            learned = true;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
+#pragma unroll
+    for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
+    int sf, sg;
+    if constexpr (MIXED) {
+        if (solve_fg_mixed<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
+            // stream and judge in one FP64 pass; on a miss, take the deposit back and
+            // finish the solve in FP64 from the current multipliers
+            if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
+                atomicAdd(&bc.hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
+                return;
+            }
+            scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
+            tc.redo++;
+        } else {
+            if (learned) tc.retry++;
+            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+            learned = false;
+        }
+    }
+    solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+    if ((sf < 0 || sg < 0) && learned) {  // the plain EPR is the fallback of the learned start
+        tc.retry++;
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+    }
+    if (sf >= 0 && sg >= 0) {
+        atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
+        if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+        if (m.rec_x) {  // training pairs: features and converged multipliers minus Eq. (IID13)
+            float xin[MlpDims<D>::NIN];
+            mlp_features<D>(c, st, xin);
+            double mf[NF], mg[NG];
+            maxwell_start_fg<D, NF, NG>(c.RT, mf, mg);
+#pragma unroll
+            for (int k = 0; k < MlpDims<D>::NIN; k++) m.rec_x[cell * MlpDims<D>::NIN + k] = xin[k];
+#pragma unroll
+            for (int j = 0; j < NF; j++) m.rec_y[cell * MlpDims<D>::NOUT + j] = (float)(lf[j] - mf[j]);
+#pragma unroll
+            for (int j = 0; j < NG; j++) m.rec_y[cell * MlpDims<D>::NOUT + NF + j] = has_g ? (float)(lg[j] - mg[j]) : 0.f;
+        }
+    } else {
+        // equilibrium constraints (omega = 1) for both populations
+#pragma unroll
+        for (int j = 0; j < NF; j++) conF[j] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NG; j++) conG[j] = 0.0;
+        conF[0] = conG[0] = 1.0;
+        int jj = 1 + D;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++) {
+                conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
+                jj++;
+            }
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+        if (sf >= 0 && sg >= 0) {
+            atomicAdd(&bc.feq, 1ull);
+        } else {
+            // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S (mass exact)
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf[j] = 0.0;
+            lf[0] = -1.0;
+            jj = 1 + D;
+#pragma unroll
+            for (int a = 0; a < D; a++)
+#pragma unroll
+                for (int b = a; b < D; b++) {
+                    lf[jj] = (a == b) ? 0.5 : 0.0;
+                    jj++;
+                }
+            double MF[MomentSet<D>::NF], MG[MomentSet<D>::NG];
+            moment_pass<D>(c, st, lf, lg, true, false, MF, MG);
+            lf[0] = log(MF[0]) - 1.0;
+#pragma unroll
+            for (int j = 0; j < NG; j++) lg[j] = lf[j];
+            atomicAdd(&bc.fmx, 1ull);
+            atomicMin(&stats->first_fail, (unsigned long long)cell);
+        }
+    }
+    scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls);
+}
+
+// One time step of the whole padded grid: warps claim chunks of 32 consecutive cells
+// from a global counter (the cost of a cell varies with its temperature, q ~
+// (n sqrt RT)^D, so a static split leaves SMs idle at the end).
+template <int D, bool MIXED>
+__global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
+                                                          const double* __restrict__ Min, double* Mout,
+                                                          DevStats* stats, unsigned long long* work) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    __shared__ BlockCounters bc;
+    __shared__ double s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
+    extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
+    double* conF = s_con[threadIdx.x];
+    double* conG = conF + NF;
+    counters_init(bc);
+    const bool mlp = m.mlp_w != nullptr;
+    if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
+    __syncthreads();
+    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}};
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(work, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)g.ncell) break;
+        const long long cell = (long long)base + lane;
+        const bool active = cell < g.ncell && type[cell] != CELL_SOLID;
+        CellState<D> c;
+        Stencil<D> st;
+        bool ok = false;
+        if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
+        float dl[MlpDims<D>::NOUT];
+        if (mlp) {  // warp-uniform: every lane takes part in the tensor-core inference
+            float xin[MlpDims<D>::NIN];
+            if (ok) mlp_features<D>(c, st, xin);
+            warp_mlp<D>(s_mlp, xin, ok, dl);
+        }
+        if (ok) finish_cell<D, MIXED>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
+    }
+    counters_flush(bc, tc, stats);
+}
+
+// Persistent 1D batch: a block claims a whole instance from the queue (order[]) and
+// runs all of its steps with block barriers only -- instances share no cells, so no
+// grid-wide barrier is needed.  Each step fills the instance's pads (Sec. III.A),
+// zeroes its block of the next buffer, then lets its warps claim 32-cell chunks from
+// a shared counter.  An instance that ends on an odd step copies its block back, so
+// every instance finishes in buffer A.  steps_left[] (may be null: unlimited) caps
+// each instance and is decremented.
+template <bool MIXED>
+__global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry g, double in0, double in1,
+                                                               double in3, int bc_left_inflow, int bc_right_inflow,
+                                                               const uint8_t* __restrict__ type, double* A, double* B,
+                                                               DevStats* stats, unsigned long long* work,
+                                                               const int* order, const long long* inst_first,
+                                                               const int* inst_pad, int* steps_left, int nsteps) {
+    constexpr int D = 1, NM = Dim<1>::NM, NF = Dim<1>::NF, NG = Dim<1>::NG;
+    __shared__ BlockCounters bc;
+    __shared__ double s_con[128][NF + NG];
+    __shared__ unsigned int s_next;
+    __shared__ int s_inst;
+    extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
+    double* conF = s_con[threadIdx.x];
+    double* conG = conF + NF;
+    counters_init(bc);
+    const bool mlp = m.mlp_w != nullptr;
+    if (mlp) mlp_stage_mma<1>(s_mlp, m.mlp_w, m.mlp_nrm);
+    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}};
+    const int lane = threadIdx.x & 31;
+    double Meq[NM];
+    {
+        const double uin[1] = {in1};
+        eq_moments<1>(m.K, in0, uin, in3, Meq);
+    }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned long long k = atomicAdd(work, 1ull);
+            s_inst = k < (unsigned long long)g.n_inst ? order[k] : -1;
+        }
+        __syncthreads();
+        const int b = s_inst;
+        if (b < 0) break;
+        const int n = g.inst_n[b];
+        const int pad = inst_pad[b];
+        const long long lo = g.inst_lo[b];
+        const long long first = inst_first[b];
+        const int nblk = n + 2 * pad;
+        int k = nsteps;
+        if (steps_left) k = min(k, steps_left[b]);
+        for (int s = 0; s < k; s++) {
+            const double* Min = (s & 1) ? B : A;
+            double* Mout = (s & 1) ? A : B;
+            // pads, then a zeroed output block
+            for (int i = threadIdx.x; i < 2 * pad; i += blockDim.x) {
+                const bool left = i < pad;
+                const long long cell = left ? first + i : lo + n + (i - pad);
+                double* Mw = const_cast<double*>(Min);
+                if (left ? bc_left_inflow : bc_right_inflow) {
+#pragma unroll
+                    for (int q = 0; q < NM; q++) Mw[q * g.ncell + cell] = Meq[q];
+                } else {
+                    const long long src = left ? lo : lo + n - 1;
+#pragma unroll
+                    for (int q = 0; q < NM; q++) Mw[q * g.ncell + cell] = Min[q * g.ncell + src];
+                }
+            }
+            for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+#pragma unroll
+                for (int q = 0; q < NM; q++) Mout[q * g.ncell + first + i] = 0.0;
+            if (threadIdx.x == 0) s_next = 0;
+            __syncthreads();
+            for (;;) {
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(&s_next, 32u);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= (unsigned int)nblk) break;
+                const int i = (int)base + lane;
+                const long long cell = first + i;
+                const bool active = i < nblk && type[cell] != CELL_SOLID;
+                CellState<D> c;
+                Stencil<D> st;
+                bool ok = false;
+                if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
+                float dl[MlpDims<D>::NOUT];
+                if (mlp) {
+                    float xin[MlpDims<D>::NIN];
+                    if (ok) mlp_features<D>(c, st, xin);
+                    warp_mlp<D>(s_mlp, xin, ok, dl);
+                }
+                if (ok)
+                    finish_cell<D, MIXED>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
+            }
+            __syncthreads();
+        }
+        if (k & 1) {  // the result is in B: copy the block back to A
+            for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+#pragma unroll
+                for (int q = 0; q < NM; q++) A[q * g.ncell + first + i] = B[q * g.ncell + first + i];
+        }
+        if (steps_left && threadIdx.x == 0) steps_left[b] -= k;
+    }
+    counters_flush(bc, tc, stats);
+}
+
+}  // namespace lbm

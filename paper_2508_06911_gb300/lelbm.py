@@ -73,6 +73,7 @@ class lelbm_stats(ctypes.Structure):
         ("points_32", ctypes.c_longlong),
         ("judge_redo", ctypes.c_longlong),
         ("mlp_retry", ctypes.c_longlong),
+        ("wall_hits", ctypes.c_longlong),
     ]
 
 

@@ -304,3 +304,28 @@ def random_smooth_2d(nx: int, ny: int, seed_index: int, RT_lo: float, RT_hi: flo
     p = 0 if periodic else max(pad, pad_for(umax, RT_hi * 1.5))
     return Grid2D(nx=nx, ny=ny, rho=rho, u=u, RT=RT, bc=bc, pad=p, K=internal_dof(GAMMA, 2), nu=5e-3,
                   Pr=0.71, steps=1, name=f"smooth2d_{nx}x{ny}")
+
+
+def cylinder_2d(nx: int = 2048, ny: int = 1024, diameter: int = 128, mach: float = 3.0, rho: float = 1.4,
+                p: float = 1.0, RT_lattice: float = 0.5, steps: int = 20000) -> Grid2D:
+    """Supersonic flow past a circular cylinder with a slip wall (Sec. V.G): inviscid
+    (nu = kappa = 0), uniform inflow (rho, p) at the given Mach number on the x- side,
+    outflow on the other three, impulsive start (the inflow state everywhere).  The
+    cylinder is the set of cells whose centres lie within diameter / 2 of (nx / 4, ny / 2)
+    (a legoland mask).  Acoustic scaling puts the free stream at lattice RT_lattice."""
+    RT = p / rho
+    s = math.sqrt(RT_lattice / RT)
+    u_lat = mach * math.sqrt(GAMMA * RT) * s
+    xc, yc = (np.arange(nx) + 0.5), (np.arange(ny) + 0.5)
+    X, Y = np.meshgrid(xc, yc)
+    solid = ((X - nx / 4) ** 2 + (Y - ny / 2) ** 2 <= (diameter / 2) ** 2).astype(np.uint8)
+    # stagnation temperature bounds the post-shock temperature
+    RT_max = RT_lattice * (1.0 + 0.5 * (GAMMA - 1.0) * mach * mach)
+    pad = pad_for(u_lat * 1.3, RT_max * 1.5)
+    rho_f = np.full((ny, nx), rho)
+    u = np.zeros((2, ny, nx))
+    u[0] = u_lat
+    RT_f = np.full((ny, nx), RT_lattice)
+    return Grid2D(nx=nx, ny=ny, rho=rho_f, u=u, RT=RT_f, bc=(1, 0, 0, 0), pad=pad, K=internal_dof(GAMMA, 2),
+                  nu=0.0, Pr=0.71, steps=steps, inlet=(rho, u_lat, 0.0, RT_lattice), solid=solid,
+                  name=f"cylinder2d_{nx}x{ny}_D{diameter}_Ma{mach:g}")
