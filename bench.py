@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--n-batch", type=int, default=4096)
     ap.add_argument("--n", type=int, default=1024, help="2D grid size")
     ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default persistent launch shape")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell"],
@@ -258,7 +258,7 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     D = desc["dims"]
     interior = desc["interior_cells"]
-    prec = {"mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
+    prec = {"fp32": L.LELBM_FP32, "mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
 
     weights = None
     wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", f"warmstart_{D}d.npy")
@@ -321,7 +321,7 @@ def run_ours(args):
     compare = None
     ablation = None
     if not args.no_compare:
-        other = "fp64" if args.precision == "mixed" else "mixed"
+        other = "fp64" if args.precision != "fp64" else "fp32"
         s2 = make(other, learned=False)  # the plain path: Eq. (IID13) start
         ms2, st2, _, _ = timed(s2, False)
         r1 = s.get_moments()[0]
@@ -353,30 +353,43 @@ def run_ours(args):
             compare["points_fp64_newton"] = st2.points_f + st2.points_g
             s4.close()
 
-    # dominant kernel: the fused cell update, FP64-ALU bound
-    # one timed launch covers args.steps steps on the persistent path; work per launch
+    # dominant kernel: the fused cell update, ALU bound (FP64 on the FP64 and mixed paths,
+    # FP32 on the FP32 path); one timed launch covers args.steps steps on the persistent path
     launches = max(st.cell_kernel_launches, 1)
     kern_ms = st.cell_kernel_ms / launches
-    flops = (st.points_f * newton_flops(N_F[D]) + st.points_g * newton_flops(N_G[D]) +
-             st.points_ms * 2 * N_M[D]) / launches
+    flops64 = (st.points_f * newton_flops(N_F[D]) + st.points_g * newton_flops(N_G[D])) / launches
     flops32 = st.points_32 * (newton_flops(N_F[D]) + newton_flops(N_G[D])) / launches
+    flops_ms = st.points_ms * 2 * N_M[D] / launches
+    if args.precision == "fp32":
+        flops32 += flops_ms
+    else:
+        flops64 += flops_ms
     steps_per_launch = args.steps if persistent else 1
     fp64_peak = 1.25e12  # nominal FP64 rate of GB300 (no tensor path for FP64)
-    achieved = flops / (kern_ms / 1e3)
+    fp32_peak = 78.2e12  # FP32 FMA probe on this machine's GB300
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     alg_bytes = (2 * s.n_mom * 8 + 1) * interior * steps_per_launch  # read state + write next + type byte
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.255 measured by an FMA probe)",
-                "kernel": (f"batch_persistent_kernel<{'true' if args.precision == 'mixed' else 'false'}>"
-                           if persistent else
-                           f"cell_update_kernel<{D},{'true' if args.precision == 'mixed' else 'false'}>"),
-                "kernel_ms": kern_ms, "steps_per_launch": steps_per_launch,
-                "fp32_side": {"achieved_tflops": flops32 / (kern_ms / 1e3) / 1e12, "peak_tflops": 78.2,
-                              "peak_source": "FP32 FMA probe on this pool's GB300"},
-                "hbm": {"achieved_gbs": alg_bytes / (kern_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                        "frac": alg_bytes / (kern_ms / 1e3) / 1e9 / hbm_peak,
+    prec_id = {"fp64": 0, "mixed": 1, "fp32": 2}[args.precision]
+    sec = kern_ms / 1e3
+    if args.precision == "fp32":
+        main_side = {"achieved": flops32 / sec / 1e12, "peak": fp32_peak / 1e12,
+                     "peak_source": "FP32 FMA probe on this pool's GB300 (78.2 TFLOP/s)"}
+        other_side = {"fp64_side": {"achieved_tflops": flops64 / sec / 1e12, "peak_tflops": 1.25,
+                                    "note": "FP64 EPR fallback of cells whose FP32 solve failed"}}
+    else:
+        main_side = {"achieved": flops64 / sec / 1e12, "peak": fp64_peak / 1e12,
+                     "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.255 measured by an FMA probe)"}
+        other_side = {"fp32_side": {"achieved_tflops": flops32 / sec / 1e12, "peak_tflops": 78.2,
+                                    "peak_source": "FP32 FMA probe on this pool's GB300"}}
+    roofline = {"bound": "alu", "achieved": main_side["achieved"], "peak": main_side["peak"], "unit": "TFLOP/s",
+                "frac": main_side["achieved"] / main_side["peak"], "traffic": None,
+                "peak_source": main_side["peak_source"],
+                "kernel": (f"batch_persistent_kernel<{prec_id}>" if persistent else
+                           f"cell_update_kernel<{D},{prec_id}>"),
+                "kernel_ms": kern_ms, "steps_per_launch": steps_per_launch, **other_side,
+                "hbm": {"achieved_gbs": alg_bytes / sec / 1e9, "peak_gbs": hbm_peak,
+                        "frac": alg_bytes / sec / 1e9 / hbm_peak,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}}
     hist = list(st.newton_hist)
     solves = sum(hist)
@@ -417,7 +430,7 @@ def run_ours(args):
                 "dtype": "f64" if args.precision == "fp64" else "f32+f64",
                 "data": "synthetic (seeded)",
                 "config": desc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
-                "speedup_vs_fp64": (value / compare["value"]) if (compare and args.precision == "mixed") else None,
+                "speedup_vs_fp64": (value / compare["value"]) if (compare and args.precision != "fp64") else None,
                 "warmstart": "learned" if weights is not None else "maxwell",
                 "ablation_no_mlp": ablation, "points_fp32": st.points_32,
                 "points_fp64_newton": st.points_f + st.points_g, "mlp_retry": st.mlp_retry,

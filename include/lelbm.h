@@ -68,6 +68,15 @@ extern "C" {
                          streaming pass computes the populations in FP64 and checks
                          their FP64 residual against tol (re-solving in FP64 on a
                          miss); state, collision and accumulation in FP64          */
+#define LELBM_FP32 2  /* EPR Newton (passes and solves) and the streaming pass in
+                         FP32, to an FP32 residual of 2e-5 (thermal units) plus one
+                         polishing update; moment fractions widened exactly to FP64
+                         and accumulated in FP64; the emitted mass, momentum and
+                         energy are summed exactly and their shortfall kept in the
+                         emitting cell, so totals are conserved to FP64 rounding.
+                         State, collision and stencil geometry in FP64.  A cell
+                         whose FP32 solve fails is solved by the FP64 EPR.  Error
+                         against LELBM_FP64: about 1e-6 relative per step.         */
 
 typedef struct lelbm* lelbm_t;
 
@@ -93,7 +102,7 @@ typedef struct {
     int max_refine;      /* cap on N_r, 0..4                                           */
     double tol;          /* EPR residual tolerance in thermal units; paper: 1e-12      */
     int max_newton;      /* Newton update cap per solve, 1..60                         */
-    int precision;       /* LELBM_FP64 or LELBM_MIXED                                  */
+    int precision;       /* LELBM_FP64, LELBM_MIXED or LELBM_FP32                      */
     const uint8_t* solid;/* host, one byte per padded cell, 1 = solid; NULL: none.
                             2D interior cells only (flags on pads and in 1D are
                             ignored).  Solid cells are stationary adiabatic slip
@@ -119,8 +128,9 @@ typedef struct {
     long long points_f;           /* stencil points visited by fluon Newton passes  */
     long long points_g;           /* stencil points visited by phonon Newton passes */
     long long points_ms;          /* stencil points streamed (moment streaming)     */
-    long long points_32;          /* stencil points of FP32 Newton passes (mixed)   */
-    long long judge_redo;         /* mixed: cells re-solved in FP64 after the check */
+    long long points_32;          /* stencil points of FP32 Newton passes           */
+    long long judge_redo;         /* mixed: cells re-solved in FP64 after the check;
+                                     FP32: cells whose FP32 solve failed (FP64 EPR) */
     long long mlp_retry;          /* learned start failed; re-solved from Eq. IID13 */
     long long wall_hits;          /* populations specularly reflected at a solid
                                      face while streaming (Sec. III.B)              */

@@ -16,12 +16,15 @@ UNITS = [
     ("lelbm_api.cu", "lelbm_api.o", []),
     ("lelbm_noalloc.cu", "lelbm_noalloc.o", []),
     ("lelbm_mlp.cu", "lelbm_mlp.o", []),
-    ("lelbm_cell.cu", "lelbm_cell_1d_fp64.o", ["-DLBM_D=1", "-DLBM_MIXED=0"]),
-    ("lelbm_cell.cu", "lelbm_cell_1d_mixed.o", ["-DLBM_D=1", "-DLBM_MIXED=1"]),
-    ("lelbm_cell.cu", "lelbm_cell_2d_fp64.o", ["-DLBM_D=2", "-DLBM_MIXED=0"]),
-    ("lelbm_cell.cu", "lelbm_cell_2d_mixed.o", ["-DLBM_D=2", "-DLBM_MIXED=1"]),
-    ("lelbm_batch.cu", "lelbm_batch_fp64.o", ["-DLBM_MIXED=0"]),
-    ("lelbm_batch.cu", "lelbm_batch_mixed.o", ["-DLBM_MIXED=1"]),
+    ("lelbm_cell.cu", "lelbm_cell_1d_fp64.o", ["-DLBM_D=1", "-DLBM_PREC=0"]),
+    ("lelbm_cell.cu", "lelbm_cell_1d_mixed.o", ["-DLBM_D=1", "-DLBM_PREC=1"]),
+    ("lelbm_cell.cu", "lelbm_cell_1d_fp32.o", ["-DLBM_D=1", "-DLBM_PREC=2"]),
+    ("lelbm_cell.cu", "lelbm_cell_2d_fp64.o", ["-DLBM_D=2", "-DLBM_PREC=0"]),
+    ("lelbm_cell.cu", "lelbm_cell_2d_mixed.o", ["-DLBM_D=2", "-DLBM_PREC=1"]),
+    ("lelbm_cell.cu", "lelbm_cell_2d_fp32.o", ["-DLBM_D=2", "-DLBM_PREC=2"]),
+    ("lelbm_batch.cu", "lelbm_batch_fp64.o", ["-DLBM_PREC=0"]),
+    ("lelbm_batch.cu", "lelbm_batch_mixed.o", ["-DLBM_PREC=1"]),
+    ("lelbm_batch.cu", "lelbm_batch_fp32.o", ["-DLBM_PREC=2"]),
 ]
 HEADERS = ["lelbm_internal.h", "lelbm_device.cuh", "lelbm_mlp.cuh", "lelbm_step.cuh",
            os.path.join("..", "..", "include", "lelbm.h")]

@@ -136,7 +136,7 @@ static int validate(const lelbm_params* p) {
     if (p->max_refine < 0 || p->max_refine > 4) return fail(nullptr, LELBM_E_INVAL, "max_refine must be 0..4");
     if (!(p->tol > 0.0)) return fail(nullptr, LELBM_E_INVAL, "tol must be > 0");
     if (p->max_newton < 1 || p->max_newton > 60) return fail(nullptr, LELBM_E_INVAL, "max_newton must be 1..60");
-    if (p->precision != LELBM_FP64 && p->precision != LELBM_MIXED)
+    if (p->precision != LELBM_FP64 && p->precision != LELBM_MIXED && p->precision != LELBM_FP32)
         return fail(nullptr, LELBM_E_INVAL, "unknown precision");
     if (p->dims == 1 && p->n_batch > 1 && p->lengths)
         for (int b = 0; b < p->n_batch; b++)
@@ -418,7 +418,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         delete h;
         return fail(nullptr, rc, "%s", e.empty() ? "device set-up failed" : e.c_str());
     }
-    h->blocks = cell_update_blocks(D, p->precision == LELBM_MIXED, h->device);
+    h->blocks = cell_update_blocks(D, p->precision, h->device);
     *out = h;
     return LELBM_OK;
 }
@@ -540,7 +540,7 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
             CUDA_TRY(h, cudaEventRecord(ev.first, h->stream));
         }
         launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks,
-                           h->p.precision == LELBM_MIXED, h->stream);
+                           h->p.precision, h->stream);
         if (h->timing) {
             CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
             h->ev_used.push_back(ev);
@@ -664,7 +664,7 @@ extern "C" int lelbm_set_steps(lelbm_t h, const int* steps) {
 static int tuned_blocks(lelbm* h, const lelbm_tuning& t) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int mx = batch_persistent_max_blocks_per_sm(h->p.precision == LELBM_MIXED, t.threads);
+    const int mx = batch_persistent_max_blocks_per_sm(h->p.precision, t.threads);
     const int per = (t.blocks_per_sm <= 0 || t.blocks_per_sm > mx) ? mx : t.blocks_per_sm;
     return sms * per;
 }
@@ -676,7 +676,7 @@ static int enqueue_batch(lelbm* h, int n, const lelbm_tuning& t) {
                             h->p.bc[1] == LELBM_BC_INFLOW, h->d_type, h->M[h->cur], h->M[1 - h->cur], h->d_stats,
                             h->d_work, h->d_order[t.order ? 1 : 0], h->d_inst_first, h->d_inst_pad,
                             h->budgets ? h->d_steps_left : nullptr, n, tuned_blocks(h, t), t.threads,
-                            h->p.precision == LELBM_MIXED, h->stream);
+                            h->p.precision, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     return LELBM_OK;
 }
@@ -748,7 +748,7 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int mx128 = batch_persistent_max_blocks_per_sm(h->p.precision == LELBM_MIXED, 128);
+    int mx128 = batch_persistent_max_blocks_per_sm(h->p.precision, 128);
     std::vector<lelbm_tuning> cand;
     for (int threads : {64, 128})
         for (int per : {1, 2, 0})

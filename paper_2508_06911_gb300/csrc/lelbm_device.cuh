@@ -1008,6 +1008,39 @@ __device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Sten
     return true;
 }
 
+// FP32 Newton alone (the FP32 path): FP32 passes and FP32 solves until the FP32
+// residual is within tol32 (thermal units), the polishing update included.  Returns
+// false on a breakdown or at the iteration cap (the caller then runs the FP64 EPR).
+// sf, sg count the FP32 updates; np32 the points of the FP32 passes.
+template <int D>
+__device__ __forceinline__ bool solve_fg32(const CellState<D>& c, const Stencil<D>& st, const double* conF,
+                                           const double* conG, bool has_g, double* lf, double* lg, int& sf, int& sg,
+                                           unsigned long long& np32) {
+    using MS = MomentSet<D>;
+    constexpr float tol32 = 2e-5f;
+    constexpr int max32 = 16;
+    bool fa = true, ga = has_g;
+    sf = 0;
+    sg = 0;
+    for (int it = 0; fa || ga; it++) {
+        float MF32[MS::NF], MG32[MS::NG];
+        np32 += moment_pass32<D>(c, st, lf, lg, fa, ga, MF32, MG32);
+        if (ga) {
+            const int r = newton_step32<D, false>(MG32, conG, lg, tol32, max32, it);
+            if (r < 0) return false;
+            sg++;
+            if (r == 1) ga = false;
+        }
+        if (fa) {
+            const int r = newton_step32<D, true>(MF32, conF, lf, tol32, max32, it);
+            if (r < 0) return false;
+            sf++;
+            if (r == 1) fa = false;
+        }
+    }
+    return true;
+}
+
 template <int D>
 __device__ __forceinline__ void eq_moments(double K, double rho, const double* u, double RT, double* M) {
     double usq = 0.0;

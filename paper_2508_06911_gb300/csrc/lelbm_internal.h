@@ -12,6 +12,9 @@ namespace lbm {
 // Cell kinds of the padded grid.
 enum : uint8_t { CELL_FLUID = 0, CELL_PAD_IN = 1, CELL_PAD_OUT = 2, CELL_SOLID = 3 };
 
+// Arithmetic of the step (the values of LELBM_FP64, LELBM_MIXED, LELBM_FP32).
+enum : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32 = 2 };
+
 // Physical and numerical constants of one handle (Sec. II, App. C, App. D).
 struct Model {
     double K;           // internal degrees of freedom
@@ -60,7 +63,7 @@ struct DevStats {
     unsigned long long points_f;       // stencil points of fluon Newton passes
     unsigned long long points_g;       // stencil points of phonon Newton passes
     unsigned long long points_ms;      // stencil points streamed
-    unsigned long long points_32;      // stencil points of FP32 Newton passes (mixed path)
+    unsigned long long points_32;      // stencil points of FP32 Newton passes (mixed and FP32 paths)
     unsigned long long judge_redo;     // mixed path: cells whose FP64 check failed and were re-solved
     unsigned long long mlp_retry;      // cells whose learned start failed and were re-solved from Eq. IID13
     unsigned long long wall_hits;      // streamed populations reflected at a solid face (Sec. III.B)
@@ -70,29 +73,29 @@ void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, l
                       const long long* pad_cell, const long long* pad_src, long long npad,
                       cudaStream_t s);
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min,
-                        double* Mout, DevStats* st, unsigned long long* work, int grid_blocks, bool mixed,
+                        double* Mout, DevStats* st, unsigned long long* work, int grid_blocks, int prec,
                         cudaStream_t s);
 void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u,
                      const double* RT, double* M, long long ncell, cudaStream_t s);
 void launch_macros(int D, double K, const uint8_t* type, const double* M, double* rho, double* u,
                    double* RT, long long ncell, cudaStream_t s);
-int cell_update_blocks(int D, bool mixed, int device);
+int cell_update_blocks(int D, int prec, int device);
 void launch_batch_persistent(const Model& m, const Geometry& g, const double inlet[4], int bc_left_inflow,
                              int bc_right_inflow, const uint8_t* type, double* A, double* B, DevStats* st,
                              unsigned long long* work, const int* order, const long long* inst_first,
-                             const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, bool mixed,
+                             const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, int prec,
                              cudaStream_t s);
-int batch_persistent_max_blocks_per_sm(bool mixed, int threads);
+int batch_persistent_max_blocks_per_sm(int prec, int threads);
 
 // One object file per kernel variant (lelbm_cell.cu, lelbm_batch.cu).
-template <int D, bool MIXED>
+template <int D, int PREC>
 struct CellVariant {
     static void launch(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, double* Mout,
                        DevStats* st, unsigned long long* work, int blocks, size_t smem, cudaStream_t s);
     static int blocks_per_sm();
 };
 
-template <bool MIXED>
+template <int PREC>
 struct BatchVariant {
     static void launch(const Model& m, const Geometry& g, const double inlet[4], int bc_left_inflow,
                        int bc_right_inflow, const uint8_t* type, double* A, double* B, DevStats* st,

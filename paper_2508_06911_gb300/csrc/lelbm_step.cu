@@ -14,19 +14,25 @@ namespace lbm {
 void launch_batch_persistent(const Model& m, const Geometry& g, const double inlet[4], int bc_left_inflow,
                              int bc_right_inflow, const uint8_t* type, double* A, double* B, DevStats* st,
                              unsigned long long* work, const int* order, const long long* inst_first,
-                             const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, bool mixed,
+                             const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, int prec,
                              cudaStream_t s) {
     const size_t sm = m.mlp_w ? MlpMma<1>::BYTES : 0;
-    if (mixed)
-        BatchVariant<true>::launch(m, g, inlet, bc_left_inflow, bc_right_inflow, type, A, B, st, work, order,
-                                   inst_first, inst_pad, steps_left, nsteps, blocks, threads, sm, s);
+    auto go = [&](auto variant) {
+        decltype(variant)::launch(m, g, inlet, bc_left_inflow, bc_right_inflow, type, A, B, st, work, order,
+                                  inst_first, inst_pad, steps_left, nsteps, blocks, threads, sm, s);
+    };
+    if (prec == PREC_MIXED)
+        go(BatchVariant<PREC_MIXED>{});
+    else if (prec == PREC_FP32)
+        go(BatchVariant<PREC_FP32>{});
     else
-        BatchVariant<false>::launch(m, g, inlet, bc_left_inflow, bc_right_inflow, type, A, B, st, work, order,
-                                    inst_first, inst_pad, steps_left, nsteps, blocks, threads, sm, s);
+        go(BatchVariant<PREC_FP64>{});
 }
 
-int batch_persistent_max_blocks_per_sm(bool mixed, int threads) {
-    const int per_sm = mixed ? BatchVariant<true>::blocks_per_sm(threads) : BatchVariant<false>::blocks_per_sm(threads);
+int batch_persistent_max_blocks_per_sm(int prec, int threads) {
+    const int per_sm = prec == PREC_MIXED  ? BatchVariant<PREC_MIXED>::blocks_per_sm(threads)
+                       : prec == PREC_FP32 ? BatchVariant<PREC_FP32>::blocks_per_sm(threads)
+                                           : BatchVariant<PREC_FP64>::blocks_per_sm(threads);
     return per_sm < 1 ? 1 : per_sm;
 }
 
@@ -121,36 +127,43 @@ void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, l
                                                    pad_src, npad);
 }
 
-int cell_update_blocks(int D, bool mixed, int device) {
+template <int D>
+static int cell_blocks_per_sm(int prec) {
+    return prec == PREC_MIXED  ? CellVariant<D, PREC_MIXED>::blocks_per_sm()
+           : prec == PREC_FP32 ? CellVariant<D, PREC_FP32>::blocks_per_sm()
+                               : CellVariant<D, PREC_FP64>::blocks_per_sm();
+}
+
+int cell_update_blocks(int D, int prec, int device) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    int per_sm;
-    if (D == 1)
-        per_sm = mixed ? CellVariant<1, true>::blocks_per_sm() : CellVariant<1, false>::blocks_per_sm();
-    else
-        per_sm = mixed ? CellVariant<2, true>::blocks_per_sm() : CellVariant<2, false>::blocks_per_sm();
+    int per_sm = D == 1 ? cell_blocks_per_sm<1>(prec) : cell_blocks_per_sm<2>(prec);
     if (per_sm < 1) per_sm = 1;
     if (sms < 1) sms = 1;
     return sms * per_sm;
 }
 
+template <int D>
+static void cell_launch(int prec, const Model& m, const Geometry& g, const uint8_t* type, const double* Min,
+                        double* Mout, DevStats* st, unsigned long long* work, int blocks, size_t sm, cudaStream_t s) {
+    if (prec == PREC_MIXED)
+        CellVariant<D, PREC_MIXED>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
+    else if (prec == PREC_FP32)
+        CellVariant<D, PREC_FP32>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
+    else
+        CellVariant<D, PREC_FP64>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
+}
+
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, double* Mout,
-                        DevStats* st, unsigned long long* work, int grid_blocks, bool mixed, cudaStream_t s) {
+                        DevStats* st, unsigned long long* work, int grid_blocks, int prec, cudaStream_t s) {
     long long need = (g.ncell + 127) / 128;
     int blocks = (int)(need < grid_blocks ? need : grid_blocks);
     if (blocks < 1) blocks = 1;
     const size_t sm = m.mlp_w ? (g.D == 1 ? MlpMma<1>::BYTES : MlpMma<2>::BYTES) : 0;
-    if (g.D == 1) {
-        if (mixed)
-            CellVariant<1, true>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
-        else
-            CellVariant<1, false>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
-    } else {
-        if (mixed)
-            CellVariant<2, true>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
-        else
-            CellVariant<2, false>::launch(m, g, type, Min, Mout, st, work, blocks, sm, s);
-    }
+    if (g.D == 1)
+        cell_launch<1>(prec, m, g, type, Min, Mout, st, work, blocks, sm, s);
+    else
+        cell_launch<2>(prec, m, g, type, Min, Mout, st, work, blocks, sm, s);
 }
 
 void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, const double* u, const double* RT,

@@ -220,6 +220,307 @@ static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8
     return L.touched;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 streaming (the FP32 path).  Populations and their moment fractions are
+// computed in FP32; every fraction is widened exactly to FP64 for the FP64 atomic
+// accumulation, with integer operations (GB300 runs FP64 at 1/64 of the FP32 rate).
+// The emitted mass, momentum and energy are summed exactly (compensated FP32 sums of
+// exactly the deposited values), and what they miss of the cell's conserved moments
+// (the FP32 Newton leaves a residual of about 1e-6) is added at the emitting cell,
+// so the totals are conserved to FP64 rounding.
+// ---------------------------------------------------------------------------
+// Subnormals become zero (before both the deposit and the accounting).
+__device__ __forceinline__ float flush_sub(float v) { return (__float_as_uint(v) & 0x7f800000u) ? v : 0.f; }
+
+// Exact FP32 -> FP64 of a normal number or zero: sign, exponent rebiased from 127 to
+// 1023, mantissa shifted into place; infinities and NaNs take the conversion unit.
+__device__ __forceinline__ double widen(float v) {
+    const unsigned int b = __float_as_uint(v);
+    const unsigned int e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    if (e == 0xffu) return (double)v;
+    const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// Compensated FP32 sum: hi + lo carries the exact sum to about 1e-14 relative
+// (Knuth's two-sum on every addition).
+struct Acc32 {
+    float hi, lo;
+    __device__ __forceinline__ void add(float v) {
+        const float s = hi + v;
+        const float bp = s - hi;
+        lo += (hi - (s - bp)) + (v - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Splits v into (1 - w) v and w v with the two parts summing to v exactly: the larger
+// part is rounded, the smaller is the exact difference (Sterbenz).
+__device__ __forceinline__ void split_exact(float v, float w, float& lo_part, float& hi_part) {
+    if (w <= 0.5f) {
+        lo_part = flush_sub(v * (1.f - w));
+        hi_part = v - lo_part;
+    } else {
+        hi_part = flush_sub(v * w);
+        lo_part = v - hi_part;
+    }
+}
+
+// Moment fractions T_N(c) mf and T_N(c) mg (stored-moment order) in FP32.
+template <int D>
+__device__ __forceinline__ void fractions32(const float* cp, float mf, float mg, float* v) {
+    float csq = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; a++) csq += cp[a] * cp[a];
+    v[0] = mf;
+#pragma unroll
+    for (int a = 0; a < D; a++) v[1 + a] = cp[a] * mf;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) v[iM2<D>(a, b)] = cp[a] * cp[b] * mf;
+#pragma unroll
+    for (int gg = 0; gg < D; gg++) v[iMD<D>(gg)] = csq * cp[gg] * mf;
+    v[iG0<D>()] = mg;
+#pragma unroll
+    for (int gg = 0; gg < D; gg++) v[iG1<D>(gg)] = cp[gg] * mg;
+#pragma unroll
+    for (int i = 0; i < Dim<D>::NM; i++) v[i] = flush_sub(v[i]);
+}
+
+// Sign of each 2D stored moment under x -> -x (ox) and y -> -y (oy).
+__device__ __forceinline__ float reflect_sign_2d(int i, bool ox, bool oy) {
+    // M0 Mx My Mxx Mxy Myy MDx MDy G0 Gx Gy
+    const bool odd_x = i == 1 || i == 4 || i == 6 || i == 9;
+    const bool odd_y = i == 2 || i == 4 || i == 7 || i == 10;
+    return ((odd_x && ox) != (odd_y && oy)) ? -1.f : 1.f;
+}
+
+// stream_traced for FP32 fractions v (of the unreflected velocity cp): the landing
+// point is shared by exact splits, and reflections and mirrored shares reverse the
+// odd moments.  Returns whether the path was reflected.
+static __device__ __noinline__ bool stream_traced32(const Geometry& g, const uint8_t* type, double* Mout, int ix,
+                                                    int iy, const double* cp, const float* v) {
+    const WallLanding L = trace_path(g, type, ix, iy, cp);
+    const bool rx = (L.cs[0] < 0.0) != (cp[0] < 0.0), ry = (L.cs[1] < 0.0) != (cp[1] < 0.0);
+    const double pos[2] = {(double)L.i + L.off[0], (double)L.j + L.off[1]};
+    int base[2];
+    float w1[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const double fl = floor(pos[a]);
+        base[a] = (int)fl;
+        w1[a] = (float)(pos[a] - fl);
+    }
+    for (int sy = 0; sy < 2; sy++)
+        for (int sx = 0; sx < 2; sx++) {
+            if ((sx && w1[0] == 0.f) || (sy && w1[1] == 0.f)) continue;
+            int tx = base[0] + sx, ty = base[1] + sy;
+            bool ox = false, oy = false;
+            if (solid_at(g, type, tx, ty)) {
+                ox = tx != L.i;
+                oy = ty != L.j;
+                if (ox && oy) {
+                    const bool sa = solid_at(g, type, tx, L.j), sb = solid_at(g, type, L.i, ty);
+                    if (!sa && sb) ox = false;
+                    else if (sa && !sb) oy = false;
+                }
+                if (ox) tx = L.i;
+                if (oy) ty = L.j;
+            }
+            const long long tgt = land<2>(g, 0, 0, 0, ix, iy, tx - ix, ty - iy);
+            if (tgt < 0 || type[tgt] != CELL_FLUID) continue;
+#pragma unroll
+            for (int mm = 0; mm < 11; mm++) {
+                float x0, x1, part = v[mm];
+                split_exact(part, w1[0], x0, x1);
+                part = sx ? x1 : x0;
+                split_exact(part, w1[1], x0, x1);
+                part = sy ? x1 : x0;
+                part *= reflect_sign_2d(mm, rx != ox, ry != oy);
+                if (part != 0.f) atomicAdd(Mout + mm * g.ncell + tgt, widen(part));
+            }
+        }
+    return L.touched;
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                               long long cell, const CellState<D>& c, const Stencil<D>& st,
+                                               const double* lf, const double* lg, LocalStats& ls) {
+    constexpr int NM = Dim<D>::NM;
+    const bool has_g = m.K > 0.0;
+    const float mfs = (float)c.rho;                              // rho dV f'
+    const float mgs = has_g ? (float)(c.rho * m.K * c.RT) : 0.f;  // rho K RT dV g'
+    long long lo = 0;
+    int n = 0, ix = 0, iy = 0;
+    if constexpr (D == 1) {
+        const int b = g.inst_of_cell[cell];
+        lo = g.inst_lo[b];
+        n = g.inst_n[b];
+    } else {
+        iy = (int)(cell / g.NX);
+        ix = (int)(cell - (long long)iy * g.NX);
+    }
+    bool near_wall = false;
+    if constexpr (D == 2) {
+        if (g.wall_dist)
+            near_wall = (double)g.wall_dist[cell] <= fmax(fabs(c.u[0]), fabs(c.u[1])) + (double)st.R + 1.5;
+    }
+    Acc32 em{0.f, 0.f}, ee{0.f, 0.f}, ep[D];
+#pragma unroll
+    for (int a = 0; a < D; a++) ep[a] = Acc32{0.f, 0.f};
+    unsigned long long q = 0;
+    long long walls = 0;
+    double dmax2 = 0.0;
+    auto account = [&](const float* v) {
+        em.add(v[0]);
+#pragma unroll
+        for (int a = 0; a < D; a++) ep[a].add(v[1 + a]);
+#pragma unroll
+        for (int a = 0; a < D; a++) ee.add(v[iM2<D>(a, a)]);
+        ee.add(v[iG0<D>()]);
+    };
+    auto put = [&](long long tgt, const float* v) {
+        if (tgt < 0 || type[tgt] != CELL_FLUID) return;
+#pragma unroll
+        for (int mm = 0; mm < NM; mm++)
+            if (v[mm] != 0.f) atomicAdd(Mout + mm * g.ncell + tgt, widen(v[mm]));
+    };
+    // the FP32 exponent polynomials of one row (the coefficients of row_coeffs)
+    float lf32[Basis<D, true>::N], lg32[Basis<D, false>::N];
+#pragma unroll
+    for (int j = 0; j < Basis<D, true>::N; j++) lf32[j] = (float)lf[j];
+#pragma unroll
+    for (int j = 0; j < Basis<D, false>::N; j++) lg32[j] = (float)lg[j];
+    auto coeffs32 = [&](float y, float* cf, float* cg) {
+        if constexpr (D == 1) {
+            cf[0] = 1.f + lf32[0];
+            cf[1] = lf32[1];
+            cf[2] = lf32[2];
+            cf[3] = lf32[3];
+            cg[0] = 1.f + lg32[0];
+            cg[1] = lg32[1];
+            cg[2] = lg32[2];
+        } else {
+            cf[0] = 1.f + lf32[0] + y * (lf32[2] + y * (lf32[5] + y * lf32[9]));
+            cf[1] = lf32[1] + y * (lf32[4] + y * lf32[7]);
+            cf[2] = lf32[3] + y * lf32[8];
+            cf[3] = lf32[6];
+            cg[0] = 1.f + lg32[0] + y * (lg32[2] + y * lg32[5]);
+            cg[1] = lg32[1] + y * lg32[4];
+            cg[2] = lg32[3];
+        }
+    };
+    const float s32 = (float)c.inv_sig;
+    auto row = [&](int cy, int xa, int xb) {
+        float y = 0.f;
+        if constexpr (D == 2) y = (float)(((double)cy - c.u[1]) * c.inv_sig);
+        float cf[4], cg[3];
+        coeffs32(y, cf, cg);
+        const float x0 = (float)(((double)xa - c.u[0]) * c.inv_sig);
+        for (int k = 0; k <= xb - xa; k++) {
+            const float x = fmaf((float)k, s32, x0);
+            const float f = __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
+            const float gp = has_g ? __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0])) : 0.f;
+            const int cx = xa + k;
+            float cpf[D];
+            cpf[0] = (float)cx;
+            if constexpr (D == 2) cpf[1] = (float)cy;
+            float v[NM];
+            fractions32<D>(cpf, mfs * f, mgs * gp, v);
+            account(v);
+            if constexpr (D == 2) {
+                if (near_wall) {
+                    const double cpd[2] = {(double)cx, (double)cy};
+                    walls += stream_traced32(g, type, Mout, ix, iy, cpd, v) ? 1 : 0;
+                    continue;
+                }
+            }
+            put(land<D>(g, cell, lo, n, ix, iy, cx, cy), v);
+        }
+        q += (unsigned long long)(xb - xa + 1);
+        const double ex = (double)(abs(xa) > abs(xb) ? xa : xb);
+        dmax2 = fmax(dmax2, ex * ex + (double)cy * (double)cy);
+    };
+    auto leaf = [&](const double* cp, double dC) {
+        const float x = (float)((cp[0] - c.u[0]) * c.inv_sig);
+        float y = 0.f;
+        if constexpr (D == 2) y = (float)((cp[1] - c.u[1]) * c.inv_sig);
+        float cf[4], cg[3];
+        coeffs32(y, cf, cg);
+        const float w = (float)dC;
+        const float f = w * __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
+        const float gp = has_g ? w * __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0])) : 0.f;
+        float cpf[D];
+        double csq = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            cpf[a] = (float)cp[a];
+            csq += cp[a] * cp[a];
+        }
+        float v[NM];
+        fractions32<D>(cpf, mfs * f, mgs * gp, v);
+        account(v);
+        q++;
+        dmax2 = fmax(dmax2, csq);
+        if constexpr (D == 2) {
+            if (near_wall) {
+                walls += stream_traced32(g, type, Mout, ix, iy, cp, v) ? 1 : 0;
+                return;
+            }
+        }
+        int base[D];
+        float w1[D];
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            const double fl = floor(cp[a]);
+            base[a] = (int)fl;
+            w1[a] = (float)(cp[a] - fl);
+        }
+        const int ncx = w1[0] > 0.f ? 2 : 1;
+        const int ncy = (D == 2 && w1[D - 1] > 0.f) ? 2 : 1;
+        for (int sy = 0; sy < ncy; sy++)
+            for (int sx = 0; sx < ncx; sx++) {
+                float part[NM];
+#pragma unroll
+                for (int mm = 0; mm < NM; mm++) {
+                    float a0, a1;
+                    split_exact(v[mm], w1[0], a0, a1);
+                    part[mm] = sx ? a1 : a0;
+                    if constexpr (D == 2) {
+                        split_exact(part[mm], w1[1], a0, a1);
+                        part[mm] = sy ? a1 : a0;
+                    }
+                }
+                put(land<D>(g, cell, lo, n, ix, iy, base[0] + sx, D == 2 ? base[D - 1] + sy : 0), part);
+            }
+    };
+    st.for_each_row(row, leaf);
+    // what the emitted fractions miss of the conserved moments stays in the cell
+    if (type[cell] == CELL_FLUID) {
+        double usq = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) usq += c.u[a] * c.u[a];
+        const double dm = c.rho - em.value();
+        const double dE = c.rho * (usq + ((double)D + m.K) * c.RT) - ee.value();
+        atomicAdd(Mout + cell, dm);
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            atomicAdd(Mout + (1 + a) * g.ncell + cell, c.rho * c.u[a] - ep[a].value());
+            atomicAdd(Mout + iM2<D>(a, a) * g.ncell + cell, dE / (double)D);
+        }
+    }
+    if (q > ls.q_max) ls.q_max = q;
+    ls.points += q;
+    ls.walls += walls;
+    ls.disp_max2 = fmax(ls.disp_max2, dmax2);
+}
+
 // Moment streaming, Eq. (IIE3): T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i added at
 // x + c_i.  Level-0 points land on one cell; refined points are shared between the
 // cells they overlap (cloud-in-cell).
@@ -479,7 +780,7 @@ __device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, 
 }
 
 // dl: the learned correction of the Maxwellian start (fluons then phonons), or null.
-template <int D, bool MIXED>
+template <int D, int PREC>
 __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                             DevStats* stats, long long cell, BlockCounters& bc, ThreadCounters& tc,
                                             double* conF, double* conG, const CellState<D>& c, const Stencil<D>& st,
@@ -509,7 +810,25 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 #pragma unroll
     for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
     int sf, sg;
-    if constexpr (MIXED) {
+    if constexpr (PREC == PREC_FP32) {
+        // FP32 Newton and FP32 streaming; the plain FP64 EPR is the fallback
+        bool ok32 = solve_fg32<D>(c, st, conF, conG, has_g, lf, lg, sf, sg, tc.p32);
+        if (!ok32 && learned) {
+            tc.retry++;
+            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+            learned = false;
+            ok32 = solve_fg32<D>(c, st, conF, conG, has_g, lf, lg, sf, sg, tc.p32);
+        }
+        if (ok32) {
+            atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
+            if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+            scatter_cell32<D>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls);
+            return;
+        }
+        tc.redo++;
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+    }
+    if constexpr (PREC == PREC_MIXED) {
         if (solve_fg_mixed<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
             // stream and judge in one FP64 pass; on a miss, take the deposit back and
             // finish the solve in FP64 from the current multipliers
@@ -593,7 +912,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 // One time step of the whole padded grid: warps claim chunks of 32 consecutive cells
 // from a global counter (the cost of a cell varies with its temperature, q ~
 // (n sqrt RT)^D, so a static split leaves SMs idle at the end).
-template <int D, bool MIXED>
+template <int D, int PREC>
 __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
                                                           DevStats* stats, unsigned long long* work) {
@@ -626,7 +945,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
             if (ok) mlp_features<D>(c, st, xin);
             warp_mlp<D>(s_mlp, xin, ok, dl);
         }
-        if (ok) finish_cell<D, MIXED>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
+        if (ok) finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
     }
     counters_flush(bc, tc, stats);
 }
@@ -638,7 +957,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
 // a shared counter.  An instance that ends on an odd step copies its block back, so
 // every instance finishes in buffer A.  steps_left[] (may be null: unlimited) caps
 // each instance and is decremented.
-template <bool MIXED>
+template <int PREC>
 __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry g, double in0, double in1,
                                                                double in3, int bc_left_inflow, int bc_right_inflow,
                                                                const uint8_t* __restrict__ type, double* A, double* B,
@@ -720,7 +1039,7 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
                     warp_mlp<D>(s_mlp, xin, ok, dl);
                 }
                 if (ok)
-                    finish_cell<D, MIXED>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
+                    finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
             }
             __syncthreads();
         }

@@ -18,6 +18,7 @@ LELBM_OK, LELBM_E_INVAL, LELBM_E_NOMEM, LELBM_E_CUDA, LELBM_E_EPR, LELBM_E_TIMEO
 LELBM_BC_OUTFLOW, LELBM_BC_INFLOW, LELBM_BC_PERIODIC = 0, 1, 2
 LELBM_FP64 = 0
 LELBM_MIXED = 1
+LELBM_FP32 = 2
 STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_EPR", 5: "E_TIMEOUT", 6: "E_STATE"}
 
 

@@ -1,0 +1,167 @@
+"""FP32 path (LELBM_FP32) against the CPU oracle.
+
+The FP32 path iterates the EPR Newton in FP32 to an FP32 residual of 2e-5 (thermal
+units) plus one polishing update, evaluates the streamed populations in FP32 and
+accumulates their moment fractions in FP64.  The multipliers are therefore accurate to
+the FP32 noise floor only, about 1e-6 of the constraints, so a step differs from the
+oracle by about that much; the bound used here per step, 2e-5 of each moment's largest
+magnitude, is the FP32 tolerance itself.  After a full run the L1 density error must be
+within 1e-4 of the oracle (the accuracy the FP32 path is held to).  Mass, momentum and
+energy are conserved exactly (to FP64 rounding) by the compensated accounting of the
+emitted fractions, which these tests check to 1e-13 per step.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_06911_gb300 import build, lelbm as L, workloads as W
+from paper_2508_06911_gb300.solver import Solver
+
+import oracle as O
+from parity_util import assert_close, interior_mask_2d, max_rel_err, oracle_1d_instance, oracle_2d
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 2e-5
+L1_TOL = 1e-4
+FP32 = dict(precision=L.LELBM_FP32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    O.build()
+
+
+def l1_rel(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def totals(D, M):
+    t = M.sum(1)
+    E = t[2] + t[4] if D == 1 else t[3] + t[5] + t[8]
+    return t[0], t[1:1 + D], E
+
+
+def test_fp32_1d_step_and_full_run():
+    """Config 0 (400 cells, 80 steps to t = 0.2): per step and after the run."""
+    w = W.riemann_1d(n=400, seed_index=0)
+    p = int(w.pads[0])
+    s = Solver.riemann1d(w, **FP32)
+    s.step(1)
+    M1 = s.get_moments()
+    assert_close(M1[:, p:p + 400], oracle_1d_instance(w, 0, 1)[:, p:p + 400], STEP_TOL, "FP32 1D step")
+    nsteps = int(w.steps[0])
+    s.step(nsteps - 1)
+    M = s.get_moments()
+    st = s.stats()
+    ref = oracle_1d_instance(w, 0, nsteps)
+    l1 = l1_rel(M[0, p:p + 400], ref[0, p:p + 400])
+    print(f"FP32 config 0: L1 density error {l1:.2e}, max rel {max_rel_err(M[:, p:p + 400], ref[:, p:p + 400]):.2e}")
+    assert l1 < L1_TOL
+    assert st.fallback_mx == 0 and st.points_32 > 0 and st.points_f == 0
+    s.close()
+
+
+def test_fp32_1d_periodic_conservation():
+    """Periodic 1D: totals of mass, momentum and energy conserved to 1e-13 per step."""
+    n = 128
+    x = np.arange(n) / n
+    g = np.random.default_rng(41)
+    rho = 1 + 0.3 * np.sin(2 * np.pi * x) ** 2
+    u = 0.9 * np.cos(2 * np.pi * x + 0.3)
+    RT = 0.25 + 2.0 * g.random(n)
+    s = Solver(1, n, 1, K=4.0, nu=1e-3, bc=(2, 2, 2, 2), **FP32)
+    s.set_state(rho, u[None], RT)
+    m0, p0, e0 = totals(1, s.get_moments())
+    for _ in range(20):
+        s.step(1)
+    m1, p1, e1 = totals(1, s.get_moments())
+    assert abs(m1 / m0 - 1) < 20e-13
+    assert abs(p1[0] - p0[0]) / m0 < 20e-13
+    assert abs(e1 / e0 - 1) < 20e-13
+    s.close()
+
+
+def test_fp32_1d_batch_persistent():
+    """The persistent batch kernel in FP32 against the oracle, instance by instance."""
+    w = W.riemann_1d_batch(n_batch=10, seed_index=405, lmin=20, lmax=120)
+    s = Solver.riemann1d(w, **FP32)
+    s.run_batch(6)
+    M = s.get_moments()
+    for b in range(w.n_batch):
+        first, n = s.instance(b)
+        ref = oracle_1d_instance(w, b, 6)
+        pb = int(w.pads[b])
+        assert_close(M[:, first:first + n], ref[:, pb:pb + n], 6 * STEP_TOL, f"FP32 instance {b}")
+    s.close()
+
+
+def test_fp32_2d_periodic_with_refinement_and_conservation():
+    w = W.random_smooth_2d(20, 14, seed_index=19, RT_lo=0.25, RT_hi=1.3, umag=0.8)
+    s = Solver.grid2d(w, **FP32)
+    m0, p0, e0 = totals(2, s.get_moments())
+    s.step(2)
+    M = s.get_moments()
+    assert_close(M, oracle_2d(w, 2), 2 * STEP_TOL, "FP32 2D periodic")
+    m1, p1, e1 = totals(2, M)
+    assert abs(m1 / m0 - 1) < 2e-13
+    assert np.abs(p1 - p0).max() / m0 < 2e-13
+    assert abs(e1 / e0 - 1) < 2e-13
+    s.close()
+
+
+def test_fp32_2d_outflow_inflow_and_lax_liu():
+    w = W.random_smooth_2d(14, 12, seed_index=20, RT_lo=0.5, RT_hi=2.5, umag=0.6, periodic=False)
+    w.bc = (1, 0, 0, 0)
+    w.inlet = (1.2, 0.9, 0.1, 0.8)
+    s = Solver.grid2d(w, **FP32)
+    s.step(2)
+    m = interior_mask_2d(w)
+    assert_close(s.get_moments()[:, m], oracle_2d(w, 2)[:, m], 2 * STEP_TOL, "FP32 2D outflow/inflow")
+    s.close()
+    w = W.lax_liu_12(n=40)
+    s = Solver.grid2d(w, **FP32)
+    s.step(10)
+    m = interior_mask_2d(w)
+    ref = oracle_2d(w, 10)
+    l1 = l1_rel(s.get_moments()[0, m], ref[0, m])
+    print(f"FP32 Lax-Liu 12 (40^2, 10 steps): L1 density error {l1:.2e}")
+    assert l1 < L1_TOL
+    s.close()
+
+
+def test_fp32_solids():
+    """Slip walls and obstacles: FP32 against the oracle, and a sealed box conserves."""
+    w = W.random_smooth_2d(30, 22, seed_index=21, RT_lo=0.2, RT_hi=1.5, umag=0.4)
+    solid = np.zeros((22, 30), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    solid[:, 0] = solid[:, -1] = 1
+    solid[8:12, 10:13] = 1
+    solid[15, 20] = 1
+    w.solid = solid
+    st_o = O.Stats()
+    ref = oracle_2d(w, 3, st_o)
+    s = Solver.grid2d(w, **FP32)
+    M0 = s.get_moments()
+    m0, p0, e0 = totals(2, M0)
+    s.step(3)
+    M = s.get_moments()
+    st = s.stats()
+    mask = interior_mask_2d(w)
+    assert_close(M[:, mask], ref[:, mask], 3 * STEP_TOL, "FP32 with solids")
+    assert st.wall_hits == st_o.wall_hits > 0
+    m1, _, e1 = totals(2, M)
+    assert abs(m1 / m0 - 1) < 3e-13
+    assert abs(e1 / e0 - 1) < 3e-13
+    s.close()
+
+
+def test_fp32_cylinder_small():
+    w = W.cylinder_2d(nx=72, ny=48, diameter=14, steps=4)
+    mask = interior_mask_2d(w)
+    ref = oracle_2d(w, 4)
+    s = Solver.grid2d(w, **FP32)
+    s.step(4)
+    M = s.get_moments()
+    s.close()
+    assert_close(M[:, mask], ref[:, mask], 4 * STEP_TOL, "FP32 cylinder, 4 steps")
