@@ -434,6 +434,7 @@ def run_ours(args):
                 "warmstart": "learned" if weights is not None else "maxwell",
                 "ablation_no_mlp": ablation, "points_fp32": st.points_32,
                 "points_fp64_newton": st.points_f + st.points_g, "mlp_retry": st.mlp_retry,
+                "mlp_cells_frac": st.mlp_cells / max(st.cells, 1),
                 "gpu_launches": 1 if persistent else int(args.steps * (2 if s.n_cells > interior else 1)),
                 "clocks": clocks, "status": L.STATUS.get(status, status),
                 "newton_mean_updates": mean_updates, "fallback_eq": st.fallback_eq,

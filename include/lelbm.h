@@ -134,6 +134,7 @@ typedef struct {
     long long mlp_retry;          /* learned start failed; re-solved from Eq. IID13 */
     long long wall_hits;          /* populations specularly reflected at a solid
                                      face while streaming (Sec. III.B)              */
+    long long mlp_cells;          /* cells given the learned warm start             */
 } lelbm_stats;
 
 /* Sizes of the structures this library was built with, so a binding can check

@@ -579,6 +579,7 @@ static int read_stats(lelbm* h, lelbm_stats* s) {
         s->judge_redo = (long long)d.judge_redo;
         s->mlp_retry = (long long)d.mlp_retry;
         s->wall_hits = (long long)d.wall_hits;
+        s->mlp_cells = (long long)d.mlp_cells;
     }
     return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
 }

@@ -324,6 +324,137 @@ struct Stencil {
 };
 
 // ---------------------------------------------------------------------------
+// Row table of the velocity set for the FP32 passes.  The stencil's membership
+// decisions are exact FP64 tests; when there is at most one refinement level they
+// are taken once per cell and kept as integer extents per row -- the level-0 points
+// [x0, x1] and the band [a, b] of level-0 points that split into 2^D children at
+// +-1/4 -- so every FP32 pass and the FP32 streaming pass enumerate the same set
+// with FP32 and integer arithmetic only.  1D keeps its one row in registers; 2D
+// keeps up to kRowsMax rows (offsets from floor(u)) in the caller's shared memory.
+// A cell with more levels, more rows or offsets beyond int8 uses Stencil directly.
+// ---------------------------------------------------------------------------
+constexpr int kRowsMax = 48;
+
+template <int D>
+struct RowTable {
+    bool ok;
+    int xc, yc;          // floor(u)
+    int y_first, nrows;  // 2D rows y_first .. y_first + nrows - 1
+    int x0, x1, a, b;    // 1D: the row
+    const char4* rows;   // 2D: (x0, x1, a, b) - xc per row; x0 > x1: empty, a > b: no band
+    float fux, fuy;      // (u - floor(u)) / sqrt(RT), FP32
+    float s32;           // 1 / sqrt(RT), FP32
+
+    __device__ __forceinline__ void build(const CellState<D>& c, const Stencil<D>& st, char4* buf) {
+        xc = (int)floor(c.u[0]);
+        yc = D == 2 ? (int)floor(c.u[D - 1]) : 0;
+        s32 = (float)c.inv_sig;
+        fux = (float)((c.u[0] - (double)xc) * c.inv_sig);
+        fuy = D == 2 ? (float)((c.u[D - 1] - (double)yc) * c.inv_sig) : 0.f;
+        rows = buf;
+        ok = st.Nr <= 1;
+        if (!ok) return;
+        const double rr = sqrt(st.rr2), r1 = sqrt(st.rad2[1]);
+        auto extents = [&](double cy, double s, int& e0, int& e1, int& ea, int& eb) {
+            double p[D];
+            if constexpr (D == 2) p[1] = cy;
+            e0 = (int)floor(c.u[0] - s) - 1;
+            e1 = (int)ceil(c.u[0] + s) + 1;
+            p[0] = (double)e0;
+            while (e0 <= e1 && st.dist2(p) > st.rr2) p[0] = (double)(++e0);
+            p[0] = (double)e1;
+            while (e1 >= e0 && st.dist2(p) > st.rr2) p[0] = (double)(--e1);
+            ea = 1;
+            eb = 0;
+            if (st.Nr == 1 && e0 <= e1) {
+                ea = (int)floor(c.u[0] - r1) - 1;
+                eb = (int)ceil(c.u[0] + r1) + 1;
+                ea = ea < e0 ? e0 : ea;
+                eb = eb > e1 ? e1 : eb;
+                p[0] = (double)ea;
+                while (ea <= eb && st.dist2(p) > st.rad2[1]) p[0] = (double)(++ea);
+                p[0] = (double)eb;
+                while (eb >= ea && st.dist2(p) > st.rad2[1]) p[0] = (double)(--eb);
+                if (ea > eb) {
+                    ea = 1;
+                    eb = 0;
+                }
+            }
+        };
+        if constexpr (D == 1) {
+            extents(0.0, rr, x0, x1, a, b);
+            if (a > b) {
+                a = x1 + 1;
+                b = x1;
+            }
+        } else {
+            y_first = (int)floor(c.u[1] - rr) - 1;
+            const int y_last = (int)ceil(c.u[1] + rr) + 1;
+            nrows = y_last - y_first + 1;
+            if (nrows > kRowsMax) {
+                ok = false;
+                return;
+            }
+            for (int r = 0; r < nrows; r++) {
+                const int cy = y_first + r;
+                const double dy = __dsub_rn((double)cy, c.u[1]);
+                const double dy2 = __dmul_rn(dy, dy);
+                int e0 = 1, e1 = 0, ea = 1, eb = 0;
+                if (dy2 <= st.rr2) extents((double)cy, sqrt(fmax(st.rr2 - dy2, 0.0)), e0, e1, ea, eb);
+                if (e0 > e1) {
+                    e0 = xc + 1;
+                    e1 = xc;
+                }
+                if (ea > eb) {
+                    ea = e1 + 1;
+                    eb = e1;
+                }
+                const int lo = e0 - xc, hi = e1 - xc;
+                if (lo < -127 || hi > 127 || ea - xc < -127 || eb - xc > 127) {
+                    ok = false;
+                    return;
+                }
+                buf[r] = make_char4((signed char)lo, (signed char)hi, (signed char)(ea - xc), (signed char)(eb - xc));
+            }
+        }
+    }
+
+    // row(cy, xa, xb) for level-0 segments; child(p, cy, sx, sy) for the 2^D children
+    // of each split point (at p + sx/4, cy + sy/4, dC = 2^-D).
+    template <class RowF, class ChildF>
+    __device__ __forceinline__ void visit(RowF& row, ChildF& child) const {
+        auto one = [&](int cy, int e0, int e1, int ea, int eb) {
+            if (ea <= eb) {
+                if (e0 <= ea - 1) row(cy, e0, ea - 1);
+                for (int p = ea; p <= eb; p++) {
+#pragma unroll
+                    for (int k = 0; k < (1 << D); k++) child(p, cy, (k & 1) ? 1 : -1, (k & 2) ? 1 : -1);
+                }
+                if (eb + 1 <= e1) row(cy, eb + 1, e1);
+            } else if (e0 <= e1) {
+                row(cy, e0, e1);
+            }
+        };
+        if constexpr (D == 1) {
+            one(0, x0, x1, a, b);
+        } else {
+            for (int r = 0; r < nrows; r++) {
+                const char4 e = rows[r];
+                one(y_first + r, xc + e.x, xc + e.y, xc + e.z, xc + e.w);
+            }
+        }
+    }
+
+    // FP32 thermal coordinate of lattice coordinate p (+ q/4) along x or y
+    __device__ __forceinline__ float tx(int p, float q4 = 0.f) const {
+        return fmaf((float)(p - xc) + q4, s32, -fux);
+    }
+    __device__ __forceinline__ float ty(int p, float q4 = 0.f) const {
+        return fmaf((float)(p - yc) + q4, s32, -fuy);
+    }
+};
+
+// ---------------------------------------------------------------------------
 // EPR module: Eq. (IID7)-(IID13) in thermal units.
 // ---------------------------------------------------------------------------
 template <int D, bool FLUON>
@@ -768,9 +899,10 @@ __device__ __forceinline__ int newton_step_tol(const double* Mom, const double* 
     return conv ? 1 : 0;
 }
 
-// The same update from FP32 moments with an FP32 solve (FP32 Newton phase).
+// The same update from FP32 moments with an FP32 solve (FP32 Newton phase); the
+// multipliers and constraints are FP32 as well.
 template <int D, bool FLUON>
-__device__ __forceinline__ int newton_step32(const float* Mom, const double* con, double* lam, float tol, int max_iter,
+__device__ __forceinline__ int newton_step32(const float* Mom, const float* con, float* lam, float tol, int max_iter,
                                              int it) {
     constexpr int N = Basis<D, FLUON>::N;
     constexpr int P = FLUON ? MomentSet<D>::PF : MomentSet<D>::PG;
@@ -779,7 +911,7 @@ __device__ __forceinline__ int newton_step32(const float* Mom, const double* con
     bool finite = true;
 #pragma unroll
     for (int j = 0; j < N; j++) {
-        r[j] = Mom[tix(bx<D, FLUON>(j), by<D, FLUON>(j), P)] - (float)con[j];
+        r[j] = Mom[tix(bx<D, FLUON>(j), by<D, FLUON>(j), P)] - con[j];
         finite = finite && isfinite(r[j]);
         rmax = fmaxf(rmax, fabsf(r[j]));
     }
@@ -794,7 +926,7 @@ __device__ __forceinline__ int newton_step32(const float* Mom, const double* con
             A[tri(i, j)] = Mom[tix(bx<D, FLUON>(i) + bx<D, FLUON>(j), by<D, FLUON>(i) + by<D, FLUON>(j), P)];
     if (!ldlt_solve<float, N>(A, r)) return -1;
 #pragma unroll
-    for (int j = 0; j < N; j++) lam[j] += (double)r[j];
+    for (int j = 0; j < N; j++) lam[j] += r[j];
     return conv ? 1 : 0;
 }
 
@@ -850,49 +982,76 @@ __device__ __forceinline__ void solve_fg(const CellState<D>& c, const Stencil<D>
 // streaming pass checks the FP64 residual of exactly the populations it
 // deposits against the same tolerance as the FP64 path.
 // ---------------------------------------------------------------------------
+// Coefficients of the FP32 exponent polynomials on the row y (as row_coeffs).
+template <int D>
+__device__ __forceinline__ void row_coeffs32(const float* lf, const float* lg, float y, float* cf, float* cg) {
+    if constexpr (D == 1) {
+        cf[0] = 1.f + lf[0];
+        cf[1] = lf[1];
+        cf[2] = lf[2];
+        cf[3] = lf[3];
+        cg[0] = 1.f + lg[0];
+        cg[1] = lg[1];
+        cg[2] = lg[2];
+    } else {
+        cf[0] = 1.f + lf[0] + y * (lf[2] + y * (lf[5] + y * lf[9]));
+        cf[1] = lf[1] + y * (lf[4] + y * lf[7]);
+        cf[2] = lf[3] + y * lf[8];
+        cf[3] = lf[6];
+        cg[0] = 1.f + lg[0] + y * (lg[2] + y * lg[5]);
+        cg[1] = lg[1] + y * lg[4];
+        cg[2] = lg[3];
+    }
+}
+
+// One FP32 pass over the velocity set (row table when valid, else Stencil)
+// accumulating the population moments of f (doF) and g (doG) for the FP32
+// multipliers lf, lg.  Returns the point count.
 template <int D>
 __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& c, const Stencil<D>& st,
-                                                            const double* lf, const double* lg, bool doF, bool doG,
-                                                            float* MF, float* MG) {
+                                                            const RowTable<D>& tab, const float* lf, const float* lg,
+                                                            bool doF, bool doG, float* MF, float* MG) {
     using MS = MomentSet<D>;
 #pragma unroll
     for (int i = 0; i < MS::NF; i++) MF[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < MS::NG; i++) MG[i] = 0.f;
     unsigned long long q = 0;
-    const float s32 = (float)c.inv_sig;
-    float lf32[Basis<D, true>::N], lg32[Basis<D, false>::N];
+    const float s32 = tab.s32;
+    // a point (x, y) of weight w, folded into the moments directly
+    auto add_point = [&](float x, float y, float w) {
+        float cf[4], cg[3];
+        row_coeffs32<D>(lf, lg, y, cf, cg);
+        float px[MS::PF + 1], py[MS::PF + 1];
+        px[0] = py[0] = 1.f;
 #pragma unroll
-    for (int j = 0; j < Basis<D, true>::N; j++) lf32[j] = (float)lf[j];
-#pragma unroll
-    for (int j = 0; j < Basis<D, false>::N; j++) lg32[j] = (float)lg[j];
-    auto coeffs32 = [&](float y, float* cf, float* cg) {
-        if constexpr (D == 1) {
-            cf[0] = 1.f + lf32[0];
-            cf[1] = lf32[1];
-            cf[2] = lf32[2];
-            cf[3] = lf32[3];
-            cg[0] = 1.f + lg32[0];
-            cg[1] = lg32[1];
-            cg[2] = lg32[2];
-        } else {
-            cf[0] = 1.f + lf32[0] + y * (lf32[2] + y * (lf32[5] + y * lf32[9]));
-            cf[1] = lf32[1] + y * (lf32[4] + y * lf32[7]);
-            cf[2] = lf32[3] + y * lf32[8];
-            cf[3] = lf32[6];
-            cg[0] = 1.f + lg32[0] + y * (lg32[2] + y * lg32[5]);
-            cg[1] = lg32[1] + y * lg32[4];
-            cg[2] = lg32[3];
+        for (int k = 1; k <= MS::PF; k++) {
+            px[k] = px[k - 1] * x;
+            py[k] = py[k - 1] * y;
         }
+        if (doF) {
+            const float f = w * __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? MS::PF : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += px[a] * py[b] * f;
+        }
+        if (doG) {
+            const float g = w * __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0]));
+#pragma unroll
+            for (int b = 0; b <= (D == 2 ? MS::PG : 0); b++)
+#pragma unroll
+                for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] += px[a] * py[b] * g;
+        }
+        q++;
     };
     auto row = [&](int cy, int xa, int xb) {
-        float y = 0.f;
-        if constexpr (D == 2) y = (float)(((double)cy - c.u[1]) * c.inv_sig);
+        const float y = D == 2 ? tab.ty(cy) : 0.f;
         float cfv[4], cgv[3];
-        coeffs32(y, cfv, cgv);
+        row_coeffs32<D>(lf, lg, y, cfv, cgv);
         const float cf0 = cfv[0], cf1 = cfv[1], cf2 = cfv[2], cf3 = cfv[3];
         const float cg0 = cgv[0], cg1 = cgv[1], cg2 = cgv[2];
-        const float x0 = (float)(((double)xa - c.u[0]) * c.inv_sig);
+        const float x0 = tab.tx(xa);
         float SF[MS::PF + 1], SG[MS::PG + 1];
 #pragma unroll
         for (int a = 0; a <= MS::PF; a++) SF[a] = 0.f;
@@ -936,35 +1095,19 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
                 for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] = fmaf(SG[a], yp[b], MG[tix(a, b, MS::PG)]);
         }
     };
-    auto leaf = [&](const double* cp, double dC) {  // refined points, FP32 as well
-        const float y = D == 2 ? (float)((cp[D - 1] - c.u[D - 1]) * c.inv_sig) : 0.f;
-        float cfd[4], cgd[3];
-        coeffs32(y, cfd, cgd);
-        const float x = (float)((cp[0] - c.u[0]) * c.inv_sig), w = (float)dC;
-        float px[MS::PF + 1], py[MS::PF + 1];
-        px[0] = py[0] = 1.f;
-#pragma unroll
-        for (int k = 1; k <= MS::PF; k++) {
-            px[k] = px[k - 1] * x;
-            py[k] = py[k - 1] * y;
-        }
-        if (doF) {
-            const float f = w * __expf(-fmaf(fmaf(fmaf(cfd[3], x, cfd[2]), x, cfd[1]), x, cfd[0]));
-#pragma unroll
-            for (int b = 0; b <= (D == 2 ? MS::PF : 0); b++)
-#pragma unroll
-                for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += px[a] * py[b] * f;
-        }
-        if (doG) {
-            const float g = w * __expf(-fmaf(fmaf(cgd[2], x, cgd[1]), x, cgd[0]));
-#pragma unroll
-            for (int b = 0; b <= (D == 2 ? MS::PG : 0); b++)
-#pragma unroll
-                for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] += px[a] * py[b] * g;
-        }
-        q++;
-    };
-    st.for_each_row(row, leaf);
+    if (tab.ok) {
+        constexpr float wch = D == 1 ? 0.5f : 0.25f;
+        auto child = [&](int p, int cy, int sx, int sy) {
+            add_point(tab.tx(p, 0.25f * (float)sx), D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f, wch);
+        };
+        tab.visit(row, child);
+    } else {
+        auto leaf = [&](const double* cp, double dC) {
+            add_point((float)((cp[0] - c.u[0]) * c.inv_sig), D == 2 ? (float)((cp[D - 1] - c.u[D - 1]) * c.inv_sig) : 0.f,
+                      (float)dC);
+        };
+        st.for_each_row(row, leaf);
+    }
     return q;
 }
 
@@ -972,28 +1115,44 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
 // solve broke down (the caller then runs the plain FP64 solve).  sf, sg count
 // the FP64 updates; np32 counts the points of the FP32 passes.
 template <int D>
-__device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Stencil<D>& st, const double* conF,
-                                               const double* conG, bool has_g, double* lf, double* lg,
-                                               const Model& m, int& sf, int& sg, unsigned long long& npf,
+__device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Stencil<D>& st, const RowTable<D>& tab,
+                                               const double* conF, const double* conG, bool has_g, double* lf,
+                                               double* lg, const Model& m, int& sf, int& sg, unsigned long long& npf,
                                                unsigned long long& npg, unsigned long long& np32) {
     using MS = MomentSet<D>;
+    constexpr int NF = Basis<D, true>::N, NG = Basis<D, false>::N;
     constexpr float tol32 = 2e-5f;  // thermal units; the FP64 pass takes it to round-off
     constexpr int max32 = 12;
+    float lf32[NF], lg32[NG], cf32[NF], cg32[NG];
+#pragma unroll
+    for (int j = 0; j < NF; j++) {
+        lf32[j] = (float)lf[j];
+        cf32[j] = (float)conF[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NG; j++) {
+        lg32[j] = (float)lg[j];
+        cg32[j] = (float)conG[j];
+    }
     bool fa = true, ga = has_g;
     for (int it = 0; (fa || ga) && it < max32; it++) {
         float MF32[MS::NF], MG32[MS::NG];
-        np32 += moment_pass32<D>(c, st, lf, lg, fa, ga, MF32, MG32);
+        np32 += moment_pass32<D>(c, st, tab, lf32, lg32, fa, ga, MF32, MG32);
         if (ga) {
-            const int r = newton_step32<D, false>(MG32, conG, lg, tol32, max32, it);
+            const int r = newton_step32<D, false>(MG32, cg32, lg32, tol32, max32, it);
             if (r < 0) return false;
             if (r == 1) ga = false;
         }
         if (fa) {
-            const int r = newton_step32<D, true>(MF32, conF, lf, tol32, max32, it);
+            const int r = newton_step32<D, true>(MF32, cf32, lf32, tol32, max32, it);
             if (r < 0) return false;
             if (r == 1) fa = false;
         }
     }
+#pragma unroll
+    for (int j = 0; j < NF; j++) lf[j] = (double)lf32[j];
+#pragma unroll
+    for (int j = 0; j < NG; j++) lg[j] = (double)lg32[j];
     double MF[MS::NF], MG[MS::NG];
     const unsigned long long q = moment_pass<D>(c, st, lf, lg, true, has_g, MF, MG);
     sg = 0;
@@ -1009,30 +1168,37 @@ __device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Sten
 }
 
 // FP32 Newton alone (the FP32 path): FP32 passes and FP32 solves until the FP32
-// residual is within tol32 (thermal units), the polishing update included.  Returns
-// false on a breakdown or at the iteration cap (the caller then runs the FP64 EPR).
-// sf, sg count the FP32 updates; np32 the points of the FP32 passes.
+// residual is within tol32 (thermal units), the polishing update included, on FP32
+// multipliers lf32, lg32 (in: the start, out: the solution).  Returns false on a
+// breakdown or at the iteration cap (the caller then runs the FP64 EPR).  sf, sg
+// count the FP32 updates; np32 the points of the FP32 passes.
 template <int D>
-__device__ __forceinline__ bool solve_fg32(const CellState<D>& c, const Stencil<D>& st, const double* conF,
-                                           const double* conG, bool has_g, double* lf, double* lg, int& sf, int& sg,
-                                           unsigned long long& np32) {
+__device__ __forceinline__ bool solve_fg32(const CellState<D>& c, const Stencil<D>& st, const RowTable<D>& tab,
+                                           const double* conF, const double* conG, bool has_g, float* lf32,
+                                           float* lg32, int& sf, int& sg, unsigned long long& np32) {
     using MS = MomentSet<D>;
+    constexpr int NF = Basis<D, true>::N, NG = Basis<D, false>::N;
     constexpr float tol32 = 2e-5f;
     constexpr int max32 = 16;
+    float cf32[NF], cg32[NG];
+#pragma unroll
+    for (int j = 0; j < NF; j++) cf32[j] = (float)conF[j];
+#pragma unroll
+    for (int j = 0; j < NG; j++) cg32[j] = (float)conG[j];
     bool fa = true, ga = has_g;
     sf = 0;
     sg = 0;
     for (int it = 0; fa || ga; it++) {
         float MF32[MS::NF], MG32[MS::NG];
-        np32 += moment_pass32<D>(c, st, lf, lg, fa, ga, MF32, MG32);
+        np32 += moment_pass32<D>(c, st, tab, lf32, lg32, fa, ga, MF32, MG32);
         if (ga) {
-            const int r = newton_step32<D, false>(MG32, conG, lg, tol32, max32, it);
+            const int r = newton_step32<D, false>(MG32, cg32, lg32, tol32, max32, it);
             if (r < 0) return false;
             sg++;
             if (r == 1) ga = false;
         }
         if (fa) {
-            const int r = newton_step32<D, true>(MF32, conF, lf, tol32, max32, it);
+            const int r = newton_step32<D, true>(MF32, cf32, lf32, tol32, max32, it);
             if (r < 0) return false;
             sf++;
             if (r == 1) fa = false;

@@ -351,7 +351,8 @@ static __device__ __noinline__ bool stream_traced32(const Geometry& g, const uin
 template <int D>
 __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                                long long cell, const CellState<D>& c, const Stencil<D>& st,
-                                               const double* lf, const double* lg, LocalStats& ls) {
+                                               const RowTable<D>& tab, const float* lf, const float* lg,
+                                               LocalStats& ls) {
     constexpr int NM = Dim<D>::NM;
     const bool has_g = m.K > 0.0;
     const float mfs = (float)c.rho;                              // rho dV f'
@@ -376,7 +377,7 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
     for (int a = 0; a < D; a++) ep[a] = Acc32{0.f, 0.f};
     unsigned long long q = 0;
     long long walls = 0;
-    double dmax2 = 0.0;
+    int dmax = 0;
     auto account = [&](const float* v) {
         em.add(v[0]);
 #pragma unroll
@@ -391,38 +392,12 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
         for (int mm = 0; mm < NM; mm++)
             if (v[mm] != 0.f) atomicAdd(Mout + mm * g.ncell + tgt, widen(v[mm]));
     };
-    // the FP32 exponent polynomials of one row (the coefficients of row_coeffs)
-    float lf32[Basis<D, true>::N], lg32[Basis<D, false>::N];
-#pragma unroll
-    for (int j = 0; j < Basis<D, true>::N; j++) lf32[j] = (float)lf[j];
-#pragma unroll
-    for (int j = 0; j < Basis<D, false>::N; j++) lg32[j] = (float)lg[j];
-    auto coeffs32 = [&](float y, float* cf, float* cg) {
-        if constexpr (D == 1) {
-            cf[0] = 1.f + lf32[0];
-            cf[1] = lf32[1];
-            cf[2] = lf32[2];
-            cf[3] = lf32[3];
-            cg[0] = 1.f + lg32[0];
-            cg[1] = lg32[1];
-            cg[2] = lg32[2];
-        } else {
-            cf[0] = 1.f + lf32[0] + y * (lf32[2] + y * (lf32[5] + y * lf32[9]));
-            cf[1] = lf32[1] + y * (lf32[4] + y * lf32[7]);
-            cf[2] = lf32[3] + y * lf32[8];
-            cf[3] = lf32[6];
-            cg[0] = 1.f + lg32[0] + y * (lg32[2] + y * lg32[5]);
-            cg[1] = lg32[1] + y * lg32[4];
-            cg[2] = lg32[3];
-        }
-    };
-    const float s32 = (float)c.inv_sig;
+    const float s32 = tab.s32;
     auto row = [&](int cy, int xa, int xb) {
-        float y = 0.f;
-        if constexpr (D == 2) y = (float)(((double)cy - c.u[1]) * c.inv_sig);
+        const float y = D == 2 ? tab.ty(cy) : 0.f;
         float cf[4], cg[3];
-        coeffs32(y, cf, cg);
-        const float x0 = (float)(((double)xa - c.u[0]) * c.inv_sig);
+        row_coeffs32<D>(lf, lg, y, cf, cg);
+        const float x0 = tab.tx(xa);
         for (int k = 0; k <= xb - xa; k++) {
             const float x = fmaf((float)k, s32, x0);
             const float f = __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
@@ -444,43 +419,26 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
             put(land<D>(g, cell, lo, n, ix, iy, cx, cy), v);
         }
         q += (unsigned long long)(xb - xa + 1);
-        const double ex = (double)(abs(xa) > abs(xb) ? xa : xb);
-        dmax2 = fmax(dmax2, ex * ex + (double)cy * (double)cy);
+        const int ex = max(abs(xa), abs(xb));
+        dmax = max(dmax, ex * ex + cy * cy);
     };
-    auto leaf = [&](const double* cp, double dC) {
-        const float x = (float)((cp[0] - c.u[0]) * c.inv_sig);
-        float y = 0.f;
-        if constexpr (D == 2) y = (float)((cp[1] - c.u[1]) * c.inv_sig);
+    // a refined point at cp (weight w), FP32 thermal coordinates (x, y); the landing
+    // cell's cloud-in-cell split along each axis is base + {0, 1} with weight w1
+    auto refined = [&](const float* cpf, float x, float y, float w, const int* base, const float* w1,
+                       const double* cpd) {
         float cf[4], cg[3];
-        coeffs32(y, cf, cg);
-        const float w = (float)dC;
+        row_coeffs32<D>(lf, lg, y, cf, cg);
         const float f = w * __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
         const float gp = has_g ? w * __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0])) : 0.f;
-        float cpf[D];
-        double csq = 0.0;
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            cpf[a] = (float)cp[a];
-            csq += cp[a] * cp[a];
-        }
         float v[NM];
         fractions32<D>(cpf, mfs * f, mgs * gp, v);
         account(v);
         q++;
-        dmax2 = fmax(dmax2, csq);
         if constexpr (D == 2) {
             if (near_wall) {
-                walls += stream_traced32(g, type, Mout, ix, iy, cp, v) ? 1 : 0;
+                walls += stream_traced32(g, type, Mout, ix, iy, cpd, v) ? 1 : 0;
                 return;
             }
-        }
-        int base[D];
-        float w1[D];
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            const double fl = floor(cp[a]);
-            base[a] = (int)fl;
-            w1[a] = (float)(cp[a] - fl);
         }
         const int ncx = w1[0] > 0.f ? 2 : 1;
         const int ncy = (D == 2 && w1[D - 1] > 0.f) ? 2 : 1;
@@ -500,7 +458,49 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
                 put(land<D>(g, cell, lo, n, ix, iy, base[0] + sx, D == 2 ? base[D - 1] + sy : 0), part);
             }
     };
-    st.for_each_row(row, leaf);
+    if (tab.ok) {
+        // children of split points at (p + sx/4, cy + sy/4): along an axis the landing
+        // point p - 1/4 splits 3/4 : 1/4 over p - 1, p and p + 1/4 splits over p, p + 1
+        auto child = [&](int p, int cy, int sx, int sy) {
+            const float qx = 0.25f * (float)sx, qy = 0.25f * (float)sy;
+            float cpf[D];
+            int base[D];
+            float w1[D];
+            cpf[0] = (float)p + qx;
+            base[0] = sx < 0 ? p - 1 : p;
+            w1[0] = sx < 0 ? 0.75f : 0.25f;
+            if constexpr (D == 2) {
+                cpf[1] = (float)cy + qy;
+                base[1] = sy < 0 ? cy - 1 : cy;
+                w1[1] = sy < 0 ? 0.75f : 0.25f;
+            }
+            double cpd[2] = {0.0, 0.0};
+            if constexpr (D == 2) {
+                if (near_wall) {
+                    cpd[0] = (double)cpf[0];
+                    cpd[1] = (double)cpf[1];
+                }
+            }
+            refined(cpf, tab.tx(p, qx), D == 2 ? tab.ty(cy, qy) : 0.f, D == 1 ? 0.5f : 0.25f, base, w1, cpd);
+        };
+        tab.visit(row, child);
+    } else {
+        auto leaf = [&](const double* cp, double dC) {
+            float cpf[D];
+            int base[D];
+            float w1[D];
+#pragma unroll
+            for (int a = 0; a < D; a++) {
+                cpf[a] = (float)cp[a];
+                const double fl = floor(cp[a]);
+                base[a] = (int)fl;
+                w1[a] = (float)(cp[a] - fl);
+            }
+            refined(cpf, (float)((cp[0] - c.u[0]) * c.inv_sig),
+                    D == 2 ? (float)((cp[D - 1] - c.u[D - 1]) * c.inv_sig) : 0.f, (float)dC, base, w1, cp);
+        };
+        st.for_each_row(row, leaf);
+    }
     // what the emitted fractions miss of the conserved moments stays in the cell
     if (type[cell] == CELL_FLUID) {
         double usq = 0.0;
@@ -518,7 +518,7 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
     if (q > ls.q_max) ls.q_max = q;
     ls.points += q;
     ls.walls += walls;
-    ls.disp_max2 = fmax(ls.disp_max2, dmax2);
+    ls.disp_max2 = fmax(ls.disp_max2, (double)dmax);
 }
 
 // Moment streaming, Eq. (IIE3): T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i added at
@@ -710,20 +710,21 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
 // Per-block counters in shared memory, flushed to DevStats once per block.
 struct BlockCounters {
     unsigned long long hist[64];
-    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls;
+    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls, mlpc;
 };
 
 // Per-thread tallies.
 struct ThreadCounters {
     unsigned long long cells, pf, pg, p32, redo, retry;
     LocalStats ls;
+    unsigned long long mlp_cells;
 };
 
 __device__ __forceinline__ void counters_init(BlockCounters& bc) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
     if (threadIdx.x == 0)
         bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = bc.retry =
-            bc.walls = 0;
+            bc.walls = bc.mlpc = 0;
 }
 
 // Adds the thread tallies to the block counters, then (after a barrier) the block
@@ -737,6 +738,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
     atomicAdd(&bc.pg, tc.pg);
     atomicAdd(&bc.pm, tc.ls.points);
     if (tc.ls.walls) atomicAdd(&bc.walls, (unsigned long long)tc.ls.walls);
+    if (tc.mlp_cells) atomicAdd(&bc.mlpc, tc.mlp_cells);
     atomicMax(&bc.q, tc.ls.q_max);
     atomicMax(&bc.dmax, (unsigned long long)__double_as_longlong(sqrt(tc.ls.disp_max2)));
     __syncthreads();
@@ -751,6 +753,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
         if (bc.redo) atomicAdd(&stats->judge_redo, bc.redo);
         if (bc.retry) atomicAdd(&stats->mlp_retry, bc.retry);
         if (bc.walls) atomicAdd(&stats->wall_hits, bc.walls);
+        if (bc.mlpc) atomicAdd(&stats->mlp_cells, bc.mlpc);
         if (bc.feq) atomicAdd(&stats->fallback_eq, bc.feq);
         if (bc.fmx) atomicAdd(&stats->fallback_mx, bc.fmx);
         atomicMax(&stats->q_max, bc.q);
@@ -784,7 +787,7 @@ template <int D, int PREC>
 __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                             DevStats* stats, long long cell, BlockCounters& bc, ThreadCounters& tc,
                                             double* conF, double* conG, const CellState<D>& c, const Stencil<D>& st,
-                                            const float* dl) {
+                                            const float* dl, char4* rowbuf) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     tc.cells++;
     const bool has_g = m.K > 0.0;
@@ -810,26 +813,37 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 #pragma unroll
     for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
     int sf, sg;
+    RowTable<D> tab;
+    if constexpr (PREC != PREC_FP64) tab.build(c, st, rowbuf);
     if constexpr (PREC == PREC_FP32) {
         // FP32 Newton and FP32 streaming; the plain FP64 EPR is the fallback
-        bool ok32 = solve_fg32<D>(c, st, conF, conG, has_g, lf, lg, sf, sg, tc.p32);
+        float lf32[NF], lg32[NG];
+#pragma unroll
+        for (int j = 0; j < NF; j++) lf32[j] = (float)lf[j];
+#pragma unroll
+        for (int j = 0; j < NG; j++) lg32[j] = (float)lg[j];
+        bool ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
         if (!ok32 && learned) {
             tc.retry++;
             maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
             learned = false;
-            ok32 = solve_fg32<D>(c, st, conF, conG, has_g, lf, lg, sf, sg, tc.p32);
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf32[j] = (float)lf[j];
+#pragma unroll
+            for (int j = 0; j < NG; j++) lg32[j] = (float)lg[j];
+            ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
         }
         if (ok32) {
             atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
             if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
-            scatter_cell32<D>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls);
+            scatter_cell32<D>(m, g, type, Mout, cell, c, st, tab, lf32, lg32, tc.ls);
             return;
         }
         tc.redo++;
         maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
     }
     if constexpr (PREC == PREC_MIXED) {
-        if (solve_fg_mixed<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
+        if (solve_fg_mixed<D>(c, st, tab, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
             // stream and judge in one FP64 pass; on a miss, take the deposit back and
             // finish the solve in FP64 from the current multipliers
             if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
@@ -919,14 +933,17 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ BlockCounters bc;
     __shared__ double s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
+    // 2D row tables of the FP32 passes (one per thread)
+    __shared__ char4 s_rows[(D == 2 && PREC != PREC_FP64) ? 128 : 1][(D == 2 && PREC != PREC_FP64) ? kRowsMax : 1];
     extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
     double* conF = s_con[threadIdx.x];
     double* conG = conF + NF;
+    char4* rowbuf = (D == 2 && PREC != PREC_FP64) ? s_rows[threadIdx.x] : nullptr;
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
     __syncthreads();
-    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}};
+    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -940,12 +957,17 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         bool ok = false;
         if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
         float dl[MlpDims<D>::NOUT];
-        if (mlp) {  // warp-uniform: every lane takes part in the tensor-core inference
+        // warp-uniform: every lane takes part in the tensor-core inference
+        const bool use_mlp = mlp;
+        if (use_mlp) {
             float xin[MlpDims<D>::NIN];
             if (ok) mlp_features<D>(c, st, xin);
             warp_mlp<D>(s_mlp, xin, ok, dl);
+            if (ok) tc.mlp_cells++;
         }
-        if (ok) finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
+        if (ok)
+            finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, use_mlp ? dl : nullptr,
+                                 rowbuf);
     }
     counters_flush(bc, tc, stats);
 }
@@ -975,7 +997,7 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<1>(s_mlp, m.mlp_w, m.mlp_nrm);
-    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}};
+    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
     const int lane = threadIdx.x & 31;
     double Meq[NM];
     {
@@ -1033,13 +1055,16 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
                 bool ok = false;
                 if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
                 float dl[MlpDims<D>::NOUT];
-                if (mlp) {
+                const bool use_mlp = mlp;
+                if (use_mlp) {
                     float xin[MlpDims<D>::NIN];
                     if (ok) mlp_features<D>(c, st, xin);
                     warp_mlp<D>(s_mlp, xin, ok, dl);
+                    if (ok) tc.mlp_cells++;
                 }
                 if (ok)
-                    finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, mlp ? dl : nullptr);
+                    finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st,
+                                         use_mlp ? dl : nullptr, nullptr);
             }
             __syncthreads();
         }

@@ -75,6 +75,7 @@ class lelbm_stats(ctypes.Structure):
         ("judge_redo", ctypes.c_longlong),
         ("mlp_retry", ctypes.c_longlong),
         ("wall_hits", ctypes.c_longlong),
+        ("mlp_cells", ctypes.c_longlong),
     ]
 
 
