@@ -52,18 +52,6 @@ struct MlpLayout {
 };
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
-// inference-only SiLU, z sigmoid(z) = z (1 + tanh(z/2)) / 2, on the hardware tanh
-// approximation (one special-function operation, no division; its ~2^-11 relative
-// error is below the BF16 rounding of the activations that follows)
-__device__ __forceinline__ float tanh_approx(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float silu_fast(float z) {
-    const float h = 0.5f * z;
-    return fmaf(h, tanh_approx(h), h);
-}
 
 __device__ __forceinline__ float silu_grad(float z) {
     const float s = 1.f / (1.f + __expf(-z));
@@ -137,7 +125,8 @@ __device__ __forceinline__ void mlp_forward(const __nv_bfloat16* W, const float*
 // once as three small GEMMs (32 x 16 x 64, 32 x 64 x 64, 32 x 64 x NOUT) with
 // mma.sync m16n8k16 BF16 -> FP32: 88 MMAs per 32 cells instead of ~5000 FMAs per
 // cell.  The weights sit in shared memory in padded rows (stride 24 / 72 BF16) so
-// the fragment loads of the 8 row groups hit distinct banks.
+// the fragment loads of the 8 row groups hit distinct banks; the hidden activations
+// never leave registers.
 // ---------------------------------------------------------------------------
 template <int D>
 struct MlpMma {
@@ -149,12 +138,11 @@ struct MlpMma {
     static constexpr int W3 = W2 + 64 * S2;
     static constexpr int NWS = W3 + N3 * S2;       // BF16 elements of the staged weights
     static constexpr int WARPS = 4;                // warps per block (128 threads)
-    // dynamic shared memory: weights | b1 b2 b3 | normalisation | per-warp X | per-warp H | per-warp O
+    // dynamic shared memory: weights | b1 b2 b3 | normalisation | per-warp X | per-warp O
     static constexpr size_t OFF_B = ((size_t)NWS * 2 + 15) & ~(size_t)15;
     static constexpr size_t OFF_N = OFF_B + sizeof(float) * (64 + 64 + 16);
     static constexpr size_t OFF_X = (OFF_N + sizeof(float) * 2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT) + 15) & ~(size_t)15;
-    static constexpr size_t OFF_H = OFF_X + (size_t)WARPS * 32 * S1 * 2;
-    static constexpr size_t OFF_O = OFF_H + (size_t)WARPS * 32 * S2 * 2;
+    static constexpr size_t OFF_O = OFF_X + (size_t)WARPS * 32 * S1 * 2;
     static constexpr size_t BYTES = OFF_O + (size_t)WARPS * 32 * 16 * sizeof(float);
 };
 
@@ -204,8 +192,22 @@ __device__ __forceinline__ void st_pair(__nv_bfloat16* p, float lo, float hi) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
 }
 
+// SiLU of two values on BF16 pairs: z sigmoid(z) = h + h tanh(h), h = z / 2, with the
+// packed hardware tanh; returns the BF16 pair (z0 in the low half), ready to be an
+// operand of the next layer.
+__device__ __forceinline__ unsigned silu_bf16x2(float z0, float z1) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(0.5f * z0, 0.5f * z1);
+    unsigned t;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const unsigned*>(&h)));
+    const __nv_bfloat162 s = __hfma2(h, *reinterpret_cast<const __nv_bfloat162*>(&t), h);
+    return *reinterpret_cast<const unsigned*>(&s);
+}
+
 // Whole-warp inference: lane i supplies the raw features x of its cell (ignored when
 // !valid) and receives the raw prediction y.  All 32 lanes must call it.
+// The accumulator fragment of an m16n8 tile holds rows (g, g + 8) x columns (2t, 2t+1)
+// of lane (g, t) -- exactly the operand fragment of the next layer's k-slice -- so
+// the hidden activations stay in registers as BF16 pairs: h[m-tile][k-slice][4].
 template <int D>
 __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bool valid, float* y) {
     using Md = MlpDims<D>;
@@ -216,7 +218,6 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
     const float* b = reinterpret_cast<const float*>(smem + Mm::OFF_B);
     const float* nr = reinterpret_cast<const float*>(smem + Mm::OFF_N);
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + Mm::OFF_X) + warp * 32 * Mm::S1;
-    __nv_bfloat16* Hh = reinterpret_cast<__nv_bfloat16*>(smem + Mm::OFF_H) + warp * 32 * Mm::S2;
     float* O = reinterpret_cast<float*>(smem + Mm::OFF_O) + warp * 32 * 16;
     // standardised inputs, one row per lane, zero padded to 16
 #pragma unroll
@@ -226,49 +227,34 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
         st_pair(X + lane * Mm::S1 + m, v0, v1);
     }
     __syncwarp();
-    // layer 1: H = silu(X W1^T + b1)
-    unsigned a[2][4][4];
+    unsigned ax[2][4];
 #pragma unroll
     for (int mt = 0; mt < 2; mt++) {
         const __nv_bfloat16* r0 = X + (mt * 16 + gid) * Mm::S1 + tig * 2;
         const __nv_bfloat16* r1 = r0 + 8 * Mm::S1;
-        a[mt][0][0] = ld_b32(r0);
-        a[mt][0][1] = ld_b32(r1);
-        a[mt][0][2] = ld_b32(r0 + 8);
-        a[mt][0][3] = ld_b32(r1 + 8);
+        ax[mt][0] = ld_b32(r0);
+        ax[mt][1] = ld_b32(r1);
+        ax[mt][2] = ld_b32(r0 + 8);
+        ax[mt][3] = ld_b32(r1 + 8);
     }
+    // layer 1: h1 = silu(X W1^T + b1)
+    unsigned h1[2][4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; nt++) {
         const __nv_bfloat16* wb = w + Mm::W1 + (nt * 8 + gid) * Mm::S1 + tig * 2;
         const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
         const int col = nt * 8 + tig * 2;
+        const float c0 = b[col], c1 = b[col + 1];
 #pragma unroll
         for (int mt = 0; mt < 2; mt++) {
             float d[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_bf16_16x8x16(d, a[mt][0][0], a[mt][0][1], a[mt][0][2], a[mt][0][3], b0, b1);
-            const int row = mt * 16 + gid;
-            st_pair(Hh + row * Mm::S2 + col, silu_fast(d[0] + b[col]), silu_fast(d[1] + b[col + 1]));
-            st_pair(Hh + (row + 8) * Mm::S2 + col, silu_fast(d[2] + b[col]), silu_fast(d[3] + b[col + 1]));
+            mma_bf16_16x8x16(d, ax[mt][0], ax[mt][1], ax[mt][2], ax[mt][3], b0, b1);
+            h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_bf16x2(d[0] + c0, d[1] + c1);
+            h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_bf16x2(d[2] + c0, d[3] + c1);
         }
     }
-    __syncwarp();
-    // layers 2 and 3 read the whole previous activation into fragments first, so the
-    // result can overwrite it in place
-    auto load_h = [&]() {
-#pragma unroll
-        for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-            for (int kt = 0; kt < 4; kt++) {
-                const __nv_bfloat16* r0 = Hh + (mt * 16 + gid) * Mm::S2 + kt * 16 + tig * 2;
-                const __nv_bfloat16* r1 = r0 + 8 * Mm::S2;
-                a[mt][kt][0] = ld_b32(r0);
-                a[mt][kt][1] = ld_b32(r1);
-                a[mt][kt][2] = ld_b32(r0 + 8);
-                a[mt][kt][3] = ld_b32(r1 + 8);
-            }
-    };
-    load_h();
-    __syncwarp();
+    // layer 2: h2 = silu(h1 W2^T + b2)
+    unsigned h2[2][4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; nt++) {
         float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
@@ -277,18 +263,18 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
             const __nv_bfloat16* wb = w + Mm::W2 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
             const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) mma_bf16_16x8x16(d[mt], a[mt][kt][0], a[mt][kt][1], a[mt][kt][2], a[mt][kt][3], b0, b1);
+            for (int mt = 0; mt < 2; mt++)
+                mma_bf16_16x8x16(d[mt], h1[mt][kt][0], h1[mt][kt][1], h1[mt][kt][2], h1[mt][kt][3], b0, b1);
         }
         const int col = nt * 8 + tig * 2;
+        const float c0 = b[64 + col], c1 = b[64 + col + 1];
 #pragma unroll
         for (int mt = 0; mt < 2; mt++) {
-            const int row = mt * 16 + gid;
-            st_pair(Hh + row * Mm::S2 + col, silu_fast(d[mt][0] + b[64 + col]), silu_fast(d[mt][1] + b[64 + col + 1]));
-            st_pair(Hh + (row + 8) * Mm::S2 + col, silu_fast(d[mt][2] + b[64 + col]), silu_fast(d[mt][3] + b[64 + col + 1]));
+            h2[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_bf16x2(d[mt][0] + c0, d[mt][1] + c1);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_bf16x2(d[mt][2] + c0, d[mt][3] + c1);
         }
     }
-    __syncwarp();
-    load_h();
+    // layer 3: y = h2 W3^T + b3, transposed to one row per lane through shared memory
 #pragma unroll
     for (int nt = 0; nt < Mm::N3 / 8; nt++) {
         float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
@@ -297,7 +283,8 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
             const __nv_bfloat16* wb = w + Mm::W3 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
             const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) mma_bf16_16x8x16(d[mt], a[mt][kt][0], a[mt][kt][1], a[mt][kt][2], a[mt][kt][3], b0, b1);
+            for (int mt = 0; mt < 2; mt++)
+                mma_bf16_16x8x16(d[mt], h2[mt][kt][0], h2[mt][kt][1], h2[mt][kt][2], h2[mt][kt][3], b0, b1);
         }
         const int col = nt * 8 + tig * 2;
 #pragma unroll
