@@ -168,6 +168,126 @@ __device__ __forceinline__ void collide(const double* M, const Model& m, CellSta
     }
 }
 
+// The collision module of the FP32 path: the macroscopic variables and the
+// non-equilibrium central moments (differences of nearly equal numbers) in FP64, the
+// relaxation frequencies, the Knudsen limiter and the normalised constraints in FP32
+// (they feed an FP32 Newton solve).  Same equations as collide.
+template <int D>
+__device__ __forceinline__ void collide32(const double* M, const Model& m, CellState<D>& c) {
+    constexpr int NG = Dim<D>::NG;
+    const double K = m.K;
+    const double rho = M[0];
+    const double irho = 1.0 / rho;
+    double usq = 0.0, tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        c.u[a] = M[1 + a] * irho;
+        usq += c.u[a] * c.u[a];
+        tr += M[iM2<D>(a, a)];
+    }
+    const double RT = ((tr + M[iG0<D>()]) * irho - usq) / ((double)D + K);
+    c.rho = rho;
+    c.RT = RT;
+    c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
+    if (!c.ok) return;
+    c.sig = sqrt(RT);
+    c.inv_sig = 1.0 / c.sig;
+    // Eq. (IIB9) in FP64
+    float P[D][D];
+    double trP = 0.0;
+    double Pd[D][D];
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = 0; b < D; b++) {
+            Pd[a][b] = M[iM2<D>(a, b)] - rho * (c.u[a] * c.u[b] + (a == b ? RT : 0.0));
+            P[a][b] = (float)Pd[a][b];
+        }
+#pragma unroll
+    for (int a = 0; a < D; a++) trP += Pd[a][a];
+    float Q[D];
+#pragma unroll
+    for (int g = 0; g < D; g++) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) s += c.u[a] * Pd[a][g];
+        Q[g] = (float)(M[iMD<D>(g)] - 2.0 * s - c.u[g] * trP - rho * (usq + (D + 2) * RT) * c.u[g]);
+    }
+    const double G0 = M[iG0<D>()];
+    const float G0n = (float)(G0 - rho * K * RT);
+    float Gn[D];
+#pragma unroll
+    for (int g = 0; g < D; g++) Gn[g] = (float)(M[iG1<D>(g)] - c.u[g] * G0);
+
+    // App. C and App. D in FP32
+    const float rf = (float)rho, RTf = (float)RT, sf = (float)c.sig, Kf = (float)K;
+    const float inv_f = (float)m.nu_s / RTf + 0.5f;
+    float wf = 1.f / inv_f;
+    const float fb = 2.f / D - 2.f / (D + Kf);
+    float wb = (m.nu_b < 0.0 || fb <= 0.f) ? 1.f : 1.f / ((float)m.nu_b / (RTf * fb) + 0.5f);
+    float wh = 1.f / ((inv_f - 0.5f) / (float)m.Pr + 0.5f);
+    const float ir = 1.f / rf;
+    if (m.limiter) {
+        float s2 = 0.f, s3 = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = 0; b < D; b++) s2 += fabsf(P[a][b] * ir);
+        s2 += fabsf(G0n * ir);
+#pragma unroll
+        for (int g = 0; g < D; g++) s3 += fabsf(Q[g] * ir) + fabsf(Gn[g] * ir);
+        const float k2 = s2 / ((D + Kf) * RTf);
+        const float k3 = s3 / ((D + Kf + 2.f) * RTf * sf);
+        const float Kn = fmaxf(k2, k3);
+        if (Kn > 0.01f) {
+            const float ks = log10f(Kn);
+            if (ks >= -1.f) {
+                wf = wb = wh = 1.f;
+            } else if (ks > -2.f) {
+                const float x = ks + 2.f;
+                wf += (1.f - wf) * x;
+                wb += (1.f - wb) * x;
+                wh += (1.f - wh) * x;
+            }
+        }
+    }
+    // Eq. (IIB10)-(IIB18), thermal units
+    const float bulk = -G0n / D;
+    const float iRT = 1.f / RTf;
+    c.cf[0] = 1.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) c.cf[1 + a] = 0.0;
+    int j = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) {
+            const float sh = P[a][b] - (a == b ? bulk : 0.f);
+            const float mm = (a == b ? rf * RTf : 0.f) + (1.f - wf) * sh + (1.f - wb) * (a == b ? bulk : 0.f);
+            c.cf[j++] = (double)(mm * ir * iRT);
+        }
+    const float s3 = iRT / sf;
+#pragma unroll
+    for (int g = 0; g < D; g++)
+#pragma unroll
+        for (int a = 0; a < D; a++)
+            c.cf[j++] = (double)((1.f - wh) * ((1.f + 2.f * (a == g)) / (D + 2) * Q[g]) * ir * s3);
+    if (K > 0.0) {
+        const float nrm = 1.f / (rf * Kf * RTf);
+        c.cg[0] = (double)((rf * Kf * RTf + (1.f - wb) * G0n) * nrm);
+#pragma unroll
+        for (int g = 0; g < D; g++) c.cg[1 + g] = (double)((1.f - wh) * Gn[g] * nrm / sf);
+        int k = 1 + D;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++) c.cg[k++] = (a == b) ? 1.0 : 0.0;
+    } else {
+#pragma unroll
+        for (int k = 0; k < NG; k++) c.cg[k] = 0.0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // LAS module: Eq. (IIC6), (IIC9)-(IIC11).  Level-0 points are the integer
 // velocities within R_ac + 1/2 of u; for Lvl = 1..N_r a point of level Lvl-1
@@ -551,6 +671,25 @@ __device__ __forceinline__ void maxwell_start_fg(double RT, double* lf, double* 
 #pragma unroll
         for (int b = a; b < D; b++) {
             lf[j] = lg[j] = (a == b) ? 0.5 : 0.0;
+            j++;
+        }
+}
+
+// Eq. (IID13) in FP32 for the FP32 path.
+template <int D, int NFv, int NGv>
+__device__ __forceinline__ void maxwell_start32(float RT, float* lf, float* lg) {
+    const float l0 = -1.f + 0.5f * D * logf(6.2831853071795865f * RT);
+#pragma unroll
+    for (int j = 0; j < NFv; j++) lf[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < NGv; j++) lg[j] = 0.f;
+    lf[0] = lg[0] = l0;
+    int j = 1 + D;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) {
+            lf[j] = lg[j] = (a == b) ? 0.5f : 0.f;
             j++;
         }
 }

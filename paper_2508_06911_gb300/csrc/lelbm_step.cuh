@@ -764,7 +764,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
 // The single-cell operation of Fig. 5 in two halves around the (warp-wide) warm-start
 // network: prepare_cell loads the moments, runs the collision module and sets up the
 // stencil; finish_cell runs EPR (with the fallbacks) and moment streaming into Mout.
-template <int D>
+template <int D, int PREC>
 __device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, const double* __restrict__ Min,
                                              DevStats* stats, long long cell, BlockCounters& bc, CellState<D>& c,
                                              Stencil<D>& st) {
@@ -772,7 +772,10 @@ __device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, 
     double M[NM];
 #pragma unroll
     for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
-    collide<D>(M, m, c);
+    if constexpr (PREC == PREC_FP32)
+        collide32<D>(M, m, c);
+    else
+        collide<D>(M, m, c);
     if (!c.ok) {  // non-physical cell: nothing can be reconstructed
         atomicAdd(&bc.fmx, 1ull);
         atomicMin(&stats->first_fail, (unsigned long long)cell);
@@ -792,13 +795,27 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     tc.cells++;
     const bool has_g = m.K > 0.0;
     double lf[NF], lg[NG];
-    maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+    float lf32[NF], lg32[NG];  // the FP32 path's multipliers
     bool learned = false;
+    bool dl_ok = dl != nullptr;
     if (dl) {
-        bool ok = true;
 #pragma unroll
-        for (int k = 0; k < MlpDims<D>::NOUT; k++) ok = ok && isfinite(dl[k]);
-        if (ok) {
+        for (int k = 0; k < MlpDims<D>::NOUT; k++) dl_ok = dl_ok && isfinite(dl[k]);
+    }
+    if constexpr (PREC == PREC_FP32) {
+        maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+        if (dl_ok) {
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf32[j] += dl[j];
+            if (has_g) {
+#pragma unroll
+                for (int j = 0; j < NG; j++) lg32[j] += dl[NF + j];
+            }
+            learned = true;
+        }
+    } else {
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        if (dl_ok) {
 #pragma unroll
             for (int j = 0; j < NF; j++) lf[j] += (double)dl[j];
             if (has_g) {
@@ -817,20 +834,11 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     if constexpr (PREC != PREC_FP64) tab.build(c, st, rowbuf);
     if constexpr (PREC == PREC_FP32) {
         // FP32 Newton and FP32 streaming; the plain FP64 EPR is the fallback
-        float lf32[NF], lg32[NG];
-#pragma unroll
-        for (int j = 0; j < NF; j++) lf32[j] = (float)lf[j];
-#pragma unroll
-        for (int j = 0; j < NG; j++) lg32[j] = (float)lg[j];
         bool ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
         if (!ok32 && learned) {
             tc.retry++;
-            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+            maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
             learned = false;
-#pragma unroll
-            for (int j = 0; j < NF; j++) lf32[j] = (float)lf[j];
-#pragma unroll
-            for (int j = 0; j < NG; j++) lg32[j] = (float)lg[j];
             ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
         }
         if (ok32) {
@@ -926,8 +934,13 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 // One time step of the whole padded grid: warps claim chunks of 32 consecutive cells
 // from a global counter (the cost of a cell varies with its temperature, q ~
 // (n sqrt RT)^D, so a static split leaves SMs idle at the end).
+// Blocks per SM the compiler must fit (registers): the 1D FP32 variants are light enough
+// in their hot path for three 128-thread blocks; the rest keep the full register file.
 template <int D, int PREC>
-__global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
+constexpr int min_blocks() { return (D == 1 && PREC == PREC_FP32) ? 3 : 1; }
+
+template <int D, int PREC>
+__global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
                                                           DevStats* stats, unsigned long long* work) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
@@ -955,7 +968,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
         CellState<D> c;
         Stencil<D> st;
         bool ok = false;
-        if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
+        if (active) ok = prepare_cell<D, PREC>(m, g, Min, stats, cell, bc, c, st);
         float dl[MlpDims<D>::NOUT];
         // warp-uniform: every lane takes part in the tensor-core inference
         const bool use_mlp = mlp;
@@ -980,7 +993,7 @@ __global__ void __launch_bounds__(128) cell_update_kernel(Model m, Geometry g, c
 // every instance finishes in buffer A.  steps_left[] (may be null: unlimited) caps
 // each instance and is decremented.
 template <int PREC>
-__global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry g, double in0, double in1,
+__global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_kernel(Model m, Geometry g, double in0, double in1,
                                                                double in3, int bc_left_inflow, int bc_right_inflow,
                                                                const uint8_t* __restrict__ type, double* A, double* B,
                                                                DevStats* stats, unsigned long long* work,
@@ -1053,7 +1066,7 @@ __global__ void __launch_bounds__(128) batch_persistent_kernel(Model m, Geometry
                 CellState<D> c;
                 Stencil<D> st;
                 bool ok = false;
-                if (active) ok = prepare_cell<D>(m, g, Min, stats, cell, bc, c, st);
+                if (active) ok = prepare_cell<D, PREC>(m, g, Min, stats, cell, bc, c, st);
                 float dl[MlpDims<D>::NOUT];
                 const bool use_mlp = mlp;
                 if (use_mlp) {
