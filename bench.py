@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default persistent launch shape")
-    ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell"],
+    ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell", "stored"],
                     help="EPR Newton start of the timed path: the trained MLP or Eq. (IID13)")
     ap.add_argument("--per-step", action="store_true", help="1D batch: one launch per step instead of the "
                     "persistent batch kernel")
@@ -262,7 +262,7 @@ def run_ours(args):
 
     weights = None
     wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", f"warmstart_{D}d.npy")
-    if args.warmstart == "learned":
+    if args.warmstart == "learned" or not args.no_compare:
         if os.path.exists(wpath):
             weights = np.load(wpath)
         else:  # no trained network shipped: train one on pairs recorded by the plain solver
@@ -274,11 +274,13 @@ def run_ours(args):
             weights, _ = WS.train(D, X, Y)
             src.close()
 
-    def make(precision, learned=True):
+    def make(precision, start):
         kw = dict(stream=stream.cuda_stream, precision=prec[precision])
         s_ = Solver.riemann1d(w, **kw) if D == 1 else Solver.grid2d(w, **kw)
-        if learned and weights is not None:
+        if start == "learned" and weights is not None:
             L.lelbm_set_mlp(s_.h, weights)
+        if start == "stored":
+            s_.set_warmstart(True)
         return s_
 
     persistent = D == 1 and not args.per_step
@@ -313,44 +315,47 @@ def run_ours(args):
             ms = float(t.item())
         return ms, s.stats(), s.synchronize(), clocks
 
-    s = make(args.precision)
+    s = make(args.precision, args.warmstart)
     state_bytes = s.n_mom * s.n_cells * 8
     ms, st, status, clocks = timed(s, True)
     value = interior * args.steps * world / (ms / 1e3) / 1e6
 
+    def summary(ms_, st_):
+        h_ = list(st_.newton_hist)
+        return {"value": interior * args.steps * world / (ms_ / 1e3) / 1e6, "ms_per_step": ms_ / args.steps,
+                "points_fp32": st_.points_32, "points_fp64_newton": st_.points_f + st_.points_g,
+                "newton_mean_updates": sum(i * x for i, x in enumerate(h_)) / max(sum(h_), 1),
+                "start_retry": st_.mlp_retry}
+
     compare = None
-    ablation = None
+    warm_starts = None
     if not args.no_compare:
         other = "fp64" if args.precision != "fp64" else "fp32"
-        s2 = make(other, learned=False)  # the plain path: Eq. (IID13) start
+        s2 = make(other, "maxwell")  # the plain path: Eq. (IID13) start
         ms2, st2, _, _ = timed(s2, False)
         r1 = s.get_moments()[0]
         r2 = s2.get_moments()[0]
         l1 = float(np.abs(r1 - r2).sum() / np.abs(r2 if other == "fp64" else r1).sum())
-        compare = {"precision": other, "value": interior * args.steps * world / (ms2 / 1e3) / 1e6,
-                   "ms_per_step": ms2 / args.steps,
+        compare = {"precision": other, **summary(ms2, st2),
                    "kernel_ms": st2.cell_kernel_ms / max(st2.cell_kernel_launches, 1),
                    "l1_density_rel": l1, "warmstart": "maxwell",
                    "note": "both runs from the same state, warmup + steps each"}
         s2.close()
-        if weights is not None:  # what the trained network gains on the timed path
-            s3 = make(args.precision, learned=False)
+        # every warm start on the timed precision, and the stored and learned ones on the other
+        warm_starts = {args.warmstart: summary(ms, st)}
+        for start in ("maxwell", "stored", "learned"):
+            if start == args.warmstart or (start == "learned" and weights is None):
+                continue
+            s3 = make(args.precision, start)
             ms3, st3, _, _ = timed(s3, False)
-            h3 = list(st3.newton_hist)
-            ablation = {"warmstart": "maxwell", "value": interior * args.steps * world / (ms3 / 1e3) / 1e6,
-                        "ms_per_step": ms3 / args.steps, "points_fp32": st3.points_32,
-                        "points_fp64_newton": st3.points_f + st3.points_g,
-                        "newton_mean_updates": sum(i * x for i, x in enumerate(h3)) / max(sum(h3), 1)}
+            warm_starts[start] = summary(ms3, st3)
             s3.close()
-            # and on the other precision: what the network gains there
-            s4 = make(other, learned=True)
+        for start in ("stored", "learned"):
+            if start == "learned" and weights is None:
+                continue
+            s4 = make(other, start)
             ms4, st4, _, _ = timed(s4, False)
-            h4 = list(st4.newton_hist)
-            compare["learned"] = {"value": interior * args.steps * world / (ms4 / 1e3) / 1e6,
-                                  "ms_per_step": ms4 / args.steps,
-                                  "points_fp64_newton": st4.points_f + st4.points_g,
-                                  "newton_mean_updates": sum(i * x for i, x in enumerate(h4)) / max(sum(h4), 1)}
-            compare["points_fp64_newton"] = st2.points_f + st2.points_g
+            compare[start] = summary(ms4, st4)
             s4.close()
 
     # dominant kernel: the fused cell update, ALU bound (FP64 on the FP64 and mixed paths,
@@ -431,8 +436,8 @@ def run_ours(args):
                 "data": "synthetic (seeded)",
                 "config": desc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
                 "speedup_vs_fp64": (value / compare["value"]) if (compare and args.precision != "fp64") else None,
-                "warmstart": "learned" if weights is not None else "maxwell",
-                "ablation_no_mlp": ablation, "points_fp32": st.points_32,
+                "warmstart": args.warmstart if (args.warmstart != "learned" or weights is not None) else "maxwell",
+                "warm_starts": warm_starts, "points_fp32": st.points_32,
                 "points_fp64_newton": st.points_f + st.points_g, "mlp_retry": st.mlp_retry,
                 "mlp_cells_frac": st.mlp_cells / max(st.cells, 1),
                 "gpu_launches": 1 if persistent else int(args.steps * (2 if s.n_cells > interior else 1)),

@@ -131,7 +131,8 @@ typedef struct {
     long long points_32;          /* stencil points of FP32 Newton passes           */
     long long judge_redo;         /* mixed: cells re-solved in FP64 after the check;
                                      FP32: cells whose FP32 solve failed (FP64 EPR) */
-    long long mlp_retry;          /* learned start failed; re-solved from Eq. IID13 */
+    long long mlp_retry;          /* learned or stored start failed; re-solved from
+                                     Eq. (IID13)                                    */
     long long wall_hits;          /* populations specularly reflected at a solid
                                      face while streaming (Sec. III.B)              */
     long long mlp_cells;          /* cells given the learned warm start             */
@@ -269,6 +270,17 @@ int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev);
 /* Use the network params (host, n_params floats) as warm start; NULL: the plain
  * Maxwellian start. */
 int lelbm_set_mlp(lelbm_t h, const float* params);
+
+/* Stored warm start (Sec. II.D: the multipliers of each cell kept as the
+ * precondition of its next step).  stored = 1 allocates a per-cell FP32 store of
+ * the converged multipliers minus Eq. (IID13) ((N_f + N_g) floats per cell: 7 in
+ * 1D, 16 in 2D; zero at first, so the first step starts from Eq. IID13).  Every
+ * solve then starts from Eq. (IID13) plus the cell's stored correction and writes
+ * the new one.  A start that does not converge is retried from Eq. (IID13)
+ * (counted in mlp_retry); a cell solved by a fallback stores zero.  Where the
+ * learned start is set, it takes precedence.  stored = 0 frees the store.
+ * Errors: E_NOMEM, E_CUDA. */
+int lelbm_set_warmstart(lelbm_t h, int stored);
 
 /* Message of the last failure of h ("" if none; h may be NULL for create). */
 const char* lelbm_last_error(lelbm_t h);

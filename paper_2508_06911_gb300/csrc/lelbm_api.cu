@@ -49,6 +49,7 @@ struct lelbm {
     lelbm_tuning tuning{128, 0, 0, 0.0};
     __nv_bfloat16* d_mlp_w = nullptr;  // learned warm start: BF16 weights
     float* d_mlp_nrm = nullptr;        // and normalisation
+    float* d_lam = nullptr;            // stored warm start (lelbm_set_warmstart)
     cudaGraphExec_t graph = nullptr;  // captured lelbm_run_batch launch
     int graph_n = -1, graph_cur = -1;
     bool graph_budgets = false;
@@ -181,6 +182,7 @@ static void free_all(lelbm* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     cudaFree(h->d_mlp_w);
     cudaFree(h->d_mlp_nrm);
+    cudaFree(h->d_lam);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -271,6 +273,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         h->own_stream = true;
     }
     Model& m = h->model;
+    m.lam_store = nullptr;
     m.K = p->K;
     m.nu_s = p->nu_shear;
     m.nu_b = p->nu_bulk;
@@ -741,9 +744,13 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
     const int nb = (int)h->inst_n_h.size();
     double* save = nullptr;
     int* save_steps = nullptr;
+    float* save_lam = nullptr;  // the stored warm start is state the trials change too
+    const size_t lam_bytes = sizeof(float) * 7 * (size_t)h->ncell;
     CUDA_TRY(h, cudaMalloc((void**)&save, bytes));
-    if (h->budgets && cudaMalloc((void**)&save_steps, sizeof(int) * nb) != cudaSuccess) {
+    if ((h->budgets && cudaMalloc((void**)&save_steps, sizeof(int) * nb) != cudaSuccess) ||
+        (h->d_lam && cudaMalloc((void**)&save_lam, lam_bytes) != cudaSuccess)) {
         cudaFree(save);
+        cudaFree(save_steps);
         return fail(h, LELBM_E_NOMEM, "autotune backup");
     }
     cudaEvent_t e0, e1;
@@ -761,6 +768,7 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
     int rc = LELBM_OK;
     cudaMemcpyAsync(save, h->M[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (save_steps) cudaMemcpyAsync(save_steps, h->d_steps_left, sizeof(int) * nb, cudaMemcpyDeviceToDevice, h->stream);
+    if (save_lam) cudaMemcpyAsync(save_lam, h->d_lam, lam_bytes, cudaMemcpyDeviceToDevice, h->stream);
     for (auto& t : cand) {
         cudaEventRecord(e0, h->stream);
         rc = enqueue_batch(h, trial_steps, t);
@@ -769,6 +777,7 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
         cudaMemcpyAsync(h->M[h->cur], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
         if (save_steps)
             cudaMemcpyAsync(h->d_steps_left, save_steps, sizeof(int) * nb, cudaMemcpyDeviceToDevice, h->stream);
+        if (save_lam) cudaMemcpyAsync(h->d_lam, save_lam, lam_bytes, cudaMemcpyDeviceToDevice, h->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = fail(h, LELBM_E_CUDA, "autotune trial failed");
             break;
@@ -783,6 +792,7 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
     cudaEventDestroy(e1);
     cudaFree(save);
     cudaFree(save_steps);
+    cudaFree(save_lam);
     if (rc) return rc;
     h->tuning = win;
     int r2 = reset_stats_dev(h);
@@ -800,6 +810,27 @@ extern "C" int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev) {
     h->model.rec_x = nullptr;
     h->model.rec_y = nullptr;
     return rc;
+}
+
+extern "C" int lelbm_set_warmstart(lelbm_t h, int stored) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (stored) {
+        if (!h->d_lam) {
+            const size_t bytes = sizeof(float) * (size_t)(h->D == 1 ? 7 : 16) * (size_t)h->ncell;
+            CUDA_TRY(h, cudaMalloc((void**)&h->d_lam, bytes));
+            CUDA_TRY(h, cudaMemsetAsync(h->d_lam, 0, bytes, h->stream));
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        }
+        h->model.lam_store = h->d_lam;
+    } else {
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_lam);
+        h->d_lam = nullptr;
+        h->model.lam_store = nullptr;
+    }
+    if (h->graph) cudaGraphExecDestroy(h->graph);  // the captured launch holds the old model
+    h->graph = nullptr;
+    return LELBM_OK;
 }
 
 extern "C" int lelbm_set_mlp(lelbm_t h, const float* params) {

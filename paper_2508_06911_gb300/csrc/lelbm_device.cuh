@@ -656,6 +656,12 @@ __device__ __forceinline__ void maxwell_start(double RT, double* lam) {
         for (int b = a; b < D; b++) lam[j++] = (a == b) ? 0.5 : 0.0;
 }
 
+// lambda_0 of Eq. (IID13).
+template <int D>
+__device__ __forceinline__ double maxwell_l0(double RT) {
+    return -1.0 + 0.5 * D * log(2.0 * 3.14159265358979323846 * RT);
+}
+
 // Eq. (IID13) for both populations with one logarithm.
 template <int D, int NFv, int NGv>
 __device__ __forceinline__ void maxwell_start_fg(double RT, double* lf, double* lg) {

@@ -33,6 +33,8 @@ struct Model {
     float* rec_y;                  // record mode: per-cell targets, or null
     const __nv_bfloat16* mlp_w;    // learned warm start: BF16 weights, or null
     const float* mlp_nrm;          // learned warm start: normalisation
+    float* lam_store;              // stored warm start: per-cell multiplier corrections, SoA
+                                   // [NF + NG][ncell], or null
 };
 
 // Padded-grid geometry.  2D: one instance, cell = iy * NX + ix.

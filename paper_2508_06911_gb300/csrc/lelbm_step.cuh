@@ -761,6 +761,14 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCo
     }
 }
 
+// Entry j of Eq. (IID13) in thermal units: lambda_0 = l0, the second-order diagonal 1/2,
+// the rest 0 (the same for the fluon and the phonon basis).
+template <int D>
+__device__ __forceinline__ float start_base(int j, float l0) {
+    const bool diag2 = D == 1 ? j == 2 : (j == 3 || j == 5);
+    return j == 0 ? l0 : (diag2 ? 0.5f : 0.f);
+}
+
 // The single-cell operation of Fig. 5 in two halves around the (warp-wide) warm-start
 // network: prepare_cell loads the moments, runs the collision module and sets up the
 // stencil; finish_cell runs EPR (with the fallbacks) and moment streaming into Mout.
@@ -812,6 +820,24 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
                 for (int j = 0; j < NG; j++) lg32[j] += dl[NF + j];
             }
             learned = true;
+        } else if (m.lam_store) {  // the correction this cell kept from its last step
+            bool fin = true;
+#pragma unroll
+            for (int j = 0; j < NF; j++) {
+                const float v = m.lam_store[(long long)j * g.ncell + cell];
+                fin = fin && isfinite(v);
+                lf32[j] += v;
+            }
+            if (has_g) {
+#pragma unroll
+                for (int j = 0; j < NG; j++) {
+                    const float v = m.lam_store[(long long)(NF + j) * g.ncell + cell];
+                    fin = fin && isfinite(v);
+                    lg32[j] += v;
+                }
+            }
+            learned = fin;
+            if (!fin) maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
         }
     } else {
         maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
@@ -823,6 +849,24 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
                 for (int j = 0; j < NG; j++) lg[j] += (double)dl[NF + j];
             }
             learned = true;
+        } else if (m.lam_store) {
+            bool fin = true;
+#pragma unroll
+            for (int j = 0; j < NF; j++) {
+                const float v = m.lam_store[(long long)j * g.ncell + cell];
+                fin = fin && isfinite(v);
+                lf[j] += (double)v;
+            }
+            if (has_g) {
+#pragma unroll
+                for (int j = 0; j < NG; j++) {
+                    const float v = m.lam_store[(long long)(NF + j) * g.ncell + cell];
+                    fin = fin && isfinite(v);
+                    lg[j] += (double)v;
+                }
+            }
+            learned = fin;
+            if (!fin) maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
         }
     }
 #pragma unroll
@@ -844,6 +888,15 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
         if (ok32) {
             atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
             if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+            if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), for the next step
+                const float l0 = -1.f + 0.5f * D * logf(6.2831853071795865f * (float)c.RT);
+#pragma unroll
+                for (int j = 0; j < NF; j++)
+                    m.lam_store[(long long)j * g.ncell + cell] = lf32[j] - start_base<D>(j, l0);
+#pragma unroll
+                for (int j = 0; j < NG; j++)
+                    m.lam_store[(long long)(NF + j) * g.ncell + cell] = has_g ? lg32[j] - start_base<D>(j, l0) : 0.f;
+            }
             scatter_cell32<D>(m, g, type, Mout, cell, c, st, tab, lf32, lg32, tc.ls);
             return;
         }
@@ -856,6 +909,16 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
             // finish the solve in FP64 from the current multipliers
             if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
                 atomicAdd(&bc.hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
+                if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
+                    const float l0 = (float)maxwell_l0<D>(c.RT);
+#pragma unroll
+                    for (int j = 0; j < NF; j++)
+                        m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
+#pragma unroll
+                    for (int j = 0; j < NG; j++)
+                        m.lam_store[(long long)(NF + j) * g.ncell + cell] =
+                            has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
+                }
                 return;
             }
             scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
@@ -875,6 +938,15 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     if (sf >= 0 && sg >= 0) {
         atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
         if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+        if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
+            const float l0 = (float)maxwell_l0<D>(c.RT);
+#pragma unroll
+            for (int j = 0; j < NF; j++)
+                m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
+#pragma unroll
+            for (int j = 0; j < NG; j++)
+                m.lam_store[(long long)(NF + j) * g.ncell + cell] = has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
+        }
         if (m.rec_x) {  // training pairs: features and converged multipliers minus Eq. (IID13)
             float xin[MlpDims<D>::NIN];
             mlp_features<D>(c, st, xin);
@@ -904,6 +976,10 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
             }
         maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
         solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
+        if (m.lam_store) {  // a cell solved by a fallback starts from Eq. (IID13) next time
+#pragma unroll
+            for (int k = 0; k < NF + NG; k++) m.lam_store[(long long)k * g.ncell + cell] = 0.f;
+        }
         if (sf >= 0 && sg >= 0) {
             atomicAdd(&bc.feq, 1ull);
         } else {

@@ -86,7 +86,7 @@ EXPORTS = [
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
     "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
     "lelbm_mlp_size", "lelbm_mlp_init", "lelbm_mlp_loss_grad", "lelbm_mlp_train", "lelbm_step_record",
-    "lelbm_set_mlp",
+    "lelbm_set_mlp", "lelbm_set_warmstart",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -151,6 +151,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
         L.lelbm_step_record.argtypes = [_H, ctypes.c_void_p, ctypes.c_void_p]
         L.lelbm_set_mlp.argtypes = [_H, ctypes.POINTER(ctypes.c_float)]
+        L.lelbm_set_warmstart.argtypes = [_H, ctypes.c_int]
         L.lelbm_step_noalloc.argtypes = [ctypes.POINTER(lelbm_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.POINTER(lelbm_stats)]
         _lib = L
@@ -338,6 +339,10 @@ def lelbm_set_mlp(h, params) -> None:
         return
     arr = np.ascontiguousarray(params, dtype=np.float32)
     _check(load().lelbm_set_mlp(h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), h)
+
+
+def lelbm_set_warmstart(h, stored: bool) -> None:
+    _check(load().lelbm_set_warmstart(h, int(bool(stored))), h)
 
 
 def lelbm_last_error(h) -> str:

@@ -71,6 +71,10 @@ class Solver:
     def set_steps(self, steps) -> None:
         L.lelbm_set_steps(self.h, steps)
 
+    def set_warmstart(self, stored: bool) -> None:
+        """Start each EPR solve from the multipliers the cell kept from its last step."""
+        L.lelbm_set_warmstart(self.h, stored)
+
     def autotune(self, trial_steps: int = 1):
         return L.lelbm_autotune(self.h, trial_steps)
 
