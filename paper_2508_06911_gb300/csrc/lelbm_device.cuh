@@ -190,8 +190,11 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
     c.RT = RT;
     c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
     if (!c.ok) return;
-    c.sig = sqrt(RT);
-    c.inv_sig = 1.0 / c.sig;
+    {
+        const float sf = sqrtf((float)RT);  // FP32 is enough: it only scales FP32 coordinates
+        c.sig = (double)sf;
+        c.inv_sig = (double)(1.f / sf);
+    }
     // Eq. (IIB9) in FP64
     float P[D][D];
     double trP = 0.0;
@@ -316,6 +319,29 @@ struct Stencil {
         for (int L = 0; L < 5; L++) {
             const double rad = m.refine_rad * ldexp(1.0, -L);
             rad2[L] = rad * rad;
+        }
+    }
+
+    // The same set-up in FP32 for the FP32 path (R_ac and N_r differ from the FP64
+    // decision only when n sqrt(RT) or 1 / (3 sqrt(RT)) lies within FP32 rounding of a
+    // half-integer).
+    __device__ __forceinline__ void init32(const CellState<D>& c, const Model& m) {
+#pragma unroll
+        for (int a = 0; a < D; a++) u[a] = c.u[a];
+        const float sf = (float)c.sig;
+        float r = roundf((float)m.n_conf * sf);
+        if (r < (float)m.r_min) r = (float)m.r_min;
+        R = (int)r;
+        const float rr = (float)R + 0.5f;
+        rr2 = (double)(rr * rr);
+        float nr = roundf(1.f / ((float)m.refine_div * sf));
+        if (nr > (float)m.max_refine) nr = (float)m.max_refine;
+        Nr = (int)nr;
+        float rad = (float)m.refine_rad;
+#pragma unroll
+        for (int L = 0; L < 5; L++) {
+            rad2[L] = (double)(rad * rad);
+            rad *= 0.5f;
         }
     }
 
@@ -535,6 +561,87 @@ struct RowTable {
                     return;
                 }
                 buf[r] = make_char4((signed char)lo, (signed char)hi, (signed char)(ea - xc), (signed char)(eb - xc));
+            }
+        }
+    }
+
+    // The same table with FP32 membership tests for the FP32 path, on offsets from
+    // floor(u) (so the tests stay exact for the dyadic cases: integer or half-integer u,
+    // (R + 1/2)^2, 9/4).
+    __device__ __forceinline__ void build32(const CellState<D>& c, const Stencil<D>& st, char4* buf) {
+        xc = (int)floor(c.u[0]);
+        yc = D == 2 ? (int)floor(c.u[D - 1]) : 0;
+        s32 = (float)c.inv_sig;
+        const float ux = (float)(c.u[0] - (double)xc);
+        const float uy = D == 2 ? (float)(c.u[D - 1] - (double)yc) : 0.f;
+        fux = ux * s32;
+        fuy = uy * s32;
+        rows = buf;
+        ok = st.Nr <= 1;
+        if (!ok) return;
+        const float rr2f = (float)st.rr2, r12 = (float)st.rad2[1];
+        const float rr = (float)st.R + 0.5f, r1 = sqrtf(r12);
+        // extents, as offsets from xc, of the row at squared y-distance dy2
+        auto extents = [&](float dy2, float s, int& e0, int& e1, int& ea, int& eb) {
+            auto d2 = [&](int k) {
+                const float d = (float)k - ux;
+                return d * d + dy2;
+            };
+            e0 = (int)floorf(ux - s) - 1;
+            e1 = (int)ceilf(ux + s) + 1;
+            while (e0 <= e1 && d2(e0) > rr2f) ++e0;
+            while (e1 >= e0 && d2(e1) > rr2f) --e1;
+            ea = 1;
+            eb = 0;
+            if (st.Nr == 1 && e0 <= e1) {
+                ea = max((int)floorf(ux - r1) - 1, e0);
+                eb = min((int)ceilf(ux + r1) + 1, e1);
+                while (ea <= eb && d2(ea) > r12) ++ea;
+                while (eb >= ea && d2(eb) > r12) --eb;
+                if (ea > eb) {
+                    ea = 1;
+                    eb = 0;
+                }
+            }
+        };
+        if constexpr (D == 1) {
+            int e0, e1, ea, eb;
+            extents(0.f, rr, e0, e1, ea, eb);
+            x0 = xc + e0;
+            x1 = xc + e1;
+            if (ea > eb) {
+                a = x1 + 1;
+                b = x1;
+            } else {
+                a = xc + ea;
+                b = xc + eb;
+            }
+        } else {
+            const int k_first = (int)floorf(uy - rr) - 1, k_last = (int)ceilf(uy + rr) + 1;
+            y_first = yc + k_first;
+            nrows = k_last - k_first + 1;
+            if (nrows > kRowsMax) {
+                ok = false;
+                return;
+            }
+            for (int r = 0; r < nrows; r++) {
+                const float dy = (float)(k_first + r) - uy;
+                const float dy2 = dy * dy;
+                int e0 = 1, e1 = 0, ea = 1, eb = 0;
+                if (dy2 <= rr2f) extents(dy2, sqrtf(fmaxf(rr2f - dy2, 0.f)), e0, e1, ea, eb);
+                if (e0 > e1) {
+                    e0 = 1;
+                    e1 = 0;
+                }
+                if (ea > eb) {
+                    ea = e1 + 1;
+                    eb = e1;
+                }
+                if (e0 < -127 || e1 > 127 || ea < -127 || eb > 127) {
+                    ok = false;
+                    return;
+                }
+                buf[r] = make_char4((signed char)e0, (signed char)e1, (signed char)ea, (signed char)eb);
             }
         }
     }

@@ -789,7 +789,10 @@ __device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, 
         atomicMin(&stats->first_fail, (unsigned long long)cell);
         return false;
     }
-    st.init(c, m);
+    if constexpr (PREC == PREC_FP32)
+        st.init32(c, m);
+    else
+        st.init(c, m);
     return true;
 }
 
@@ -875,7 +878,10 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
     int sf, sg;
     RowTable<D> tab;
-    if constexpr (PREC != PREC_FP64) tab.build(c, st, rowbuf);
+    if constexpr (PREC == PREC_FP32)
+        tab.build32(c, st, rowbuf);
+    else if constexpr (PREC == PREC_MIXED)
+        tab.build(c, st, rowbuf);
     if constexpr (PREC == PREC_FP32) {
         // FP32 Newton and FP32 streaming; the plain FP64 EPR is the fallback
         bool ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
