@@ -165,3 +165,54 @@ def test_fp32_cylinder_small():
     M = s.get_moments()
     s.close()
     assert_close(M[:, mask], ref[:, mask], 4 * STEP_TOL, "FP32 cylinder, 4 steps")
+
+
+def _interior_rho(s, w):
+    M = s.get_moments()
+    parts = []
+    for b in range(w.n_batch):
+        first, n = s.instance(b)
+        parts.append(M[0, first:first + n])
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("start", ["maxwell", "stored", "learned"])
+def test_fp32_long_run_against_fp64_path(start):
+    """300 steps of a 64-instance batch on the FP32 path, from each warm start, against
+    the FP64 path (itself within 1e-12 per step of the oracle): the L1 density error
+    stays within 1e-4 over a long run, not only per step."""
+    import os
+    w = W.riemann_1d_batch(n_batch=64, seed_index=407, lmin=128, lmax=512)
+    ref = Solver.riemann1d(w)
+    ref.run_batch(300)
+    rho_ref = _interior_rho(ref, w)
+    ref.close()
+    s = Solver.riemann1d(w, **FP32)
+    if start == "stored":
+        s.set_warmstart(True)
+    if start == "learned":
+        here = os.path.dirname(os.path.abspath(__file__))
+        L.lelbm_set_mlp(s.h, np.load(os.path.join(here, "..", "paper_2508_06911_gb300", "weights", "warmstart_1d.npy")))
+    s.run_batch(300)
+    l1 = l1_rel(_interior_rho(s, w), rho_ref)
+    st = s.stats()
+    s.close()
+    print(f"FP32 ({start} start), 300 steps: L1 density error against the FP64 path {l1:.2e}")
+    assert l1 < L1_TOL
+    assert st.fallback_mx == 0
+
+
+def test_fp32_long_run_2d_against_fp64_path():
+    """200 steps of the 2D four-quadrant problem at 128^2, FP32 against FP64."""
+    w = W.riemann_2d(n=128, seed_index=24)
+    mask = interior_mask_2d(w)
+    a = Solver.grid2d(w)
+    b = Solver.grid2d(w, **FP32)
+    b.set_warmstart(True)
+    a.step(200)
+    b.step(200)
+    l1 = l1_rel(b.get_moments()[0, mask], a.get_moments()[0, mask])
+    a.close()
+    b.close()
+    print(f"FP32 2D four-quadrant 128^2, 200 steps: L1 density error against the FP64 path {l1:.2e}")
+    assert l1 < L1_TOL
