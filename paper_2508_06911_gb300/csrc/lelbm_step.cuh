@@ -769,6 +769,114 @@ __device__ __forceinline__ float start_base(int j, float l0) {
     return j == 0 ? l0 : (diag2 ? 0.5f : 0.f);
 }
 
+// The FP64 EPR of one cell from the multipliers lf, lg, with the fallbacks of a failed
+// solve (equilibrium constraints, then normalised Maxwellian weights), and its FP64
+// streaming pass.
+template <int D>
+__device__ __forceinline__ void fp64_tail(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                          DevStats* stats, long long cell, BlockCounters& bc,
+                                          unsigned long long& pf, unsigned long long& pg, unsigned long long& retry,
+                                          LocalStats& ls, double* conF, double* conG, const CellState<D>& c,
+                                          const Stencil<D>& st, double* lf, double* lg, bool learned) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    const bool has_g = m.K > 0.0;
+    int sf, sg;
+    solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, pf, pg);
+    if ((sf < 0 || sg < 0) && learned) {  // the plain EPR is the fallback of the learned start
+        retry++;
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, pf, pg);
+    }
+    if (sf >= 0 && sg >= 0) {
+        atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
+        if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
+        if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
+            const float l0 = (float)maxwell_l0<D>(c.RT);
+#pragma unroll
+            for (int j = 0; j < NF; j++)
+                m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
+#pragma unroll
+            for (int j = 0; j < NG; j++)
+                m.lam_store[(long long)(NF + j) * g.ncell + cell] = has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
+        }
+        if (m.rec_x) {  // training pairs: features and converged multipliers minus Eq. (IID13)
+            float xin[MlpDims<D>::NIN];
+            mlp_features<D>(c, st, xin);
+            double mf[NF], mg[NG];
+            maxwell_start_fg<D, NF, NG>(c.RT, mf, mg);
+#pragma unroll
+            for (int k = 0; k < MlpDims<D>::NIN; k++) m.rec_x[cell * MlpDims<D>::NIN + k] = xin[k];
+#pragma unroll
+            for (int j = 0; j < NF; j++) m.rec_y[cell * MlpDims<D>::NOUT + j] = (float)(lf[j] - mf[j]);
+#pragma unroll
+            for (int j = 0; j < NG; j++) m.rec_y[cell * MlpDims<D>::NOUT + NF + j] = has_g ? (float)(lg[j] - mg[j]) : 0.f;
+        }
+    } else {
+        // equilibrium constraints (omega = 1) for both populations
+#pragma unroll
+        for (int j = 0; j < NF; j++) conF[j] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NG; j++) conG[j] = 0.0;
+        conF[0] = conG[0] = 1.0;
+        int jj = 1 + D;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++) {
+                conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
+                jj++;
+            }
+        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, pf, pg);
+        if (m.lam_store) {  // a cell solved by a fallback starts from Eq. (IID13) next time
+#pragma unroll
+            for (int k = 0; k < NF + NG; k++) m.lam_store[(long long)k * g.ncell + cell] = 0.f;
+        }
+        if (sf >= 0 && sg >= 0) {
+            atomicAdd(&bc.feq, 1ull);
+        } else {
+            // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S (mass exact)
+#pragma unroll
+            for (int j = 0; j < NF; j++) lf[j] = 0.0;
+            lf[0] = -1.0;
+            jj = 1 + D;
+#pragma unroll
+            for (int a = 0; a < D; a++)
+#pragma unroll
+                for (int b = a; b < D; b++) {
+                    lf[jj] = (a == b) ? 0.5 : 0.0;
+                    jj++;
+                }
+            double MF[MomentSet<D>::NF], MG[MomentSet<D>::NG];
+            moment_pass<D>(c, st, lf, lg, true, false, MF, MG);
+            lf[0] = log(MF[0]) - 1.0;
+#pragma unroll
+            for (int j = 0; j < NG; j++) lg[j] = lf[j];
+            atomicAdd(&bc.fmx, 1ull);
+            atomicMin(&stats->first_fail, (unsigned long long)cell);
+        }
+    }
+    scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls);
+}
+
+struct TailCounts {
+    unsigned long long pf, pg, retry;
+    LocalStats ls;
+};
+
+// fp64_tail from Eq. (IID13), out of line, for the FP32 path's rare failed solves.
+template <int D>
+static __device__ __noinline__ TailCounts fp64_tail_cold(const Model& m, const Geometry& g, const uint8_t* type,
+                                                         double* Mout, DevStats* stats, long long cell,
+                                                         BlockCounters* bc, double* conF, double* conG,
+                                                         const CellState<D> c, const Stencil<D> st) {
+    TailCounts t{0, 0, 0, {0, 0.0, 0, 0}};
+    double lf[Dim<D>::NF], lg[Dim<D>::NG];
+    maxwell_start_fg<D, Dim<D>::NF, Dim<D>::NG>(c.RT, lf, lg);
+    fp64_tail<D>(m, g, type, Mout, stats, cell, *bc, t.pf, t.pg, t.retry, t.ls, conF, conG, c, st, lf, lg, false);
+    return t;
+}
+
 // The single-cell operation of Fig. 5 in two halves around the (warp-wide) warm-start
 // network: prepare_cell loads the moments, runs the collision module and sets up the
 // stencil; finish_cell runs EPR (with the fallbacks) and moment streaming into Mout.
@@ -906,123 +1014,61 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
             scatter_cell32<D>(m, g, type, Mout, cell, c, st, tab, lf32, lg32, tc.ls);
             return;
         }
+        // the plain FP64 EPR, out of line: it is rare, and inline it would shape the
+        // register allocation of the whole FP32 path
         tc.redo++;
-        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-    }
-    if constexpr (PREC == PREC_MIXED) {
-        if (solve_fg_mixed<D>(c, st, tab, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
-            // stream and judge in one FP64 pass; on a miss, take the deposit back and
-            // finish the solve in FP64 from the current multipliers
-            if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
-                atomicAdd(&bc.hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
-                if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
-                    const float l0 = (float)maxwell_l0<D>(c.RT);
-#pragma unroll
-                    for (int j = 0; j < NF; j++)
-                        m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
-#pragma unroll
-                    for (int j = 0; j < NG; j++)
-                        m.lam_store[(long long)(NF + j) * g.ncell + cell] =
-                            has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
-                }
-                return;
-            }
-            scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
-            tc.redo++;
-        } else {
-            if (learned) tc.retry++;
-            maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-            learned = false;
-        }
-    }
-    solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
-    if ((sf < 0 || sg < 0) && learned) {  // the plain EPR is the fallback of the learned start
-        tc.retry++;
-        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
-    }
-    if (sf >= 0 && sg >= 0) {
-        atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
-        if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
-        if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
-            const float l0 = (float)maxwell_l0<D>(c.RT);
-#pragma unroll
-            for (int j = 0; j < NF; j++)
-                m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
-#pragma unroll
-            for (int j = 0; j < NG; j++)
-                m.lam_store[(long long)(NF + j) * g.ncell + cell] = has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
-        }
-        if (m.rec_x) {  // training pairs: features and converged multipliers minus Eq. (IID13)
-            float xin[MlpDims<D>::NIN];
-            mlp_features<D>(c, st, xin);
-            double mf[NF], mg[NG];
-            maxwell_start_fg<D, NF, NG>(c.RT, mf, mg);
-#pragma unroll
-            for (int k = 0; k < MlpDims<D>::NIN; k++) m.rec_x[cell * MlpDims<D>::NIN + k] = xin[k];
-#pragma unroll
-            for (int j = 0; j < NF; j++) m.rec_y[cell * MlpDims<D>::NOUT + j] = (float)(lf[j] - mf[j]);
-#pragma unroll
-            for (int j = 0; j < NG; j++) m.rec_y[cell * MlpDims<D>::NOUT + NF + j] = has_g ? (float)(lg[j] - mg[j]) : 0.f;
-        }
+        const TailCounts t = fp64_tail_cold<D>(m, g, type, Mout, stats, cell, &bc, conF, conG, c, st);
+        tc.pf += t.pf;
+        tc.pg += t.pg;
+        tc.retry += t.retry;
+        if (t.ls.q_max > tc.ls.q_max) tc.ls.q_max = t.ls.q_max;
+        tc.ls.points += t.ls.points;
+        tc.ls.walls += t.ls.walls;
+        tc.ls.disp_max2 = fmax(tc.ls.disp_max2, t.ls.disp_max2);
     } else {
-        // equilibrium constraints (omega = 1) for both populations
+        if constexpr (PREC == PREC_MIXED) {
+            if (solve_fg_mixed<D>(c, st, tab, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
+                // stream and judge in one FP64 pass; on a miss, take the deposit back and
+                // finish the solve in FP64 from the current multipliers
+                if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
+                    atomicAdd(&bc.hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
+                    if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
+                        const float l0 = (float)maxwell_l0<D>(c.RT);
 #pragma unroll
-        for (int j = 0; j < NF; j++) conF[j] = 0.0;
+                        for (int j = 0; j < NF; j++)
+                            m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
 #pragma unroll
-        for (int j = 0; j < NG; j++) conG[j] = 0.0;
-        conF[0] = conG[0] = 1.0;
-        int jj = 1 + D;
-#pragma unroll
-        for (int a = 0; a < D; a++)
-#pragma unroll
-            for (int b = a; b < D; b++) {
-                conF[jj] = conG[jj] = (a == b) ? 1.0 : 0.0;
-                jj++;
-            }
-        maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-        solve_fg<D>(c, st, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg);
-        if (m.lam_store) {  // a cell solved by a fallback starts from Eq. (IID13) next time
-#pragma unroll
-            for (int k = 0; k < NF + NG; k++) m.lam_store[(long long)k * g.ncell + cell] = 0.f;
-        }
-        if (sf >= 0 && sg >= 0) {
-            atomicAdd(&bc.feq, 1ull);
-        } else {
-            // normalised Maxwellian weights: f'_i = dC_i exp(-t^2/2) / S (mass exact)
-#pragma unroll
-            for (int j = 0; j < NF; j++) lf[j] = 0.0;
-            lf[0] = -1.0;
-            jj = 1 + D;
-#pragma unroll
-            for (int a = 0; a < D; a++)
-#pragma unroll
-                for (int b = a; b < D; b++) {
-                    lf[jj] = (a == b) ? 0.5 : 0.0;
-                    jj++;
+                        for (int j = 0; j < NG; j++)
+                            m.lam_store[(long long)(NF + j) * g.ncell + cell] =
+                                has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
+                    }
+                    return;
                 }
-            double MF[MomentSet<D>::NF], MG[MomentSet<D>::NG];
-            moment_pass<D>(c, st, lf, lg, true, false, MF, MG);
-            lf[0] = log(MF[0]) - 1.0;
-#pragma unroll
-            for (int j = 0; j < NG; j++) lg[j] = lf[j];
-            atomicAdd(&bc.fmx, 1ull);
-            atomicMin(&stats->first_fail, (unsigned long long)cell);
+                scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
+                tc.redo++;
+            } else {
+                if (learned) tc.retry++;
+                maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
+                learned = false;
+            }
         }
+        fp64_tail<D>(m, g, type, Mout, stats, cell, bc, tc.pf, tc.pg, tc.retry, tc.ls, conF, conG, c, st, lf, lg,
+                     learned);
     }
-    scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls);
 }
 
 // One time step of the whole padded grid: warps claim chunks of 32 consecutive cells
 // from a global counter (the cost of a cell varies with its temperature, q ~
 // (n sqrt RT)^D, so a static split leaves SMs idle at the end).
-// Blocks per SM the compiler must fit (registers): the 1D FP32 variants are light enough
-// in their hot path for three 128-thread blocks; the rest keep the full register file.
+// Blocks per SM the compiler must fit (registers): the FP32 variants, whose FP64 fallback
+// is out of line, are light enough in their hot path for three 128-thread blocks; the
+// rest keep the full register file.
 template <int D, int PREC>
-constexpr int min_blocks() { return (D == 1 && PREC == PREC_FP32) ? 3 : 1; }
+constexpr int min_blocks() { return PREC == PREC_FP32 ? 3 : 1; }
 
 template <int D, int PREC>
-__global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel(Model m, Geometry g, const uint8_t* __restrict__ type,
+__global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel(const __grid_constant__ Model m, const __grid_constant__ Geometry g,
+                                                          const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
                                                           DevStats* stats, unsigned long long* work) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
@@ -1075,7 +1121,8 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
 // every instance finishes in buffer A.  steps_left[] (may be null: unlimited) caps
 // each instance and is decremented.
 template <int PREC>
-__global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_kernel(Model m, Geometry g, double in0, double in1,
+__global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_kernel(const __grid_constant__ Model m,
+                                                               const __grid_constant__ Geometry g, double in0, double in1,
                                                                double in3, int bc_left_inflow, int bc_right_inflow,
                                                                const uint8_t* __restrict__ type, double* A, double* B,
                                                                DevStats* stats, unsigned long long* work,
