@@ -104,3 +104,34 @@ def test_training_lowers_loss_and_newton_work_without_changing_results():
     assert b.stats().fallback_mx == 0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("dims,case", [(1, "batch"), (2, "cylinder"), (2, "hotbox")])
+def test_shipped_networks_save_newton_updates(dims, case):
+    """The trained networks in weights/ take fewer Newton updates than Eq. (IID13) on
+    the FP64 path, on states none of them was trained on, with the same results."""
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    params = np.load(os.path.join(here, "..", "paper_2508_06911_gb300", "weights", f"warmstart_{dims}d.npy"))
+    if dims == 1:
+        w = W.riemann_1d_batch(n_batch=64, seed_index=810, lmin=128, lmax=512)
+        make = lambda: Solver.riemann1d(w)
+    elif case == "cylinder":
+        w = W.cylinder_2d(nx=192, ny=96, diameter=16)
+        make = lambda: Solver.grid2d(w)
+    else:
+        w = W.hot_box(2, 64, 0.5)
+        make = lambda: Solver.grid2d(w)
+    a, b = make(), make()
+    L.lelbm_set_mlp(b.h, params)
+    for s in (a, b):
+        s.step(3)
+        L.lelbm_reset_stats(s.h)
+        s.step(2)
+    mean = lambda st: float((np.arange(64) * np.array(st.newton_hist)).sum() / np.array(st.newton_hist).sum())
+    ma, mb = mean(a.stats()), mean(b.stats())
+    print(f"{dims}D {case}: mean Newton updates {ma:.3f} (Eq. IID13) -> {mb:.3f} (learned)")
+    assert mb < ma - 0.2, (ma, mb)
+    assert_close(b.get_moments(), a.get_moments(), 5e-12, "learned vs plain start")
+    a.close()
+    b.close()
