@@ -39,6 +39,16 @@ N_G = {1: 3, 2: 6}
 N_M = {1: 6, 2: 11}
 
 
+# DRAM bytes (read + write) per time step of the timed kernel, from one ncu capture of the
+# same kernel on the same workload and launch of one step (the summaries in profiles/).
+# Configurations without a capture report traffic null.
+DRAM_PER_STEP = {
+    ("batch1d", 4096, "fp32", "learned"): (1244.5e6, "profiles/batch_persistent_fp32_riemann1d_batch4096.md"),
+    ("batch1d", 4096, "fp64", "maxwell"): (1007.8e6, "profiles/batch_persistent_fp64_riemann1d_batch4096.md"),
+    ("riemann2d", 1024, "fp32", "learned"): (324.2e6, "profiles/cell_update_fp32_riemann2d_1024.md"),
+}
+
+
 def newton_flops(n: int) -> int:
     return 2 * (2 * n + n * (n + 1) // 2)
 
@@ -420,8 +430,13 @@ def run_ours(args):
                      "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.255 measured by an FMA probe)"}
         other_side = {"fp32_side": {"achieved_tflops": flops32 / sec / 1e12, "peak_tflops": 78.2,
                                     "peak_source": "FP32 FMA probe on this pool's GB300"}}
+    size = args.n_batch if args.workload == "batch1d" else args.n
+    dram = DRAM_PER_STEP.get((args.workload, size, args.precision, args.warmstart))
     roofline = {"bound": "alu", "achieved": main_side["achieved"], "peak": main_side["peak"], "unit": "TFLOP/s",
-                "frac": main_side["achieved"] / main_side["peak"], "traffic": None,
+                "frac": main_side["achieved"] / main_side["peak"],
+                "traffic": dram[0] * steps_per_launch if dram else None,
+                "traffic_source": (f"{dram[1]}: ncu dram bytes of one step x {steps_per_launch} steps per launch"
+                                   if dram else None),
                 "peak_source": main_side["peak_source"],
                 "kernel": (f"batch_persistent_kernel<{prec_id}>" if persistent else
                            f"cell_update_kernel<{D},{prec_id}>"),
