@@ -147,7 +147,9 @@ struct MlpMma {
 };
 
 // Stage the weights of the FP32-layout BF16 copy (W) and the FP32 normalisation into
-// the padded shared-memory layout; every thread of the block must call it.
+// the padded shared-memory layout; every thread of the block must call it.  The two
+// hidden layers' weights and biases are staged halved (exact in BF16 and FP32), so
+// their products are h = z / 2, the argument of SiLU's tanh form.
 template <int D>
 __device__ __forceinline__ void mlp_stage_mma(unsigned char* smem, const __nv_bfloat16* W, const float* nrm) {
     using Md = MlpDims<D>;
@@ -159,19 +161,19 @@ __device__ __forceinline__ void mlp_stage_mma(unsigned char* smem, const __nv_bf
     const __nv_bfloat16 z = __float2bfloat16(0.f);
     for (int i = threadIdx.x; i < 64 * Mm::S1; i += blockDim.x) {
         const int n = i / Mm::S1, k = i % Mm::S1;
-        w[Mm::W1 + i] = k < Md::NIN ? W[Ly::W1 + n * Md::NIN + k] : z;
+        w[Mm::W1 + i] = k < Md::NIN ? __hmul(W[Ly::W1 + n * Md::NIN + k], __float2bfloat16(0.5f)) : z;
     }
     for (int i = threadIdx.x; i < 64 * Mm::S2; i += blockDim.x) {
         const int n = i / Mm::S2, k = i % Mm::S2;
-        w[Mm::W2 + i] = k < 64 ? W[Ly::W2 + n * 64 + k] : z;
+        w[Mm::W2 + i] = k < 64 ? __hmul(W[Ly::W2 + n * 64 + k], __float2bfloat16(0.5f)) : z;
     }
     for (int i = threadIdx.x; i < Mm::N3 * Mm::S2; i += blockDim.x) {
         const int n = i / Mm::S2, k = i % Mm::S2;
         w[Mm::W3 + i] = (n < Md::NOUT && k < 64) ? W[Ly::W3 + n * 64 + k] : z;
     }
     for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-        b[i] = __bfloat162float(W[Ly::B1 + i]);
-        b[64 + i] = __bfloat162float(W[Ly::B2 + i]);
+        b[i] = 0.5f * __bfloat162float(W[Ly::B1 + i]);
+        b[64 + i] = 0.5f * __bfloat162float(W[Ly::B2 + i]);
     }
     for (int i = threadIdx.x; i < 16; i += blockDim.x) b[128 + i] = i < Md::NOUT ? __bfloat162float(W[Ly::B3 + i]) : 0.f;
     for (int i = threadIdx.x; i < 2 * (Md::NIN + Md::NOUT); i += blockDim.x) nr[i] = nrm[i];
@@ -192,11 +194,11 @@ __device__ __forceinline__ void st_pair(__nv_bfloat16* p, float lo, float hi) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
 }
 
-// SiLU of two values on BF16 pairs: z sigmoid(z) = h + h tanh(h), h = z / 2, with the
-// packed hardware tanh; returns the BF16 pair (z0 in the low half), ready to be an
-// operand of the next layer.
-__device__ __forceinline__ unsigned silu_bf16x2(float z0, float z1) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(0.5f * z0, 0.5f * z1);
+// SiLU on BF16 pairs from h = z / 2 (the staged halves of the weights and biases give h
+// directly): z sigmoid(z) = h + h tanh(h), with the packed hardware tanh.  Returns the BF16
+// pair (h0 in the low half), ready to be an operand of the next layer.
+__device__ __forceinline__ unsigned silu_half_bf16x2(float h0, float h1) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(h0, h1);
     unsigned t;
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const unsigned*>(&h)));
     const __nv_bfloat162 s = __hfma2(h, *reinterpret_cast<const __nv_bfloat162*>(&t), h);
@@ -247,17 +249,19 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
         const float c0 = b[col], c1 = b[col + 1];
 #pragma unroll
         for (int mt = 0; mt < 2; mt++) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            float d[4] = {c0, c1, c0, c1};  // the accumulator starts at the (halved) bias
             mma_bf16_16x8x16(d, ax[mt][0], ax[mt][1], ax[mt][2], ax[mt][3], b0, b1);
-            h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_bf16x2(d[0] + c0, d[1] + c1);
-            h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_bf16x2(d[2] + c0, d[3] + c1);
+            h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_half_bf16x2(d[0], d[1]);
+            h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_half_bf16x2(d[2], d[3]);
         }
     }
     // layer 2: h2 = silu(h1 W2^T + b2)
     unsigned h2[2][4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; nt++) {
-        float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        const int col = nt * 8 + tig * 2;
+        const float c0 = b[64 + col], c1 = b[64 + col + 1];
+        float d[2][4] = {{c0, c1, c0, c1}, {c0, c1, c0, c1}};
 #pragma unroll
         for (int kt = 0; kt < 4; kt++) {
             const __nv_bfloat16* wb = w + Mm::W2 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
@@ -266,12 +270,10 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
             for (int mt = 0; mt < 2; mt++)
                 mma_bf16_16x8x16(d[mt], h1[mt][kt][0], h1[mt][kt][1], h1[mt][kt][2], h1[mt][kt][3], b0, b1);
         }
-        const int col = nt * 8 + tig * 2;
-        const float c0 = b[64 + col], c1 = b[64 + col + 1];
 #pragma unroll
         for (int mt = 0; mt < 2; mt++) {
-            h2[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_bf16x2(d[mt][0] + c0, d[mt][1] + c1);
-            h2[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_bf16x2(d[mt][2] + c0, d[mt][3] + c1);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_half_bf16x2(d[mt][0], d[mt][1]);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_half_bf16x2(d[mt][2], d[mt][3]);
         }
     }
     // layer 3: y = h2 W3^T + b3, transposed to one row per lane through shared memory
