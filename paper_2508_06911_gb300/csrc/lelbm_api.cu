@@ -275,6 +275,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     Model& m = h->model;
     m.lam_store = nullptr;
     m.K = p->K;
+    m.inv_dk = 1.0 / ((double)D + p->K);
     m.nu_s = p->nu_shear;
     m.nu_b = p->nu_bulk;
     m.Pr = p->prandtl;

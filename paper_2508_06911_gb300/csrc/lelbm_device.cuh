@@ -177,7 +177,16 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
     constexpr int NG = Dim<D>::NG;
     const double K = m.K;
     const double rho = M[0];
-    const double irho = 1.0 / rho;
+    // 1 / rho from the FP32 reciprocal and two Newton steps (24 -> 48 -> 53 bits), not
+    // an FP64 division; 1 / (D + K) is a constant of the handle
+    double irho;
+    if (rho > 1e-30 && rho < 1e30) {
+        irho = (double)(1.f / (float)rho);
+        irho = fma(irho, fma(-rho, irho, 1.0), irho);
+        irho = fma(irho, fma(-rho, irho, 1.0), irho);
+    } else {
+        irho = 1.0 / rho;
+    }
     double usq = 0.0, tr = 0.0;
 #pragma unroll
     for (int a = 0; a < D; a++) {
@@ -185,7 +194,7 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
         usq += c.u[a] * c.u[a];
         tr += M[iM2<D>(a, a)];
     }
-    const double RT = ((tr + M[iG0<D>()]) * irho - usq) / ((double)D + K);
+    const double RT = ((tr + M[iG0<D>()]) * irho - usq) * m.inv_dk;
     c.rho = rho;
     c.RT = RT;
     c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);

@@ -18,6 +18,7 @@ enum : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32 = 2 };
 // Physical and numerical constants of one handle (Sec. II, App. C, App. D).
 struct Model {
     double K;           // internal degrees of freedom
+    double inv_dk;      // 1 / (D + K)
     double nu_s;        // kinematic shear viscosity
     double nu_b;        // kinematic bulk viscosity, < 0 -> omega_b = 1
     double Pr;          // Prandtl number

@@ -398,6 +398,7 @@ extern "C" int lelbm_step_noalloc(const lelbm_params* p, const double* m_in, dou
 
     Model m{};
     m.K = p->K;
+    m.inv_dk = 1.0 / ((double)p->dims + p->K);
     m.nu_s = p->nu_shear;
     m.nu_b = p->nu_bulk;
     m.Pr = p->prandtl;
