@@ -232,17 +232,17 @@ static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8
 // Subnormals become zero (before both the deposit and the accounting).
 __device__ __forceinline__ float flush_sub(float v) { return (__float_as_uint(v) & 0x7f800000u) ? v : 0.f; }
 
-// Exact FP32 -> FP64 of a normal number or zero: sign, exponent rebiased from 127 to
-// 1023, mantissa shifted into place; infinities and NaNs take the conversion unit.
+// Exact FP32 -> FP64 of a normal number or zero in integer operations only: sign,
+// exponent rebiased from 127 to 1023 (all ones stays all ones, so infinities stay
+// infinite and NaNs NaN), mantissa shifted into place.  No branch to a conversion
+// instruction: an if-converted one would occupy the FP64 pipe on every call.
 __device__ __forceinline__ double widen(float v) {
     const unsigned int b = __float_as_uint(v);
     const unsigned int e = (b >> 23) & 0xffu;
-    if (e == 0u) return 0.0;
-    if (e == 0xffu) return (double)v;
-    const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) |
-                                    ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(b & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
+    const unsigned int ed = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned int hi = (b & 0x80000000u) | (ed << 20) | ((b & 0x7fffffu) >> 3);
+    const unsigned int lo = b << 29;
+    return e == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
 }
 
 // Compensated FP32 sum: hi + lo carries the exact sum to about 1e-14 relative
