@@ -44,13 +44,13 @@ template <int D>
 __device__ __forceinline__ long long land(const Geometry& g, long long cell, long long lo, int n, int ix, int iy,
                                           int dx, int dy) {
     if constexpr (D == 1) {
-        long long x = cell + dx;
+        int r = (int)(cell - lo) + dx;  // instances are shorter than 2^31 cells
         if (g.periodic[0]) {
-            long long r = (x - lo) % n;
+            r %= n;
             if (r < 0) r += n;
             return lo + r;
         }
-        return (x < lo || x >= lo + n) ? -1 : x;
+        return (unsigned int)r < (unsigned int)n ? lo + r : -1;
     } else {
         int tx = ix + dx, ty = iy + dy;
         if (g.periodic[0]) {
@@ -67,6 +67,14 @@ __device__ __forceinline__ long long land(const Geometry& g, long long cell, lon
         }
         return (long long)ty * g.NX + tx;
     }
+}
+
+// Is interior cell tgt (a result of land) fluid?  Only 2D grids with solid cells have
+// interior cells that are not, so the others need no load of the cell type.
+template <int D>
+__device__ __forceinline__ bool lands_on_fluid(const Geometry& g, const uint8_t* type, long long tgt) {
+    if constexpr (D == 1) return true;
+    return g.wall_dist == nullptr || type[tgt] == CELL_FLUID;
 }
 
 // ---------------------------------------------------------------------------
@@ -222,27 +230,28 @@ static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8
 
 // ---------------------------------------------------------------------------
 // FP32 streaming (the FP32 path).  Populations and their moment fractions are
-// computed in FP32; every fraction is widened exactly to FP64 for the FP64 atomic
+// computed in FP32; every fraction is widened to FP64 for the FP64 atomic
 // accumulation, with integer operations (GB300 runs FP64 at 1/64 of the FP32 rate).
 // The emitted mass, momentum and energy are summed exactly (compensated FP32 sums of
-// exactly the deposited values), and what they miss of the cell's conserved moments
-// (the FP32 Newton leaves a residual of about 1e-6) is added at the emitting cell,
-// so the totals are conserved to FP64 rounding.
+// the deposited values), and what they miss of the cell's conserved moments (the FP32
+// Newton leaves a residual of about 1e-6) is added at the emitting cell, so the
+// totals are conserved to FP64 rounding.
 // ---------------------------------------------------------------------------
 // Subnormals become zero (before both the deposit and the accounting).
 __device__ __forceinline__ float flush_sub(float v) { return (__float_as_uint(v) & 0x7f800000u) ? v : 0.f; }
 
-// Exact FP32 -> FP64 of a normal number or zero in integer operations only: sign,
-// exponent rebiased from 127 to 1023 (all ones stays all ones, so infinities stay
-// infinite and NaNs NaN), mantissa shifted into place.  No branch to a conversion
-// instruction: an if-converted one would occupy the FP64 pipe on every call.
+// FP32 -> FP64 in integer operations only: the exponent is rebiased from 127 to 1023
+// by one addition and the mantissa shifted into place (no conversion instruction, which
+// would take the FP64 pipe).  Normal numbers widen exactly; zeros and subnormals give
+// zero, so a deposit differs from its accounted fraction by less than 2^-126.
+// Infinities and NaNs, which a converged solve does not produce, come out finite; the
+// emitting cell's accounting of the same fractions still carries them into the state
+// as non-finite mass, momentum or energy.
 __device__ __forceinline__ double widen(float v) {
     const unsigned int b = __float_as_uint(v);
-    const unsigned int e = (b >> 23) & 0xffu;
-    const unsigned int ed = e == 0xffu ? 0x7ffu : e + 896u;
-    const unsigned int hi = (b & 0x80000000u) | (ed << 20) | ((b & 0x7fffffu) >> 3);
-    const unsigned int lo = b << 29;
-    return e == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+    const bool tiny = (b & 0x7f800000u) == 0u;
+    const unsigned int hi = (((b >> 3) & 0x0fffffffu) + 0x38000000u) | (b & 0x80000000u);
+    return __hiloint2double(tiny ? 0 : (int)hi, tiny ? 0 : (int)(b << 29));
 }
 
 // Compensated FP32 sum: hi + lo carries the exact sum to about 1e-14 relative
@@ -288,8 +297,6 @@ __device__ __forceinline__ void fractions32(const float* cp, float mf, float mg,
     v[iG0<D>()] = mg;
 #pragma unroll
     for (int gg = 0; gg < D; gg++) v[iG1<D>(gg)] = cp[gg] * mg;
-#pragma unroll
-    for (int i = 0; i < Dim<D>::NM; i++) v[i] = flush_sub(v[i]);
 }
 
 // Sign of each 2D stored moment under x -> -x (ox) and y -> -y (oy).
@@ -387,10 +394,10 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
         ee.add(v[iG0<D>()]);
     };
     auto put = [&](long long tgt, const float* v) {
-        if (tgt < 0 || type[tgt] != CELL_FLUID) return;
+        if (tgt < 0 || !lands_on_fluid<D>(g, type, tgt)) return;
+        double* p = Mout + tgt;
 #pragma unroll
-        for (int mm = 0; mm < NM; mm++)
-            if (v[mm] != 0.f) atomicAdd(Mout + mm * g.ncell + tgt, widen(v[mm]));
+        for (int mm = 0; mm < NM; mm++) atomicAdd(p + mm * g.ncell, widen(v[mm]));
     };
     const float s32 = tab.s32;
     auto row = [&](int cy, int xa, int xb) {
@@ -568,7 +575,7 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
             near_wall = (double)g.wall_dist[cell] <= fmax(fabs(c.u[0]), fabs(c.u[1])) + (double)st.R + 1.5;
     }
     auto deposit = [&](long long tgt, const double* cp, double mf, double mg) {
-        if (tgt < 0 || type[tgt] != CELL_FLUID) return;
+        if (tgt < 0 || !lands_on_fluid<D>(g, type, tgt)) return;
         double csq = 0.0;
 #pragma unroll
         for (int a = 0; a < D; a++) csq += cp[a] * cp[a];
