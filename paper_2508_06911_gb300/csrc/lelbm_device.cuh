@@ -1090,6 +1090,11 @@ __device__ __forceinline__ unsigned long long moment_pass(const CellState<D>& c,
     return q;
 }
 
+// Reciprocal of an LDL^T pivot: IEEE in FP64; in FP32 (the FP32 Newton, which corrects
+// its own step errors) the hardware approximation, within 2 ulp.
+__device__ __forceinline__ double pivot_recip(double d) { return 1.0 / d; }
+__device__ __forceinline__ float pivot_recip(float d) { return __fdividef(1.f, d); }
+
 // LDL^T factorisation of the packed lower triangle and solve A x = b: the same
 // SPD solve as Cholesky without square roots, one reciprocal per column.
 template <typename T, int N>
@@ -1102,7 +1107,7 @@ __device__ __forceinline__ bool ldlt_solve(T* A, T* b) {
         for (int k = 0; k < j; k++) d -= A[tri(j, k)] * A[tri(j, k)] * A[tri(k, k)];
         if (!(d > T(0))) return false;
         A[tri(j, j)] = d;
-        inv[j] = T(1) / d;
+        inv[j] = pivot_recip(d);
 #pragma unroll
         for (int i = j + 1; i < N; i++) {
             T t = A[tri(i, j)];
@@ -1318,24 +1323,33 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
         for (int a = 0; a <= MS::PF; a++) SF[a] = 0.f;
 #pragma unroll
         for (int a = 0; a <= MS::PG; a++) SG[a] = 0.f;
-        for (int k = 0; k <= xb - xa; k++) {
-            const float x = fmaf((float)k, s32, x0);
-            float pw[MS::PF + 1];
-            pw[0] = 1.f;
-#pragma unroll
-            for (int e = 1; e <= MS::PF; e++) pw[e] = pw[e - 1] * x;
+        // one point: powers and exponents as shallow trees (x^6 = (x^3)^2, Estrin's
+        // scheme for the polynomials), so that two points in flight overlap well
+        static_assert(MS::PF == 6 && MS::PG == 4, "moment degrees of the FP32 pass");
+        auto point = [&](float x) {
+            const float x2 = x * x;
+            const float x3 = x2 * x, x4 = x2 * x2;
+            const float pw[7] = {1.f, x, x2, x3, x4, x4 * x, x3 * x3};
             if (doF) {
-                const float f = __expf(-fmaf(fmaf(fmaf(cf3, x, cf2), x, cf1), x, cf0));
+                const float f = __expf(-fmaf(x2, fmaf(cf3, x, cf2), fmaf(cf1, x, cf0)));
 #pragma unroll
                 for (int a = 0; a <= MS::PF; a++) SF[a] = fmaf(pw[a], f, SF[a]);
             }
             if (doG) {
-                const float g = __expf(-fmaf(fmaf(cg2, x, cg1), x, cg0));
+                const float g = __expf(-fmaf(x2, cg2, fmaf(cg1, x, cg0)));
 #pragma unroll
                 for (int a = 0; a <= MS::PG; a++) SG[a] = fmaf(pw[a], g, SG[a]);
             }
+        };
+        const int np = xb - xa + 1;
+        float kf = 0.f;  // the point index as a float (exact), with no conversion per point
+        int k = 0;
+        for (; k + 2 <= np; k += 2, kf += 2.f) {
+            point(fmaf(kf, s32, x0));
+            point(fmaf(kf + 1.f, s32, x0));
         }
-        q += (unsigned long long)(xb - xa + 1);
+        if (k < np) point(fmaf(kf, s32, x0));
+        q += (unsigned long long)np;
         if constexpr (D == 1) {
 #pragma unroll
             for (int a = 0; a <= MS::PF; a++) MF[a] += SF[a];

@@ -405,13 +405,14 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
         float cf[4], cg[3];
         row_coeffs32<D>(lf, lg, y, cf, cg);
         const float x0 = tab.tx(xa);
-        for (int k = 0; k <= xb - xa; k++) {
-            const float x = fmaf((float)k, s32, x0);
+        float kf = 0.f, cxf = (float)xa;  // point index and c_x as floats (exact)
+        for (int k = 0; k <= xb - xa; k++, kf += 1.f, cxf += 1.f) {
+            const float x = fmaf(kf, s32, x0);
             const float f = __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
             const float gp = has_g ? __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0])) : 0.f;
             const int cx = xa + k;
             float cpf[D];
-            cpf[0] = (float)cx;
+            cpf[0] = cxf;
             if constexpr (D == 2) cpf[1] = (float)cy;
             float v[NM];
             fractions32<D>(cpf, mfs * f, mgs * gp, v);
