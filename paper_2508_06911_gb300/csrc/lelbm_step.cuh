@@ -1069,10 +1069,11 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 // from a global counter (the cost of a cell varies with its temperature, q ~
 // (n sqrt RT)^D, so a static split leaves SMs idle at the end).
 // Blocks per SM the compiler must fit (registers): the FP32 variants, whose FP64 fallback
-// is out of line, are light enough in their hot path for three 128-thread blocks; the
-// rest keep the full register file.
+// is out of line and whose per-thread tallies live in shared memory, are light enough in
+// their hot path for four 128-thread blocks (128 registers); the rest keep the full
+// register file.
 template <int D, int PREC>
-constexpr int min_blocks() { return PREC == PREC_FP32 ? 3 : 1; }
+constexpr int min_blocks() { return PREC == PREC_FP32 ? 4 : 1; }
 
 template <int D, int PREC>
 __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel(const __grid_constant__ Model m, const __grid_constant__ Geometry g,
@@ -1092,7 +1093,11 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
     __syncthreads();
-    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
+    // the whole cell update would cost the hot path registers or spills
+    __shared__ ThreadCounters s_tc[128];
+    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -1147,7 +1152,11 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<1>(s_mlp, m.mlp_w, m.mlp_nrm);
-    ThreadCounters tc{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
+    // the whole cell update would cost the hot path registers or spills
+    __shared__ ThreadCounters s_tc[128];
+    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
     double Meq[NM];
     {
