@@ -466,6 +466,62 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
                 put(land<D>(g, cell, lo, n, ix, iy, base[0] + sx, D == 2 ? base[D - 1] + sy : 0), part);
             }
     };
+    // 1D band: fractions of the level-0 point cx and of the child p + s/4 (s = -1, 1)
+    auto point_1d = [&](int cx, float* v) {
+        const float x = tab.tx(cx);
+        const float f = __expf(-fmaf(fmaf(fmaf(lf[3], x, lf[2]), x, lf[1]), x, 1.f + lf[0]));
+        const float gp = has_g ? __expf(-fmaf(fmaf(lg[2], x, lg[1]), x, 1.f + lg[0])) : 0.f;
+        const float cpf[1] = {(float)cx};
+        fractions32<D>(cpf, mfs * f, mgs * gp, v);
+    };
+    auto child_1d = [&](int p, int s, float* v) {
+        const float x = tab.tx(p, 0.25f * (float)s);
+        const float f = 0.5f * __expf(-fmaf(fmaf(fmaf(lf[3], x, lf[2]), x, lf[1]), x, 1.f + lf[0]));
+        const float gp = has_g ? 0.5f * __expf(-fmaf(fmaf(lg[2], x, lg[1]), x, 1.f + lg[0])) : 0.f;
+        const float cpf[1] = {(float)p + 0.25f * (float)s};
+        fractions32<D>(cpf, mfs * f, mgs * gp, v);
+    };
+    auto emit_1d = [&](int t, const float* v) {
+        account(v);
+        put(land<D>(g, cell, lo, n, ix, iy, t, 0), v);
+    };
+    auto band_1d = [&](int a, int b, int x0, int x1) {
+        float cA[NM], cB[NM], v[NM];  // what targets p - 1 and p hold so far
+        if (a - 1 >= x0) {
+            point_1d(a - 1, cA);
+            q++;
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) cA[mm] = 0.f;
+        }
+#pragma unroll
+        for (int mm = 0; mm < NM; mm++) cB[mm] = 0.f;
+        for (int p = a; p <= b; p++) {
+            child_1d(p, -1, v);
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) cA[mm] += 0.25f * v[mm];
+            emit_1d(p - 1, cA);  // target p - 1 is complete
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) cA[mm] = fmaf(0.75f, v[mm], cB[mm]);
+            child_1d(p, 1, v);
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) {
+                cA[mm] = fmaf(0.75f, v[mm], cA[mm]);
+                cB[mm] = 0.25f * v[mm];
+            }
+        }
+        q += 2ull * (unsigned long long)(b - a + 1);
+        emit_1d(b, cA);
+        if (b + 1 <= x1) {
+            point_1d(b + 1, v);
+            q++;
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) cB[mm] += v[mm];
+        }
+        emit_1d(b + 1, cB);
+        const int ex = max(abs(x0), abs(x1));
+        dmax = max(dmax, ex * ex);
+    };
     if (tab.ok) {
         // children of split points at (p + sx/4, cy + sy/4): along an axis the landing
         // point p - 1/4 splits 3/4 : 1/4 over p - 1, p and p + 1/4 splits over p, p + 1
@@ -491,7 +547,21 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
             }
             refined(cpf, tab.tx(p, qx), D == 2 ? tab.ty(cy, qy) : 0.f, D == 1 ? 0.5f : 0.25f, base, w1, cpd);
         };
-        tab.visit(row, child);
+        if constexpr (D == 1) {
+            if (tab.a <= tab.b) {
+                // 1D with split points a..b: one deposit per landing cell.  The children
+                // p -/+ 1/4 (weight 1/2) land 3/4 on p and 1/4 on p -/+ 1; their shares are
+                // summed with each other and with the level-0 points a - 1 and b + 1 that
+                // land on the same cells, and the accounting takes the summed deposits.
+                if (tab.x0 <= tab.a - 2) row(0, tab.x0, tab.a - 2);
+                band_1d(tab.a, tab.b, tab.x0, tab.x1);
+                if (tab.b + 2 <= tab.x1) row(0, tab.b + 2, tab.x1);
+            } else {
+                row(0, tab.x0, tab.x1);
+            }
+        } else {
+            tab.visit(row, child);
+        }
     } else {
         auto leaf = [&](const double* cp, double dC) {
             float cpf[D];
