@@ -255,13 +255,15 @@ __device__ __forceinline__ double widen(float v) {
 }
 
 // Compensated FP32 sum: hi + lo carries the exact sum to about 1e-14 relative
-// (Knuth's two-sum on every addition).
+// (Knuth's two-sum on every addition).  The explicitly rounded operations keep the
+// compiler from fusing a product that produced v into these additions: the sum must be
+// of v as rounded, the value that is deposited.
 struct Acc32 {
     float hi, lo;
     __device__ __forceinline__ void add(float v) {
-        const float s = hi + v;
-        const float bp = s - hi;
-        lo += (hi - (s - bp)) + (v - bp);
+        const float s = __fadd_rn(hi, v);
+        const float bp = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp)));
         hi = s;
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
@@ -466,61 +468,103 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
                 put(land<D>(g, cell, lo, n, ix, iy, base[0] + sx, D == 2 ? base[D - 1] + sy : 0), part);
             }
     };
-    // 1D band: fractions of the level-0 point cx and of the child p + s/4 (s = -1, 1)
-    auto point_1d = [&](int cx, float* v) {
+    // Split points without wall tracing: one deposit per landing cell and child row.  Along
+    // x the children p -/+ 1/4 land 3/4 on p and 1/4 on p -/+ 1; their shares are summed
+    // with each other and with the level-0 points a - 1 and b + 1 of the row (1D), or, in
+    // 2D, per child row cy + sy/4 and then shared 3/4 : 1/4 between rows cy and cy + sy.
+    // The accounting takes the deposits as they are.
+    constexpr float w_child = D == 1 ? 0.5f : 0.25f;
+    // fractions of the level-0 point (cx, cy), and of the child (p + sx/4, cy + sy/4) with
+    // the exponent polynomials cf, cg of its row
+    auto point_v = [&](int cx, int cy, float* v) {
+        float cf[4], cg[3];
+        row_coeffs32<D>(lf, lg, D == 2 ? tab.ty(cy) : 0.f, cf, cg);
         const float x = tab.tx(cx);
-        const float f = __expf(-fmaf(fmaf(fmaf(lf[3], x, lf[2]), x, lf[1]), x, 1.f + lf[0]));
-        const float gp = has_g ? __expf(-fmaf(fmaf(lg[2], x, lg[1]), x, 1.f + lg[0])) : 0.f;
-        const float cpf[1] = {(float)cx};
+        const float f = __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
+        const float gp = has_g ? __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0])) : 0.f;
+        float cpf[D];
+        cpf[0] = (float)cx;
+        if constexpr (D == 2) cpf[1] = (float)cy;
         fractions32<D>(cpf, mfs * f, mgs * gp, v);
     };
-    auto child_1d = [&](int p, int s, float* v) {
-        const float x = tab.tx(p, 0.25f * (float)s);
-        const float f = 0.5f * __expf(-fmaf(fmaf(fmaf(lf[3], x, lf[2]), x, lf[1]), x, 1.f + lf[0]));
-        const float gp = has_g ? 0.5f * __expf(-fmaf(fmaf(lg[2], x, lg[1]), x, 1.f + lg[0])) : 0.f;
-        const float cpf[1] = {(float)p + 0.25f * (float)s};
+    auto child_v = [&](const float* cf, const float* cg, int p, int sx, float cyq, float* v) {
+        const float x = tab.tx(p, 0.25f * (float)sx);
+        const float f = w_child * __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
+        const float gp = has_g ? w_child * __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0])) : 0.f;
+        float cpf[D];
+        cpf[0] = (float)p + 0.25f * (float)sx;
+        if constexpr (D == 2) cpf[1] = cyq;
         fractions32<D>(cpf, mfs * f, mgs * gp, v);
     };
-    auto emit_1d = [&](int t, const float* v) {
+    auto emit = [&](int tx, int ty, const float* v) {
         account(v);
-        put(land<D>(g, cell, lo, n, ix, iy, t, 0), v);
+        put(land<D>(g, cell, lo, n, ix, iy, tx, ty), v);
     };
-    auto band_1d = [&](int a, int b, int x0, int x1) {
-        float cA[NM], cB[NM], v[NM];  // what targets p - 1 and p hold so far
-        if (a - 1 >= x0) {
-            point_1d(a - 1, cA);
-            q++;
+    // column t of child row sy: V (x-summed children) and, when l0, the level-0 point (t, cy)
+    auto emit_col = [&](int t, int cy, int sy, float* V, bool l0) {
+        if constexpr (D == 1) {
+            if (l0) {
+                float v[NM];
+                point_v(t, 0, v);
+#pragma unroll
+                for (int mm = 0; mm < NM; mm++) V[mm] += v[mm];
+            }
+            emit(t, 0, V);
         } else {
+            float o[NM];
 #pragma unroll
-            for (int mm = 0; mm < NM; mm++) cA[mm] = 0.f;
+            for (int mm = 0; mm < NM; mm++) o[mm] = 0.25f * V[mm];
+            emit(t, cy + sy, o);
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) o[mm] = 0.75f * V[mm];
+            if (l0) {
+                float v[NM];
+                point_v(t, cy, v);
+#pragma unroll
+                for (int mm = 0; mm < NM; mm++) o[mm] += v[mm];
+            }
+            emit(t, cy, o);
         }
+    };
+    // child row sy (0 in 1D) of the split points a..b of row cy (level-0 points x0..x1);
+    // with_l0: the level-0 points a - 1 and b + 1 join their columns' deposits
+    auto band_row = [&](int cy, int sy, int a, int b, int x0, int x1, bool with_l0) {
+        float cf[4], cg[3];
+        row_coeffs32<D>(lf, lg, D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f, cf, cg);
+        const float cyq = (float)cy + 0.25f * (float)sy;
+        float cA[NM], cB[NM], v[NM];  // what columns p - 1 and p hold so far
 #pragma unroll
-        for (int mm = 0; mm < NM; mm++) cB[mm] = 0.f;
+        for (int mm = 0; mm < NM; mm++) cA[mm] = cB[mm] = 0.f;
         for (int p = a; p <= b; p++) {
-            child_1d(p, -1, v);
+            child_v(cf, cg, p, -1, cyq, v);
 #pragma unroll
-            for (int mm = 0; mm < NM; mm++) cA[mm] += 0.25f * v[mm];
-            emit_1d(p - 1, cA);  // target p - 1 is complete
+            for (int mm = 0; mm < NM; mm++) cA[mm] = fmaf(0.25f, v[mm], cA[mm]);
+            emit_col(p - 1, cy, sy, cA, with_l0 && p == a && p - 1 >= x0);  // column p - 1 is complete
 #pragma unroll
             for (int mm = 0; mm < NM; mm++) cA[mm] = fmaf(0.75f, v[mm], cB[mm]);
-            child_1d(p, 1, v);
+            child_v(cf, cg, p, 1, cyq, v);
 #pragma unroll
             for (int mm = 0; mm < NM; mm++) {
                 cA[mm] = fmaf(0.75f, v[mm], cA[mm]);
                 cB[mm] = 0.25f * v[mm];
             }
         }
-        q += 2ull * (unsigned long long)(b - a + 1);
-        emit_1d(b, cA);
-        if (b + 1 <= x1) {
-            point_1d(b + 1, v);
-            q++;
-#pragma unroll
-            for (int mm = 0; mm < NM; mm++) cB[mm] += v[mm];
-        }
-        emit_1d(b + 1, cB);
+        emit_col(b, cy, sy, cA, false);
+        emit_col(b + 1, cy, sy, cB, with_l0 && b + 1 <= x1);
+        q += 2ull * (unsigned long long)(b - a + 1) + (with_l0 ? (a - 1 >= x0) + (b + 1 <= x1) : 0);
         const int ex = max(abs(x0), abs(x1));
-        dmax = max(dmax, ex * ex);
+        dmax = max(dmax, ex * ex + cy * cy);
+    };
+    // a row with split points a..b: its level-0 segments and its child rows
+    auto split_row = [&](int cy, int x0, int x1, int a, int b) {
+        if (x0 <= a - 2) row(cy, x0, a - 2);
+        if constexpr (D == 1) {
+            band_row(0, 0, a, b, x0, x1, true);
+        } else {
+            band_row(cy, -1, a, b, x0, x1, true);
+            band_row(cy, 1, a, b, x0, x1, false);
+        }
+        if (b + 2 <= x1) row(cy, b + 2, x1);
     };
     if (tab.ok) {
         // children of split points at (p + sx/4, cy + sy/4): along an axis the landing
@@ -547,20 +591,22 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
             }
             refined(cpf, tab.tx(p, qx), D == 2 ? tab.ty(cy, qy) : 0.f, D == 1 ? 0.5f : 0.25f, base, w1, cpd);
         };
-        if constexpr (D == 1) {
-            if (tab.a <= tab.b) {
-                // 1D with split points a..b: one deposit per landing cell.  The children
-                // p -/+ 1/4 (weight 1/2) land 3/4 on p and 1/4 on p -/+ 1; their shares are
-                // summed with each other and with the level-0 points a - 1 and b + 1 that
-                // land on the same cells, and the accounting takes the summed deposits.
-                if (tab.x0 <= tab.a - 2) row(0, tab.x0, tab.a - 2);
-                band_1d(tab.a, tab.b, tab.x0, tab.x1);
-                if (tab.b + 2 <= tab.x1) row(0, tab.b + 2, tab.x1);
-            } else {
+        if (near_wall) {
+            tab.visit(row, child);  // every share is traced on its own
+        } else if constexpr (D == 1) {
+            if (tab.a <= tab.b)
+                split_row(0, tab.x0, tab.x1, tab.a, tab.b);
+            else
                 row(0, tab.x0, tab.x1);
-            }
         } else {
-            tab.visit(row, child);
+            for (int r = 0; r < tab.nrows; r++) {
+                const char4 e = tab.rows[r];
+                const int cy = tab.y_first + r;
+                if (e.z <= e.w)
+                    split_row(cy, tab.xc + e.x, tab.xc + e.y, tab.xc + e.z, tab.xc + e.w);
+                else if (e.x <= e.y)
+                    row(cy, tab.xc + e.x, tab.xc + e.y);
+            }
         }
     } else {
         auto leaf = [&](const double* cp, double dC) {
