@@ -47,6 +47,7 @@ struct CellState {
     double rho, u[D], RT, sig, inv_sig;
     double cf[Dim<D>::NF];  // fluon constraints in thermal units
     double cg[Dim<D>::NG];  // phonon constraints in thermal units
+    float cf32[Dim<D>::NF], cg32[Dim<D>::NG];  // the same in FP32 (collide32 sets these only)
     bool ok;
 };
 
@@ -266,9 +267,9 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
     // Eq. (IIB10)-(IIB18), thermal units
     const float bulk = -G0n / D;
     const float iRT = 1.f / RTf;
-    c.cf[0] = 1.0;
+    c.cf32[0] = 1.f;
 #pragma unroll
-    for (int a = 0; a < D; a++) c.cf[1 + a] = 0.0;
+    for (int a = 0; a < D; a++) c.cf32[1 + a] = 0.f;
     int j = 1 + D;
 #pragma unroll
     for (int a = 0; a < D; a++)
@@ -276,27 +277,27 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
         for (int b = a; b < D; b++) {
             const float sh = P[a][b] - (a == b ? bulk : 0.f);
             const float mm = (a == b ? rf * RTf : 0.f) + (1.f - wf) * sh + (1.f - wb) * (a == b ? bulk : 0.f);
-            c.cf[j++] = (double)(mm * ir * iRT);
+            c.cf32[j++] = mm * ir * iRT;
         }
     const float s3 = iRT / sf;
 #pragma unroll
     for (int g = 0; g < D; g++)
 #pragma unroll
         for (int a = 0; a < D; a++)
-            c.cf[j++] = (double)((1.f - wh) * ((1.f + 2.f * (a == g)) / (D + 2) * Q[g]) * ir * s3);
+            c.cf32[j++] = (1.f - wh) * ((1.f + 2.f * (a == g)) / (D + 2) * Q[g]) * ir * s3;
     if (K > 0.0) {
         const float nrm = 1.f / (rf * Kf * RTf);
-        c.cg[0] = (double)((rf * Kf * RTf + (1.f - wb) * G0n) * nrm);
+        c.cg32[0] = (rf * Kf * RTf + (1.f - wb) * G0n) * nrm;
 #pragma unroll
-        for (int g = 0; g < D; g++) c.cg[1 + g] = (double)((1.f - wh) * Gn[g] * nrm / sf);
+        for (int g = 0; g < D; g++) c.cg32[1 + g] = (1.f - wh) * Gn[g] * nrm / sf;
         int k = 1 + D;
 #pragma unroll
         for (int a = 0; a < D; a++)
 #pragma unroll
-            for (int b = a; b < D; b++) c.cg[k++] = (a == b) ? 1.0 : 0.0;
+            for (int b = a; b < D; b++) c.cg32[k++] = (a == b) ? 1.f : 0.f;
     } else {
 #pragma unroll
-        for (int k = 0; k < NG; k++) c.cg[k] = 0.0;
+        for (int k = 0; k < NG; k++) c.cg32[k] = 0.f;
     }
 }
 
@@ -485,10 +486,13 @@ struct Stencil {
 // [x0, x1] and the band [a, b] of level-0 points that split into 2^D children at
 // +-1/4 -- so every FP32 pass and the FP32 streaming pass enumerate the same set
 // with FP32 and integer arithmetic only.  1D keeps its one row in registers; 2D
-// keeps up to kRowsMax rows (offsets from floor(u)) in the caller's shared memory.
-// A cell with more levels, more rows or offsets beyond int8 uses Stencil directly.
+// keeps the extents of up to kRowsMax rows (offsets from floor(u)) in the caller's
+// shared memory and the split points of up to kBandMax rows packed in registers.
+// A cell with more levels, rows or split-point rows, or offsets beyond int8, uses
+// Stencil directly.
 // ---------------------------------------------------------------------------
 constexpr int kRowsMax = 48;
+constexpr int kBandMax = 4;  // rows with split points: |y - u_y| <= 3/2 spans at most 4
 
 template <int D>
 struct RowTable {
@@ -496,17 +500,48 @@ struct RowTable {
     int xc, yc;          // floor(u)
     int y_first, nrows;  // 2D rows y_first .. y_first + nrows - 1
     int x0, x1, a, b;    // 1D: the row
-    const char4* rows;   // 2D: (x0, x1, a, b) - xc per row; x0 > x1: empty, a > b: no band
+    const char2* rows;   // 2D: (x0, x1) - xc per row; x0 > x1: empty
+    int band_first, band_n;        // 2D: rows band_first .. + band_n - 1 have split points
+    unsigned long long band;       // 2D: their (a, b) - xc, 16 bits per row
     float fux, fuy;      // (u - floor(u)) / sqrt(RT), FP32
     float s32;           // 1 / sqrt(RT), FP32
 
-    __device__ __forceinline__ void build(const CellState<D>& c, const Stencil<D>& st, char4* buf) {
+    // 2D: records (ea, eb) (offsets from xc) of row r as a split-point row; false when the
+    // rows with split points are not consecutive or more than kBandMax
+    __device__ __forceinline__ bool add_band(int r, int ea, int eb) {
+        if (band_n == 0) band_first = r;
+        if (r != band_first + band_n || band_n == kBandMax) return false;
+        const unsigned long long w = (unsigned long long)(((unsigned)(ea & 0xff)) | ((unsigned)(eb & 0xff) << 8));
+        band |= w << (16 * band_n);
+        band_n++;
+        return true;
+    }
+    // 2D: extents of row r as lattice offsets: level-0 points x0..x1, split points a..b
+    // (a > b: none)
+    __device__ __forceinline__ void row_ext(int r, int& rx0, int& rx1, int& ra, int& rb) const {
+        const char2 e = rows[r];
+        rx0 = xc + e.x;
+        rx1 = xc + e.y;
+        const int k = r - band_first;
+        if ((unsigned)k < (unsigned)band_n) {
+            const unsigned w = (unsigned)(band >> (16 * k));
+            ra = xc + (int)(signed char)(w & 0xffu);
+            rb = xc + (int)(signed char)((w >> 8) & 0xffu);
+        } else {
+            ra = rx1 + 1;
+            rb = rx1;
+        }
+    }
+
+    __device__ __forceinline__ void build(const CellState<D>& c, const Stencil<D>& st, char2* buf) {
         xc = (int)floor(c.u[0]);
         yc = D == 2 ? (int)floor(c.u[D - 1]) : 0;
         s32 = (float)c.inv_sig;
         fux = (float)((c.u[0] - (double)xc) * c.inv_sig);
         fuy = D == 2 ? (float)((c.u[D - 1] - (double)yc) * c.inv_sig) : 0.f;
         rows = buf;
+        band_first = band_n = 0;
+        band = 0ull;
         ok = st.Nr <= 1;
         if (!ok) return;
         const double rr = sqrt(st.rr2), r1 = sqrt(st.rad2[1]);
@@ -569,7 +604,11 @@ struct RowTable {
                     ok = false;
                     return;
                 }
-                buf[r] = make_char4((signed char)lo, (signed char)hi, (signed char)(ea - xc), (signed char)(eb - xc));
+                buf[r] = make_char2((signed char)lo, (signed char)hi);
+                if (ea <= eb && !add_band(r, ea - xc, eb - xc)) {
+                    ok = false;
+                    return;
+                }
             }
         }
     }
@@ -577,7 +616,7 @@ struct RowTable {
     // The same table with FP32 membership tests for the FP32 path, on offsets from
     // floor(u) (so the tests stay exact for the dyadic cases: integer or half-integer u,
     // (R + 1/2)^2, 9/4).
-    __device__ __forceinline__ void build32(const CellState<D>& c, const Stencil<D>& st, char4* buf) {
+    __device__ __forceinline__ void build32(const CellState<D>& c, const Stencil<D>& st, char2* buf) {
         xc = (int)floor(c.u[0]);
         yc = D == 2 ? (int)floor(c.u[D - 1]) : 0;
         s32 = (float)c.inv_sig;
@@ -586,6 +625,8 @@ struct RowTable {
         fux = ux * s32;
         fuy = uy * s32;
         rows = buf;
+        band_first = band_n = 0;
+        band = 0ull;
         ok = st.Nr <= 1;
         if (!ok) return;
         const float rr2f = (float)st.rr2, r12 = (float)st.rad2[1];
@@ -650,7 +691,11 @@ struct RowTable {
                     ok = false;
                     return;
                 }
-                buf[r] = make_char4((signed char)e0, (signed char)e1, (signed char)ea, (signed char)eb);
+                buf[r] = make_char2((signed char)e0, (signed char)e1);
+                if (ea <= eb && !add_band(r, ea, eb)) {
+                    ok = false;
+                    return;
+                }
             }
         }
     }
@@ -675,8 +720,9 @@ struct RowTable {
             one(0, x0, x1, a, b);
         } else {
             for (int r = 0; r < nrows; r++) {
-                const char4 e = rows[r];
-                one(y_first + r, xc + e.x, xc + e.y, xc + e.z, xc + e.w);
+                int rx0, rx1, ra, rb;
+                row_ext(r, rx0, rx1, ra, rb);
+                one(y_first + r, rx0, rx1, ra, rb);
             }
         }
     }
@@ -1207,7 +1253,7 @@ __device__ __forceinline__ int newton_step(const double* Mom, const double* con,
 template <int D>
 __device__ __forceinline__ void solve_fg(const CellState<D>& c, const Stencil<D>& st, const double* conF,
                                          const double* conG, bool has_g, double* lf, double* lg, const Model& m,
-                                         int& sf, int& sg, unsigned long long& npf, unsigned long long& npg) {
+                                         int& sf, int& sg, unsigned int& npf, unsigned int& npg) {
     using MS = MomentSet<D>;
     bool fa = true, ga = has_g;
     sf = 0;
@@ -1392,8 +1438,8 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
 template <int D>
 __device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Stencil<D>& st, const RowTable<D>& tab,
                                                const double* conF, const double* conG, bool has_g, double* lf,
-                                               double* lg, const Model& m, int& sf, int& sg, unsigned long long& npf,
-                                               unsigned long long& npg, unsigned long long& np32) {
+                                               double* lg, const Model& m, int& sf, int& sg, unsigned int& npf,
+                                               unsigned int& npg, unsigned int& np32) {
     using MS = MomentSet<D>;
     constexpr int NF = Basis<D, true>::N, NG = Basis<D, false>::N;
     constexpr float tol32 = 2e-5f;  // thermal units; the FP64 pass takes it to round-off
@@ -1449,17 +1495,11 @@ __device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Sten
 // count the FP32 updates; np32 the points of the FP32 passes.
 template <int D>
 __device__ __forceinline__ bool solve_fg32(const CellState<D>& c, const Stencil<D>& st, const RowTable<D>& tab,
-                                           const double* conF, const double* conG, bool has_g, float* lf32,
-                                           float* lg32, int& sf, int& sg, unsigned long long& np32) {
+                                           const float* cf32, const float* cg32, bool has_g, float* lf32,
+                                           float* lg32, int& sf, int& sg, unsigned int& np32) {
     using MS = MomentSet<D>;
-    constexpr int NF = Basis<D, true>::N, NG = Basis<D, false>::N;
     constexpr float tol32 = 2e-5f;
     constexpr int max32 = 16;
-    float cf32[NF], cg32[NG];
-#pragma unroll
-    for (int j = 0; j < NF; j++) cf32[j] = (float)conF[j];
-#pragma unroll
-    for (int j = 0; j < NG; j++) cg32[j] = (float)conG[j];
     bool fa = true, ga = has_g;
     sf = 0;
     sg = 0;

@@ -3,6 +3,7 @@
 // lelbm_mlp.cu) and the C ABI (lelbm_api.cu, host side).
 #pragma once
 
+#include <type_traits>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -14,6 +15,9 @@ enum : uint8_t { CELL_FLUID = 0, CELL_PAD_IN = 1, CELL_PAD_OUT = 2, CELL_SOLID =
 
 // Arithmetic of the step (the values of LELBM_FP64, LELBM_MIXED, LELBM_FP32).
 enum : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32 = 2 };
+// storage type of a cell's normalised constraints: the FP32 path computes them in FP32
+template <int PREC>
+using Con = typename std::conditional<PREC == PREC_FP32, float, double>::type;
 
 // Physical and numerical constants of one handle (Sec. II, App. C, App. D).
 struct Model {

@@ -58,28 +58,34 @@ __device__ __forceinline__ float silu_grad(float z) {
     return s * (1.f + z * (1.f - s));
 }
 
-template <int D>
+template <int D, bool F32 = false>
 __device__ __forceinline__ void mlp_features(const CellState<D>& c, const Stencil<D>& st, float* x) {
+    // the constraints in FP32: the FP32 path's own (exact), else rounded from FP64
+    float cf[Dim<D>::NF], cg[Dim<D>::NG];
+#pragma unroll
+    for (int j = 0; j < Dim<D>::NF; j++) cf[j] = F32 ? c.cf32[j] : (float)c.cf[j];
+#pragma unroll
+    for (int j = 0; j < Dim<D>::NG; j++) cg[j] = F32 ? c.cg32[j] : (float)c.cg[j];
     if constexpr (D == 1) {
-        x[0] = (float)(c.cf[2] - 1.0);
-        x[1] = (float)c.cf[3];
-        x[2] = (float)(c.cg[0] - 1.0);
-        x[3] = (float)c.cg[1];
+        x[0] = F32 ? cf[2] - 1.f : (float)(c.cf[2] - 1.0);
+        x[1] = cf[3];
+        x[2] = F32 ? cg[0] - 1.f : (float)(c.cg[0] - 1.0);
+        x[3] = cg[1];
         x[4] = (float)((c.u[0] - round(c.u[0])) * c.inv_sig);
         x[5] = (float)c.inv_sig;
         x[6] = (float)(st.R * c.inv_sig);
         x[7] = (float)st.Nr;
     } else {
-        x[0] = (float)(c.cf[3] - 1.0);
-        x[1] = (float)c.cf[4];
-        x[2] = (float)(c.cf[5] - 1.0);
-        x[3] = (float)c.cf[6];
-        x[4] = (float)c.cf[7];
-        x[5] = (float)c.cf[8];
-        x[6] = (float)c.cf[9];
-        x[7] = (float)(c.cg[0] - 1.0);
-        x[8] = (float)c.cg[1];
-        x[9] = (float)c.cg[2];
+        x[0] = F32 ? cf[3] - 1.f : (float)(c.cf[3] - 1.0);
+        x[1] = cf[4];
+        x[2] = F32 ? cf[5] - 1.f : (float)(c.cf[5] - 1.0);
+        x[3] = cf[6];
+        x[4] = cf[7];
+        x[5] = cf[8];
+        x[6] = cf[9];
+        x[7] = F32 ? cg[0] - 1.f : (float)(c.cg[0] - 1.0);
+        x[8] = cg[1];
+        x[9] = cg[2];
         x[10] = (float)((c.u[0] - round(c.u[0])) * c.inv_sig);
         x[11] = (float)((c.u[1] - round(c.u[1])) * c.inv_sig);
         x[12] = (float)c.inv_sig;
@@ -138,12 +144,15 @@ struct MlpMma {
     static constexpr int W3 = W2 + 64 * S2;
     static constexpr int NWS = W3 + N3 * S2;       // BF16 elements of the staged weights
     static constexpr int WARPS = 4;                // warps per block (128 threads)
-    // dynamic shared memory: weights | b1 b2 b3 | normalisation | per-warp X | per-warp O
+    // dynamic shared memory: weights | b1 b2 b3 | normalisation | per-warp X, then O
+    // (a warp's inputs X are dead once loaded into its fragments; its outputs O reuse them)
     static constexpr size_t OFF_B = ((size_t)NWS * 2 + 15) & ~(size_t)15;
     static constexpr size_t OFF_N = OFF_B + sizeof(float) * (64 + 64 + 16);
     static constexpr size_t OFF_X = (OFF_N + sizeof(float) * 2 * (MlpDims<D>::NIN + MlpDims<D>::NOUT) + 15) & ~(size_t)15;
-    static constexpr size_t OFF_O = OFF_X + (size_t)WARPS * 32 * S1 * 2;
-    static constexpr size_t BYTES = OFF_O + (size_t)WARPS * 32 * 16 * sizeof(float);
+    static constexpr size_t WARP_IO = 32 * 16 * sizeof(float);  // >= 32 * S1 BF16
+    static_assert(WARP_IO >= 32 * S1 * 2, "per-warp X fits in the O region");
+    static constexpr size_t OFF_O = OFF_X;
+    static constexpr size_t BYTES = OFF_X + (size_t)WARPS * WARP_IO;
 };
 
 // Stage the weights of the FP32-layout BF16 copy (W) and the FP32 normalisation into
@@ -219,8 +228,8 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
     const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(smem);
     const float* b = reinterpret_cast<const float*>(smem + Mm::OFF_B);
     const float* nr = reinterpret_cast<const float*>(smem + Mm::OFF_N);
-    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + Mm::OFF_X) + warp * 32 * Mm::S1;
-    float* O = reinterpret_cast<float*>(smem + Mm::OFF_O) + warp * 32 * 16;
+    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + Mm::OFF_X + warp * Mm::WARP_IO);
+    float* O = reinterpret_cast<float*>(smem + Mm::OFF_O + warp * Mm::WARP_IO);  // the same bytes as X
     // standardised inputs, one row per lane, zero padded to 16
 #pragma unroll
     for (int m = 0; m < 16; m += 2) {
@@ -239,6 +248,7 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
         ax[mt][2] = ld_b32(r0 + 8);
         ax[mt][3] = ld_b32(r1 + 8);
     }
+    __syncwarp();  // every lane has its fragments: X may be overwritten by O
     // layer 1: h1 = silu(X W1^T + b1)
     unsigned h1[2][4][4];
 #pragma unroll

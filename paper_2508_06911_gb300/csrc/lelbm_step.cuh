@@ -600,12 +600,13 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
                 row(0, tab.x0, tab.x1);
         } else {
             for (int r = 0; r < tab.nrows; r++) {
-                const char4 e = tab.rows[r];
+                int rx0, rx1, ra, rb;
+                tab.row_ext(r, rx0, rx1, ra, rb);
                 const int cy = tab.y_first + r;
-                if (e.z <= e.w)
-                    split_row(cy, tab.xc + e.x, tab.xc + e.y, tab.xc + e.z, tab.xc + e.w);
-                else if (e.x <= e.y)
-                    row(cy, tab.xc + e.x, tab.xc + e.y);
+                if (ra <= rb)
+                    split_row(cy, rx0, rx1, ra, rb);
+                else if (rx0 <= rx1)
+                    row(cy, rx0, rx1);
             }
         }
     } else {
@@ -838,10 +839,12 @@ struct BlockCounters {
 };
 
 // Per-thread tallies.
+// Per-thread tallies (32-bit: a thread adds them to its block's counters at least once per
+// time step, see counters_to_block).
 struct ThreadCounters {
-    unsigned long long cells, pf, pg, p32, redo, retry;
+    unsigned int cells, pf, pg, p32, redo, retry;
     LocalStats ls;
-    unsigned long long mlp_cells;
+    unsigned int mlp_cells;
 };
 
 __device__ __forceinline__ void counters_init(BlockCounters& bc) {
@@ -853,18 +856,25 @@ __device__ __forceinline__ void counters_init(BlockCounters& bc) {
 
 // Adds the thread tallies to the block counters, then (after a barrier) the block
 // counters to the device counters.  Every thread of the block must call it.
-__device__ __forceinline__ void counters_flush(BlockCounters& bc, const ThreadCounters& tc, DevStats* stats) {
-    atomicAdd(&bc.cells, tc.cells);
-    atomicAdd(&bc.p32, tc.p32);
-    atomicAdd(&bc.redo, tc.redo);
-    atomicAdd(&bc.retry, tc.retry);
-    atomicAdd(&bc.pf, tc.pf);
-    atomicAdd(&bc.pg, tc.pg);
+// Adds the thread tallies to the block counters and clears them.
+__device__ __forceinline__ void counters_to_block(BlockCounters& bc, ThreadCounters& tc) {
+    using ull = unsigned long long;
+    atomicAdd(&bc.cells, (ull)tc.cells);
+    atomicAdd(&bc.p32, (ull)tc.p32);
+    if (tc.redo) atomicAdd(&bc.redo, (ull)tc.redo);
+    if (tc.retry) atomicAdd(&bc.retry, (ull)tc.retry);
+    if (tc.pf) atomicAdd(&bc.pf, (ull)tc.pf);
+    if (tc.pg) atomicAdd(&bc.pg, (ull)tc.pg);
     atomicAdd(&bc.pm, tc.ls.points);
-    if (tc.ls.walls) atomicAdd(&bc.walls, (unsigned long long)tc.ls.walls);
-    if (tc.mlp_cells) atomicAdd(&bc.mlpc, tc.mlp_cells);
+    if (tc.ls.walls) atomicAdd(&bc.walls, (ull)tc.ls.walls);
+    if (tc.mlp_cells) atomicAdd(&bc.mlpc, (ull)tc.mlp_cells);
     atomicMax(&bc.q, tc.ls.q_max);
-    atomicMax(&bc.dmax, (unsigned long long)__double_as_longlong(sqrt(tc.ls.disp_max2)));
+    atomicMax(&bc.dmax, (ull)__double_as_longlong(sqrt(tc.ls.disp_max2)));
+    tc = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+}
+
+__device__ __forceinline__ void counters_flush(BlockCounters& bc, ThreadCounters& tc, DevStats* stats) {
+    counters_to_block(bc, tc);
     __syncthreads();
     for (int i = threadIdx.x; i < 64; i += blockDim.x)
         if (bc.hist[i]) atomicAdd(&stats->newton_hist[i], bc.hist[i]);
@@ -899,7 +909,7 @@ __device__ __forceinline__ float start_base(int j, float l0) {
 template <int D>
 __device__ __forceinline__ void fp64_tail(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                           DevStats* stats, long long cell, BlockCounters& bc,
-                                          unsigned long long& pf, unsigned long long& pg, unsigned long long& retry,
+                                          unsigned int& pf, unsigned int& pg, unsigned int& retry,
                                           LocalStats& ls, double* conF, double* conG, const CellState<D>& c,
                                           const Stencil<D>& st, double* lf, double* lg, bool learned) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
@@ -984,17 +994,23 @@ __device__ __forceinline__ void fp64_tail(const Model& m, const Geometry& g, con
 }
 
 struct TailCounts {
-    unsigned long long pf, pg, retry;
+    unsigned int pf, pg, retry;
     LocalStats ls;
 };
 
-// fp64_tail from Eq. (IID13), out of line, for the FP32 path's rare failed solves.
+// fp64_tail from Eq. (IID13), out of line, for the FP32 path's rare failed solves; the
+// FP32 constraints cf32, cg32 are widened to FP64.
 template <int D>
 static __device__ __noinline__ TailCounts fp64_tail_cold(const Model& m, const Geometry& g, const uint8_t* type,
                                                          double* Mout, DevStats* stats, long long cell,
-                                                         BlockCounters* bc, double* conF, double* conG,
-                                                         const CellState<D> c, const Stencil<D> st) {
+                                                         BlockCounters* bc, const float* cf32, const float* cg32,
+                                                         CellState<D> c, const Stencil<D> st) {
     TailCounts t{0, 0, 0, {0, 0.0, 0, 0}};
+    double conF[Dim<D>::NF], conG[Dim<D>::NG];
+#pragma unroll
+    for (int j = 0; j < Dim<D>::NF; j++) c.cf[j] = conF[j] = (double)cf32[j];
+#pragma unroll
+    for (int j = 0; j < Dim<D>::NG; j++) c.cg[j] = conG[j] = (double)cg32[j];
     double lf[Dim<D>::NF], lg[Dim<D>::NG];
     maxwell_start_fg<D, Dim<D>::NF, Dim<D>::NG>(c.RT, lf, lg);
     fp64_tail<D>(m, g, type, Mout, stats, cell, *bc, t.pf, t.pg, t.retry, t.ls, conF, conG, c, st, lf, lg, false);
@@ -1032,8 +1048,8 @@ __device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, 
 template <int D, int PREC>
 __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                             DevStats* stats, long long cell, BlockCounters& bc, ThreadCounters& tc,
-                                            double* conF, double* conG, const CellState<D>& c, const Stencil<D>& st,
-                                            const float* dl, char4* rowbuf) {
+                                            Con<PREC>* conF, Con<PREC>* conG, const CellState<D>& c, const Stencil<D>& st,
+                                            const float* dl, char2* rowbuf) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     tc.cells++;
     const bool has_g = m.K > 0.0;
@@ -1105,9 +1121,9 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
         }
     }
 #pragma unroll
-    for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
+    for (int j = 0; j < NF; j++) conF[j] = PREC == PREC_FP32 ? c.cf32[j] : c.cf[j];
 #pragma unroll
-    for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
+    for (int j = 0; j < NG; j++) conG[j] = PREC == PREC_FP32 ? c.cg32[j] : c.cg[j];
     int sf, sg;
     RowTable<D> tab;
     if constexpr (PREC == PREC_FP32)
@@ -1198,13 +1214,13 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
                                                           DevStats* stats, unsigned long long* work) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ BlockCounters bc;
-    __shared__ double s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
+    __shared__ Con<PREC> s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
     // 2D row tables of the FP32 passes (one per thread)
-    __shared__ char4 s_rows[(D == 2 && PREC != PREC_FP64) ? 128 : 1][(D == 2 && PREC != PREC_FP64) ? kRowsMax : 1];
+    __shared__ char2 s_rows[(D == 2 && PREC != PREC_FP64) ? 128 : 1][(D == 2 && PREC != PREC_FP64) ? kRowsMax : 1];
     extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
-    double* conF = s_con[threadIdx.x];
-    double* conG = conF + NF;
-    char4* rowbuf = (D == 2 && PREC != PREC_FP64) ? s_rows[threadIdx.x] : nullptr;
+    Con<PREC>* conF = s_con[threadIdx.x];
+    Con<PREC>* conG = conF + NF;
+    char2* rowbuf = (D == 2 && PREC != PREC_FP64) ? s_rows[threadIdx.x] : nullptr;
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
@@ -1231,7 +1247,7 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
         const bool use_mlp = mlp;
         if (use_mlp) {
             float xin[MlpDims<D>::NIN];
-            if (ok) mlp_features<D>(c, st, xin);
+            if (ok) mlp_features<D, PREC == PREC_FP32>(c, st, xin);
             warp_mlp<D>(s_mlp, xin, ok, dl);
             if (ok) tc.mlp_cells++;
         }
@@ -1259,12 +1275,12 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
                                                                const int* inst_pad, int* steps_left, int nsteps) {
     constexpr int D = 1, NM = Dim<1>::NM, NF = Dim<1>::NF, NG = Dim<1>::NG;
     __shared__ BlockCounters bc;
-    __shared__ double s_con[128][NF + NG];
+    __shared__ Con<PREC> s_con[128][NF + NG];
     __shared__ unsigned int s_next;
     __shared__ int s_inst;
     extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
-    double* conF = s_con[threadIdx.x];
-    double* conG = conF + NF;
+    Con<PREC>* conF = s_con[threadIdx.x];
+    Con<PREC>* conG = conF + NF;
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<1>(s_mlp, m.mlp_w, m.mlp_nrm);
@@ -1333,7 +1349,7 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
                 const bool use_mlp = mlp;
                 if (use_mlp) {
                     float xin[MlpDims<D>::NIN];
-                    if (ok) mlp_features<D>(c, st, xin);
+                    if (ok) mlp_features<D, PREC == PREC_FP32>(c, st, xin);
                     warp_mlp<D>(s_mlp, xin, ok, dl);
                     if (ok) tc.mlp_cells++;
                 }
@@ -1341,6 +1357,7 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
                     finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st,
                                          use_mlp ? dl : nullptr, nullptr);
             }
+            counters_to_block(bc, tc);  // keeps the 32-bit tallies of a long launch small
             __syncthreads();
         }
         if (k & 1) {  // the result is in B: copy the block back to A
