@@ -287,6 +287,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     m.max_refine = p->max_refine;
     m.tol = p->tol;
     m.max_iter = p->max_newton;
+    set_fp32_params(m);
 
     Geometry& g = h->geo;
     g.D = D;

@@ -48,6 +48,7 @@ struct CellState {
     double cf[Dim<D>::NF];  // fluon constraints in thermal units
     double cg[Dim<D>::NG];  // phonon constraints in thermal units
     float cf32[Dim<D>::NF], cg32[Dim<D>::NG];  // the same in FP32 (collide32 sets these only)
+    float RT32, sig32, isig32;                 // RT, sqrt(RT), 1/sqrt(RT) in FP32 (collide32)
     bool ok;
 };
 
@@ -201,9 +202,12 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
     c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
     if (!c.ok) return;
     {
-        const float sf = sqrtf((float)RT);  // FP32 is enough: it only scales FP32 coordinates
+        c.RT32 = (float)RT;
+        const float sf = sqrtf(c.RT32);  // FP32 is enough: it only scales FP32 coordinates
+        c.sig32 = sf;
+        c.isig32 = 1.f / sf;
         c.sig = (double)sf;
-        c.inv_sig = (double)(1.f / sf);
+        c.inv_sig = (double)c.isig32;
     }
     // Eq. (IIB9) in FP64
     float P[D][D];
@@ -233,12 +237,12 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
     for (int g = 0; g < D; g++) Gn[g] = (float)(M[iG1<D>(g)] - c.u[g] * G0);
 
     // App. C and App. D in FP32
-    const float rf = (float)rho, RTf = (float)RT, sf = (float)c.sig, Kf = (float)K;
-    const float inv_f = (float)m.nu_s / RTf + 0.5f;
+    const float rf = (float)rho, RTf = c.RT32, sf = c.sig32, Kf = m.K32;
+    const float inv_f = m.nu_s32 / RTf + 0.5f;
     float wf = 1.f / inv_f;
     const float fb = 2.f / D - 2.f / (D + Kf);
-    float wb = (m.nu_b < 0.0 || fb <= 0.f) ? 1.f : 1.f / ((float)m.nu_b / (RTf * fb) + 0.5f);
-    float wh = 1.f / ((inv_f - 0.5f) / (float)m.Pr + 0.5f);
+    float wb = (m.nu_b32 < 0.f || fb <= 0.f) ? 1.f : 1.f / (m.nu_b32 / (RTf * fb) + 0.5f);
+    float wh = 1.f / ((inv_f - 0.5f) / m.Pr32 + 0.5f);
     const float ir = 1.f / rf;
     if (m.limiter) {
         float s2 = 0.f, s3 = 0.f;
@@ -285,7 +289,7 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
 #pragma unroll
         for (int a = 0; a < D; a++)
             c.cf32[j++] = (1.f - wh) * ((1.f + 2.f * (a == g)) / (D + 2) * Q[g]) * ir * s3;
-    if (K > 0.0) {
+    if (Kf > 0.f) {
         const float nrm = 1.f / (rf * Kf * RTf);
         c.cg32[0] = (rf * Kf * RTf + (1.f - wb) * G0n) * nrm;
 #pragma unroll
@@ -338,21 +342,17 @@ struct Stencil {
     __device__ __forceinline__ void init32(const CellState<D>& c, const Model& m) {
 #pragma unroll
         for (int a = 0; a < D; a++) u[a] = c.u[a];
-        const float sf = (float)c.sig;
-        float r = roundf((float)m.n_conf * sf);
-        if (r < (float)m.r_min) r = (float)m.r_min;
+        const float sf = c.sig32;
+        float r = roundf(m.n_conf32 * sf);
+        if (r < m.r_min32) r = m.r_min32;
         R = (int)r;
         const float rr = (float)R + 0.5f;
         rr2 = (double)(rr * rr);
-        float nr = roundf(1.f / ((float)m.refine_div * sf));
+        float nr = roundf(1.f / (m.refine_div32 * sf));
         if (nr > (float)m.max_refine) nr = (float)m.max_refine;
         Nr = (int)nr;
-        float rad = (float)m.refine_rad;
 #pragma unroll
-        for (int L = 0; L < 5; L++) {
-            rad2[L] = (double)(rad * rad);
-            rad *= 0.5f;
-        }
+        for (int L = 0; L < 5; L++) rad2[L] = m.rad2_32[L];
     }
 
     __device__ __forceinline__ double dist2(const double* c) const {
@@ -619,7 +619,7 @@ struct RowTable {
     __device__ __forceinline__ void build32(const CellState<D>& c, const Stencil<D>& st, char2* buf) {
         xc = (int)floor(c.u[0]);
         yc = D == 2 ? (int)floor(c.u[D - 1]) : 0;
-        s32 = (float)c.inv_sig;
+        s32 = c.isig32;
         const float ux = (float)(c.u[0] - (double)xc);
         const float uy = D == 2 ? (float)(c.u[D - 1] - (double)yc) : 0.f;
         fux = ux * s32;
@@ -629,8 +629,8 @@ struct RowTable {
         band = 0ull;
         ok = st.Nr <= 1;
         if (!ok) return;
-        const float rr2f = (float)st.rr2, r12 = (float)st.rad2[1];
-        const float rr = (float)st.R + 0.5f, r1 = sqrtf(r12);
+        const float rr = (float)st.R + 0.5f, rr2f = rr * rr, r12 = (float)st.rad2[1];
+        const float r1 = sqrtf(r12);
         // extents, as offsets from xc, of the row at squared y-distance dy2
         auto extents = [&](float dy2, float s, int& e0, int& e1, int& ea, int& eb) {
             auto d2 = [&](int k) {
@@ -1334,22 +1334,19 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
     auto add_point = [&](float x, float y, float w) {
         float cf[4], cg[3];
         row_coeffs32<D>(lf, lg, y, cf, cg);
-        float px[MS::PF + 1], py[MS::PF + 1];
-        px[0] = py[0] = 1.f;
-#pragma unroll
-        for (int k = 1; k <= MS::PF; k++) {
-            px[k] = px[k - 1] * x;
-            py[k] = py[k - 1] * y;
-        }
+        static_assert(MS::PF == 6, "moment degree of the FP32 pass");
+        const float x2 = x * x, x3 = x2 * x, x4 = x2 * x2, y2 = y * y, y3 = y2 * y, y4 = y2 * y2;
+        const float px[7] = {1.f, x, x2, x3, x4, x4 * x, x3 * x3};
+        const float py[7] = {1.f, y, y2, y3, y4, y4 * y, y3 * y3};
         if (doF) {
-            const float f = w * __expf(-fmaf(fmaf(fmaf(cf[3], x, cf[2]), x, cf[1]), x, cf[0]));
+            const float f = w * __expf(-fmaf(x2, fmaf(cf[3], x, cf[2]), fmaf(cf[1], x, cf[0])));
 #pragma unroll
             for (int b = 0; b <= (D == 2 ? MS::PF : 0); b++)
 #pragma unroll
                 for (int a = 0; a + b <= MS::PF; a++) MF[tix(a, b, MS::PF)] += px[a] * py[b] * f;
         }
         if (doG) {
-            const float g = w * __expf(-fmaf(fmaf(cg[2], x, cg[1]), x, cg[0]));
+            const float g = w * __expf(-fmaf(x2, cg[2], fmaf(cg[1], x, cg[0])));
 #pragma unroll
             for (int b = 0; b <= (D == 2 ? MS::PG : 0); b++)
 #pragma unroll

@@ -40,7 +40,27 @@ struct Model {
     const float* mlp_nrm;          // learned warm start: normalisation
     float* lam_store;              // stored warm start: per-cell multiplier corrections, SoA
                                    // [NF + NG][ncell], or null
+    // FP32 copies for the FP32 path (set by set_fp32_params)
+    float K32, nu_s32, nu_b32, Pr32, n_conf32, r_min32, refine_div32;
+    double rad2_32[5];  // squared refinement radii, FP32 arithmetic: (refine_rad / 2^L)^2
 };
+
+// Fills the FP32 copies of the model parameters (host).
+inline void set_fp32_params(Model& m) {
+    m.K32 = (float)m.K;
+    m.nu_s32 = (float)m.nu_s;
+    m.nu_b32 = (float)m.nu_b;
+    m.Pr32 = (float)m.Pr;
+    m.n_conf32 = (float)m.n_conf;
+    m.r_min32 = (float)m.r_min;
+    m.refine_div32 = (float)m.refine_div;
+    float rad = (float)m.refine_rad;
+    for (int L = 0; L < 5; L++) {
+        const float r2 = rad * rad;
+        m.rad2_32[L] = (double)r2;
+        rad *= 0.5f;
+    }
+}
 
 // Padded-grid geometry.  2D: one instance, cell = iy * NX + ix.
 // 1D: n_inst instances concatenated, each [pad | n | pad] (no pads if periodic).

@@ -72,8 +72,8 @@ __device__ __forceinline__ void mlp_features(const CellState<D>& c, const Stenci
         x[2] = F32 ? cg[0] - 1.f : (float)(c.cg[0] - 1.0);
         x[3] = cg[1];
         x[4] = (float)((c.u[0] - round(c.u[0])) * c.inv_sig);
-        x[5] = (float)c.inv_sig;
-        x[6] = (float)(st.R * c.inv_sig);
+        x[5] = F32 ? c.isig32 : (float)c.inv_sig;
+        x[6] = F32 ? (float)st.R * c.isig32 : (float)(st.R * c.inv_sig);
         x[7] = (float)st.Nr;
     } else {
         x[0] = F32 ? cf[3] - 1.f : (float)(c.cf[3] - 1.0);
@@ -88,8 +88,8 @@ __device__ __forceinline__ void mlp_features(const CellState<D>& c, const Stenci
         x[9] = cg[2];
         x[10] = (float)((c.u[0] - round(c.u[0])) * c.inv_sig);
         x[11] = (float)((c.u[1] - round(c.u[1])) * c.inv_sig);
-        x[12] = (float)c.inv_sig;
-        x[13] = (float)(st.R * c.inv_sig);
+        x[12] = F32 ? c.isig32 : (float)c.inv_sig;
+        x[13] = F32 ? (float)st.R * c.isig32 : (float)(st.R * c.inv_sig);
         x[14] = (float)st.Nr;
     }
 }

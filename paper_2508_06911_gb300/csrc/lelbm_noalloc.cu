@@ -410,6 +410,7 @@ extern "C" int lelbm_step_noalloc(const lelbm_params* p, const double* m_in, dou
     m.max_refine = p->max_refine;
     m.tol = p->tol;
     m.max_iter = p->max_newton;
+    set_fp32_params(m);
 
     Topo t{};
     t.D = p->dims;

@@ -1062,7 +1062,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
         for (int k = 0; k < MlpDims<D>::NOUT; k++) dl_ok = dl_ok && isfinite(dl[k]);
     }
     if constexpr (PREC == PREC_FP32) {
-        maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+        maxwell_start32<D, NF, NG>(c.RT32, lf32, lg32);
         if (dl_ok) {
 #pragma unroll
             for (int j = 0; j < NF; j++) lf32[j] += dl[j];
@@ -1088,7 +1088,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
                 }
             }
             learned = fin;
-            if (!fin) maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+            if (!fin) maxwell_start32<D, NF, NG>(c.RT32, lf32, lg32);
         }
     } else {
         maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
@@ -1135,7 +1135,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
         bool ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
         if (!ok32 && learned) {
             tc.retry++;
-            maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+            maxwell_start32<D, NF, NG>(c.RT32, lf32, lg32);
             learned = false;
             ok32 = solve_fg32<D>(c, st, tab, conF, conG, has_g, lf32, lg32, sf, sg, tc.p32);
         }
@@ -1143,7 +1143,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
             atomicAdd(&bc.hist[sf < 63 ? sf : 63], 1ull);
             if (has_g) atomicAdd(&bc.hist[sg < 63 ? sg : 63], 1ull);
             if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), for the next step
-                const float l0 = -1.f + 0.5f * D * logf(6.2831853071795865f * (float)c.RT);
+                const float l0 = -1.f + 0.5f * D * logf(6.2831853071795865f * c.RT32);
 #pragma unroll
                 for (int j = 0; j < NF; j++)
                     m.lam_store[(long long)j * g.ncell + cell] = lf32[j] - start_base<D>(j, l0);
