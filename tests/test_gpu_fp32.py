@@ -1,14 +1,14 @@
 """FP32 path (LELBM_FP32) against the CPU oracle.
 
-The FP32 path iterates the EPR Newton in FP32 to an FP32 residual of 2e-5 (thermal
-units) plus one polishing update, evaluates the streamed populations in FP32 and
-accumulates their moment fractions in FP64.  The multipliers are therefore accurate to
-the FP32 noise floor only, about 1e-6 of the constraints, so a step differs from the
-oracle by about that much; the bound used here per step, 2e-5 of each moment's largest
-magnitude, is the FP32 tolerance itself.  After a full run the L1 density error must be
-within 1e-4 of the oracle (the accuracy the FP32 path is held to).  Mass, momentum and
-energy are conserved exactly (to FP64 rounding) by the compensated accounting of the
-emitted fractions, which these tests check to 1e-13 per step.
+The FP32 path iterates the EPR Newton in FP32 to an FP32 residual of 3e-4 (thermal
+units) plus one polishing update (which, Newton converging quadratically, leaves about
+1e-7), evaluates the streamed populations in FP32 and accumulates their moment fractions
+in FP64.  The multipliers are therefore accurate to the FP32 noise floor only, about
+1e-6 of the constraints, so a step differs from the oracle by about that much; the bound
+used here per step is 2e-5 of each moment's largest magnitude.  After a full run the L1
+density error must be within 1e-4 of the oracle (the accuracy the FP32 path is held to).
+Mass, momentum and energy are conserved exactly (to FP64 rounding) by the compensated
+accounting of the emitted fractions, which these tests check to 1e-13 per step.
 """
 import numpy as np
 import pytest
