@@ -500,71 +500,86 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
         account(v);
         put(land<D>(g, cell, lo, n, ix, iy, tx, ty), v);
     };
-    // column t of child row sy: V (x-summed children) and, when l0, the level-0 point (t, cy)
-    auto emit_col = [&](int t, int cy, int sy, float* V, bool l0) {
-        if constexpr (D == 1) {
-            if (l0) {
-                float v[NM];
-                point_v(t, 0, v);
-#pragma unroll
-                for (int mm = 0; mm < NM; mm++) V[mm] += v[mm];
-            }
-            emit(t, 0, V);
+    // column t of child row sy: V (x-summed children) and, when l0, the level-0 point (t, cy).
+    // 1D: one deposit V (+ the point); 2D: V/4 on row cy + sy, 3V/4 (+ the point) on row cy.
+    // One call site each for emit and point_v keeps the code of this path short.
+    auto emit_col = [&](int t, int cy, int sy, const float* V, bool l0) {
+        float lv[NM];
+        if (l0) {
+            point_v(t, cy, lv);
         } else {
+#pragma unroll
+            for (int mm = 0; mm < NM; mm++) lv[mm] = 0.f;
+        }
+#pragma unroll 1
+        for (int k = (D == 2 ? 0 : 1); k < 2; k++) {
+            const float w = D == 1 ? 1.f : (k == 0 ? 0.25f : 0.75f);
             float o[NM];
 #pragma unroll
-            for (int mm = 0; mm < NM; mm++) o[mm] = 0.25f * V[mm];
-            emit(t, cy + sy, o);
-#pragma unroll
-            for (int mm = 0; mm < NM; mm++) o[mm] = 0.75f * V[mm];
-            if (l0) {
-                float v[NM];
-                point_v(t, cy, v);
-#pragma unroll
-                for (int mm = 0; mm < NM; mm++) o[mm] += v[mm];
-            }
-            emit(t, cy, o);
+            for (int mm = 0; mm < NM; mm++) o[mm] = k == 0 ? w * V[mm] : fmaf(w, V[mm], lv[mm]);
+            emit(t, k == 0 ? cy + sy : cy, o);
         }
     };
     // child row sy (0 in 1D) of the split points a..b of row cy (level-0 points x0..x1);
-    // with_l0: the level-0 points a - 1 and b + 1 join their columns' deposits
+    // with_l0: the level-0 points a - 1 and b + 1 join their columns' deposits.  The
+    // children are taken in order p - 1/4, p + 1/4, ...; each adds w_lo of its fractions
+    // to column lo (cA) and w_hi to column lo + 1 (cB): (p - 1, p) with (1/4, 3/4) for the
+    // left child, (p, p + 1) with (3/4, 1/4) for the right one.  After a left child,
+    // column p - 1 is complete.  Two empty left children past b emit columns b and b + 1.
     auto band_row = [&](int cy, int sy, int a, int b, int x0, int x1, bool with_l0) {
         float cf[4], cg[3];
         row_coeffs32<D>(lf, lg, D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f, cf, cg);
         const float cyq = (float)cy + 0.25f * (float)sy;
-        float cA[NM], cB[NM], v[NM];  // what columns p - 1 and p hold so far
+        float cA[NM], cB[NM], v[NM];
 #pragma unroll
         for (int mm = 0; mm < NM; mm++) cA[mm] = cB[mm] = 0.f;
-        for (int p = a; p <= b; p++) {
-            child_v(cf, cg, p, -1, cyq, v);
+        const int nch = 2 * (b - a + 1);
+#pragma unroll 1
+        for (int h = 0; h <= nch + 2; h++) {
+            const int p = a + (h >> 1);
+            const bool left = (h & 1) == 0;
+            if (h < nch) {
+                child_v(cf, cg, p, left ? -1 : 1, cyq, v);
+            } else {
 #pragma unroll
-            for (int mm = 0; mm < NM; mm++) cA[mm] = fmaf(0.25f, v[mm], cA[mm]);
-            emit_col(p - 1, cy, sy, cA, with_l0 && p == a && p - 1 >= x0);  // column p - 1 is complete
-#pragma unroll
-            for (int mm = 0; mm < NM; mm++) cA[mm] = fmaf(0.75f, v[mm], cB[mm]);
-            child_v(cf, cg, p, 1, cyq, v);
+                for (int mm = 0; mm < NM; mm++) v[mm] = 0.f;
+            }
+            const float w_lo = left ? 0.25f : 0.75f, w_hi = left ? 0.75f : 0.25f;
 #pragma unroll
             for (int mm = 0; mm < NM; mm++) {
-                cA[mm] = fmaf(0.75f, v[mm], cA[mm]);
-                cB[mm] = 0.25f * v[mm];
+                cA[mm] = fmaf(w_lo, v[mm], cA[mm]);
+                cB[mm] = fmaf(w_hi, v[mm], cB[mm]);
+            }
+            if (left) {
+                const int t = p - 1;  // complete
+                emit_col(t, cy, sy, cA, with_l0 && ((t == a - 1 && t >= x0) || (t == b + 1 && t <= x1)));
+#pragma unroll
+                for (int mm = 0; mm < NM; mm++) {
+                    cA[mm] = cB[mm];
+                    cB[mm] = 0.f;
+                }
             }
         }
-        emit_col(b, cy, sy, cA, false);
-        emit_col(b + 1, cy, sy, cB, with_l0 && b + 1 <= x1);
-        q += 2ull * (unsigned long long)(b - a + 1) + (with_l0 ? (a - 1 >= x0) + (b + 1 <= x1) : 0);
+        q += (unsigned long long)nch + (with_l0 ? (a - 1 >= x0) + (b + 1 <= x1) : 0);
         const int ex = max(abs(x0), abs(x1));
         dmax = max(dmax, ex * ex + cy * cy);
     };
     // a row with split points a..b: its level-0 segments and its child rows
     auto split_row = [&](int cy, int x0, int x1, int a, int b) {
-        if (x0 <= a - 2) row(cy, x0, a - 2);
-        if constexpr (D == 1) {
-            band_row(0, 0, a, b, x0, x1, true);
-        } else {
-            band_row(cy, -1, a, b, x0, x1, true);
-            band_row(cy, 1, a, b, x0, x1, false);
+#pragma unroll 1
+        for (int sy = (D == 2 ? -1 : 0); sy <= (D == 2 ? 1 : 0); sy += 2) band_row(cy, sy, a, b, x0, x1, sy <= 0);
+    };
+    // the level-0 segments of a row: x0..x1 less the split points a..b and their
+    // neighbours a - 1, b + 1 (which split_row deposits)
+    auto row_segments = [&](int cy, int x0, int x1, int a, int b) {
+        const bool band = a <= b;
+#pragma unroll 1
+        for (int k = 0; k < (band ? 2 : 1); k++) {
+            const int xa = band ? (k == 0 ? x0 : b + 2) : x0;
+            const int xb = band ? (k == 0 ? a - 2 : x1) : x1;
+            if (xa <= xb) row(cy, xa, xb);
         }
-        if (b + 2 <= x1) row(cy, b + 2, x1);
+        if (band) split_row(cy, x0, x1, a, b);
     };
     if (tab.ok) {
         // children of split points at (p + sx/4, cy + sy/4): along an axis the landing
@@ -594,19 +609,12 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
         if (near_wall) {
             tab.visit(row, child);  // every share is traced on its own
         } else if constexpr (D == 1) {
-            if (tab.a <= tab.b)
-                split_row(0, tab.x0, tab.x1, tab.a, tab.b);
-            else
-                row(0, tab.x0, tab.x1);
+            row_segments(0, tab.x0, tab.x1, tab.a, tab.b);
         } else {
             for (int r = 0; r < tab.nrows; r++) {
                 int rx0, rx1, ra, rb;
                 tab.row_ext(r, rx0, rx1, ra, rb);
-                const int cy = tab.y_first + r;
-                if (ra <= rb)
-                    split_row(cy, rx0, rx1, ra, rb);
-                else if (rx0 <= rx1)
-                    row(cy, rx0, rx1);
+                row_segments(tab.y_first + r, rx0, rx1, ra, rb);
             }
         }
     } else {

@@ -203,13 +203,20 @@ def test_fp32_long_run_against_fp64_path(start):
 
 
 def test_fp32_long_run_2d_against_fp64_path():
-    """200 steps of the 2D four-quadrant problem at 128^2, FP32 against FP64."""
+    """200 steps of the 2D four-quadrant problem at 128^2, FP32 against FP64.
+
+    The two runs go one after the other.  Run side by side on two streams, the FP32 run
+    sees a different order of its FP64 atomic additions, and on this flow that order
+    decides, in some executions, whether a cell near a stencil threshold (N_r or R_ac,
+    both rounded from sqrt(RT)) takes the other stencil: the L1 error then rises from
+    about 1e-6 to 1e-3, while every step stays within FP32 noise of the oracle."""
     w = W.riemann_2d(n=128, seed_index=24)
     mask = interior_mask_2d(w)
     a = Solver.grid2d(w)
     b = Solver.grid2d(w, **FP32)
     b.set_warmstart(True)
     a.step(200)
+    a.synchronize()
     b.step(200)
     l1 = l1_rel(b.get_moments()[0, mask], a.get_moments()[0, mask])
     a.close()
