@@ -70,11 +70,12 @@ extern "C" {
                          miss); state, collision and accumulation in FP64          */
 #define LELBM_FP32 2  /* EPR Newton (passes and solves) and the streaming pass in
                          FP32, to an FP32 residual of 3e-4 (thermal units) plus one
-                         polishing update; moment fractions widened exactly to FP64
-                         and accumulated in FP64; the emitted mass, momentum and
-                         energy are summed exactly and their shortfall kept in the
-                         emitting cell, so totals are conserved to FP64 rounding.
-                         State, collision and stencil geometry in FP64.  A cell
+                         polishing update; moment fractions widened to FP64 (exact
+                         for normal numbers, subnormals dropped) and accumulated in
+                         FP64; the emitted mass, momentum and energy are summed
+                         exactly and their shortfall kept in the emitting cell, so
+                         totals are conserved to FP64 rounding.  State, macroscopic
+                         variables and non-equilibrium moments in FP64.  A cell
                          whose FP32 solve fails is solved by the FP64 EPR.  Error
                          against LELBM_FP64: about 1e-6 relative per step.         */
 
