@@ -190,7 +190,7 @@ __device__ __forceinline__ void mlp_stage_mma(unsigned char* smem, const __nv_bf
 
 __device__ __forceinline__ void mma_bf16_16x8x16(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
                                                  unsigned b0, unsigned b1) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -198,6 +198,16 @@ __device__ __forceinline__ void mma_bf16_16x8x16(float* d, unsigned a0, unsigned
 }
 
 __device__ __forceinline__ unsigned ld_b32(const __nv_bfloat16* p) { return *reinterpret_cast<const unsigned*>(p); }
+
+// Four 8x8 BF16 tiles from shared memory in one instruction: lane L gives the address of
+// row L % 8 of tile L / 8 (16-byte aligned); each lane receives, of every tile, the pair
+// of row lane / 4 at columns 2 (lane % 4), +1 -- the fragment layout of mma.m16n8k16.
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
 
 __device__ __forceinline__ void st_pair(__nv_bfloat16* p, float lo, float hi) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
@@ -238,31 +248,32 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
         st_pair(X + lane * Mm::S1 + m, v0, v1);
     }
     __syncwarp();
+    // A fragments: tiles (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
+    const int lr = lane & 7, lt = lane >> 3;
     unsigned ax[2][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++) {
-        const __nv_bfloat16* r0 = X + (mt * 16 + gid) * Mm::S1 + tig * 2;
-        const __nv_bfloat16* r1 = r0 + 8 * Mm::S1;
-        ax[mt][0] = ld_b32(r0);
-        ax[mt][1] = ld_b32(r1);
-        ax[mt][2] = ld_b32(r0 + 8);
-        ax[mt][3] = ld_b32(r1 + 8);
-    }
+    for (int mt = 0; mt < 2; mt++)
+        ldsm_x4(ax[mt][0], ax[mt][1], ax[mt][2], ax[mt][3], X + (mt * 16 + (lt & 1) * 8 + lr) * Mm::S1 + (lt >> 1) * 8);
     __syncwarp();  // every lane has its fragments: X may be overwritten by O
     // layer 1: h1 = silu(X W1^T + b1)
     unsigned h1[2][4][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-        const __nv_bfloat16* wb = w + Mm::W1 + (nt * 8 + gid) * Mm::S1 + tig * 2;
-        const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
-        const int col = nt * 8 + tig * 2;
-        const float c0 = b[col], c1 = b[col + 1];
+    for (int np = 0; np < 8; np += 2) {
+        // B fragments of n-tiles np and np + 1: tiles (n, k 0-7), (n, k 8-15) of each
+        unsigned bb[2][2];
+        ldsm_x4(bb[0][0], bb[0][1], bb[1][0], bb[1][1], w + Mm::W1 + ((np + (lt >> 1)) * 8 + lr) * Mm::S1 + (lt & 1) * 8);
 #pragma unroll
-        for (int mt = 0; mt < 2; mt++) {
-            float d[4] = {c0, c1, c0, c1};  // the accumulator starts at the (halved) bias
-            mma_bf16_16x8x16(d, ax[mt][0], ax[mt][1], ax[mt][2], ax[mt][3], b0, b1);
-            h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_half_bf16x2(d[0], d[1]);
-            h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_half_bf16x2(d[2], d[3]);
+        for (int u = 0; u < 2; u++) {
+            const int nt = np + u;
+            const int col = nt * 8 + tig * 2;
+            const float c0 = b[col], c1 = b[col + 1];
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) {
+                float d[4] = {c0, c1, c0, c1};  // the accumulator starts at the (halved) bias
+                mma_bf16_16x8x16(d, ax[mt][0], ax[mt][1], ax[mt][2], ax[mt][3], bb[u][0], bb[u][1]);
+                h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_half_bf16x2(d[0], d[1]);
+                h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_half_bf16x2(d[2], d[3]);
+            }
         }
     }
     // layer 2: h2 = silu(h1 W2^T + b2)
@@ -273,12 +284,16 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
         const float c0 = b[64 + col], c1 = b[64 + col + 1];
         float d[2][4] = {{c0, c1, c0, c1}, {c0, c1, c0, c1}};
 #pragma unroll
-        for (int kt = 0; kt < 4; kt++) {
-            const __nv_bfloat16* wb = w + Mm::W2 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
-            const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
+        for (int kp = 0; kp < 4; kp += 2) {
+            // B fragments of k-tiles kp and kp + 1: tiles (n, k 0-7), (n, k 8-15) of each
+            unsigned bb[2][2];
+            ldsm_x4(bb[0][0], bb[0][1], bb[1][0], bb[1][1], w + Mm::W2 + (nt * 8 + lr) * Mm::S2 + kp * 16 + lt * 8);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-                mma_bf16_16x8x16(d[mt], h1[mt][kt][0], h1[mt][kt][1], h1[mt][kt][2], h1[mt][kt][3], b0, b1);
+            for (int u = 0; u < 2; u++)
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++)
+                    mma_bf16_16x8x16(d[mt], h1[mt][kp + u][0], h1[mt][kp + u][1], h1[mt][kp + u][2], h1[mt][kp + u][3],
+                                     bb[u][0], bb[u][1]);
         }
 #pragma unroll
         for (int mt = 0; mt < 2; mt++) {
@@ -291,12 +306,15 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
     for (int nt = 0; nt < Mm::N3 / 8; nt++) {
         float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-        for (int kt = 0; kt < 4; kt++) {
-            const __nv_bfloat16* wb = w + Mm::W3 + (nt * 8 + gid) * Mm::S2 + kt * 16 + tig * 2;
-            const unsigned b0 = ld_b32(wb), b1 = ld_b32(wb + 8);
+        for (int kp = 0; kp < 4; kp += 2) {
+            unsigned bb[2][2];
+            ldsm_x4(bb[0][0], bb[0][1], bb[1][0], bb[1][1], w + Mm::W3 + (nt * 8 + lr) * Mm::S2 + kp * 16 + lt * 8);
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-                mma_bf16_16x8x16(d[mt], h2[mt][kt][0], h2[mt][kt][1], h2[mt][kt][2], h2[mt][kt][3], b0, b1);
+            for (int u = 0; u < 2; u++)
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++)
+                    mma_bf16_16x8x16(d[mt], h2[mt][kp + u][0], h2[mt][kp + u][1], h2[mt][kp + u][2], h2[mt][kp + u][3],
+                                     bb[u][0], bb[u][1]);
         }
         const int col = nt * 8 + tig * 2;
 #pragma unroll
