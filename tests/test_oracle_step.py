@@ -230,3 +230,43 @@ def test_sound_speed_from_acoustic_pulse(K):
     cs = (xp - x0) / nsteps
     gamma = (D + K + 2) / (D + K)
     assert cs == pytest.approx(np.sqrt(gamma * RT), rel=0.02)
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_refined_landing_moves_centre_of_mass_by_momentum(D):
+    """Streaming moves every population to x + c (Eq. IIE3); a refined child landing between
+    cells is shared so that its mass-weighted landing position is exactly x + c (cloud in
+    cell, 3/4 and 1/4 per axis at level 1).  So over one step the centre of mass moves by
+    the total momentum: sum(x rho)' = sum(x rho) + sum(rho u).  A cold blob (RT = 0.3 < 4/9,
+    one refinement level) moving inside a resting uniform background checks it; the
+    background is symmetric, so what crosses the periodic edges cancels."""
+    n = 48 if D == 1 else 20
+    K = 4.0 if D == 1 else 3.0
+    g = O.grid(D, n, n if D == 2 else 1, periodic=(True, True))
+    p = O.params(D, K, nu_s=5e-3, Pr=0.71)
+    assert O.refine_levels(p, 0.3) == 1
+    shp = (n, n) if D == 2 else (n,)
+    rho = np.ones(shp)
+    u = np.zeros((D,) + shp)
+    RT = np.full(shp, 0.3)
+    rng = np.random.default_rng(29)
+    blob = (slice(n // 2 - 3, n // 2 + 3),) * D
+    rho[blob] = 1.0 + 0.4 * rng.random(rho[blob].shape)
+    for a in range(D):
+        u[(a,) + blob] = 0.8 * rng.random(rho[blob].shape) - 0.2
+    RT[blob] = 0.25 + 0.1 * rng.random(rho[blob].shape)
+    M = O.state_from_primitives(g, p, rho, u, RT)
+    c = (n - 1) / 2.0
+    if D == 1:
+        pos = [np.arange(n) - c]
+    else:
+        iy, ix = np.divmod(np.arange(n * n), n)
+        pos = [ix - c, iy - c]
+    st = O.Stats()
+    for _ in range(2):
+        M1 = O.step(g, p, M, st)
+        for a in range(D):
+            moved = (pos[a] * M1[0]).sum() - (pos[a] * M[0]).sum()
+            assert abs(moved - M[1 + a].sum()) < 1e-11, (a, moved, M[1 + a].sum())
+        M = M1
+    assert st.fallback_eq == 0 and st.fallback_mx == 0
