@@ -270,3 +270,35 @@ def test_refined_landing_moves_centre_of_mass_by_momentum(D):
             assert abs(moved - M[1 + a].sum()) < 1e-11, (a, moved, M[1 + a].sum())
         M = M1
     assert st.fallback_eq == 0 and st.fallback_mx == 0
+
+
+def test_failed_solve_falls_back_to_equilibrium_constraints():
+    """A cell whose post-collision constraints no positive populations can meet (a negative
+    normal stress deeper than the pressure, kept after a weak collision: large viscosity, no
+    limiter) is solved with the equilibrium constraints of both populations instead.  Its
+    emitted moments are then those of a cell holding the equilibrium state of the same
+    rho, u and RT, so the whole step matches that state's step."""
+    D, K, n = 2, 3.0, 8
+    g = O.grid(D, n, n, periodic=(True, True))
+    p = O.params(D, K, nu_s=5.0, Pr=0.71, limiter=0)
+    rho = np.ones((n, n))
+    u = np.zeros((D, n, n))
+    u[0], u[1] = 0.2, -0.1
+    RT = np.full((n, n), 0.6)
+    M_eq = O.state_from_primitives(g, p, rho, u, RT)
+    M_bad = M_eq.copy()
+    cell = 3 * n + 4
+    d, e = 2.0, 0.6  # multiples of rho RT; the energy trM2 + G0 is unchanged
+    M_bad[3, cell] -= d * 0.6
+    M_bad[5, cell] += (d - e) * 0.6
+    M_bad[8, cell] += e * 0.6
+    co = O.collide(p, M_bad[:, cell])
+    assert co["cf"][3] < 0.0  # the xx constraint asks for a negative variance
+    assert np.abs(co["cg"][1:3]).max() > 0.01  # and the phonon heat-flux constraints are not zero
+    st_bad, st_eq = O.Stats(), O.Stats()
+    out_bad = O.step(g, p, M_bad, st_bad)
+    out_eq = O.step(g, p, M_eq, st_eq)
+    assert st_bad.fallback_eq == 1 and st_bad.fallback_mx == 0
+    assert st_eq.fallback_eq == 0
+    scale = np.abs(out_eq).max(axis=1, keepdims=True)
+    assert (np.abs(out_bad - out_eq) / scale).max() < 1e-13
