@@ -83,6 +83,24 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
+def rank_reduce(x: float, op: str, world: int, device) -> float:
+    """x combined over the ranks of the job: "max" (the slowest rank's time) or "sum" (the
+    work of all ranks); x itself when the job has one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_mlups(units_all_ranks: float, steps: int, ms_slowest: float) -> float:
+    """Cell updates of all ranks per second of the slowest rank, in millions."""
+    return units_all_ranks * steps / (ms_slowest / 1e3) / 1e6
+
+
 def make_workload(args, rank):
     from paper_2508_06911_gb300 import workloads as W
 
@@ -351,21 +369,18 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         clocks = clock_sampler_stop(clk, local) if sample_clocks else None
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = rank_reduce(e0.elapsed_time(e1), "max", world, "cuda")
         return ms, s.stats(), s.synchronize(), clocks
 
     s = make(args.precision, args.warmstart)
     state_bytes = s.n_mom * s.n_cells * 8
     ms, st, status, clocks = timed(s, True)
-    value = interior * args.steps * world / (ms / 1e3) / 1e6
+    units = rank_reduce(interior, "sum", world, "cuda")  # each rank has its own seeded batch
+    value = whole_job_mlups(units, args.steps, ms)
 
     def summary(ms_, st_):
         h_ = list(st_.newton_hist)
-        return {"value": interior * args.steps * world / (ms_ / 1e3) / 1e6, "ms_per_step": ms_ / args.steps,
+        return {"value": whole_job_mlups(units, args.steps, ms_), "ms_per_step": ms_ / args.steps,
                 "points_fp32": st_.points_32, "points_fp64_newton": st_.points_f + st_.points_g,
                 "newton_mean_updates": sum(i * x for i, x in enumerate(h_)) / max(sum(h_), 1),
                 "start_retry": st_.mlp_retry}
@@ -461,12 +476,8 @@ def run_ours(args):
             L.lelbm_set_moments(s.h, host)
             advance(s, 1)
             L.lelbm_get_moments(s.h, host)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": interior * ke * world / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": state_bytes,
+        dt = rank_reduce(time.perf_counter() - t0, "max", world, "cuda")
+        e2e = {"value": whole_job_mlups(units, ke, dt * 1e3), "unit": "MLUPS", "h2d_bytes_per_step": state_bytes,
                "d2h_bytes_per_step": state_bytes, "steps": ke}
 
     cpu = None
