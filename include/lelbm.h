@@ -64,10 +64,17 @@ extern "C" {
 
 /* arithmetic of the step */
 #define LELBM_FP64 0  /* every operation in FP64                                     */
-#define LELBM_MIXED 1 /* EPR Newton passes in FP32, then one FP64 Newton pass; the
-                         streaming pass computes the populations in FP64 and checks
-                         their FP64 residual against tol (re-solving in FP64 on a
-                         miss); state, collision and accumulation in FP64          */
+#define LELBM_MIXED 1 /* EPR Newton in FP32 to the FP32 noise floor, then per
+                         population one Newton correction whose residual is summed
+                         in double-float (FP32 pairs, about 48 bits) with an FP32
+                         Jacobian, and a double-float streaming pass that re-checks
+                         the residual of exactly the populations it deposits
+                         against tol (a miss is taken back and corrected again,
+                         then left to the FP64 EPR).  Exponents are exact int64
+                         fixed-point polynomials, 2^w a table-driven double-float
+                         exponential; deposits are FP64 atomic additions of both
+                         words.  State, collision and accumulation in FP64.
+                         Matches LELBM_FP64 to about 1e-13 per step.             */
 #define LELBM_FP32 2  /* EPR Newton (passes and solves) and the streaming pass in
                          FP32, to an FP32 residual of 3e-4 (thermal units) plus one
                          polishing update; moment fractions widened to FP64 (exact
@@ -141,6 +148,7 @@ typedef struct {
     long long wall_hits;          /* populations specularly reflected at a solid
                                      face while streaming (Sec. III.B)              */
     long long mlp_cells;          /* cells given the learned warm start             */
+    long long points_df;          /* mixed: stencil points of double-float passes   */
 } lelbm_stats;
 
 /* Sizes of the structures this library was built with, so a binding can check

@@ -26,7 +26,7 @@ UNITS = [
     ("lelbm_batch.cu", "lelbm_batch_mixed.o", ["-DLBM_PREC=1"]),
     ("lelbm_batch.cu", "lelbm_batch_fp32.o", ["-DLBM_PREC=2"]),
 ]
-HEADERS = ["lelbm_internal.h", "lelbm_device.cuh", "lelbm_mlp.cuh", "lelbm_step.cuh",
+HEADERS = ["lelbm_internal.h", "lelbm_device.cuh", "lelbm_df.cuh", "lelbm_land.cuh", "lelbm_mlp.cuh", "lelbm_step.cuh",
            os.path.join("..", "..", "include", "lelbm.h")]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -585,6 +585,7 @@ static int read_stats(lelbm* h, lelbm_stats* s) {
         s->mlp_retry = (long long)d.mlp_retry;
         s->wall_hits = (long long)d.wall_hits;
         s->mlp_cells = (long long)d.mlp_cells;
+        s->points_df = (long long)d.points_df;
     }
     return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
 }

@@ -1319,7 +1319,8 @@ __device__ __forceinline__ void row_coeffs32(const float* lf, const float* lg, f
 // One FP32 pass over the velocity set (row table when valid, else Stencil)
 // accumulating the population moments of f (doF) and g (doG) for the FP32
 // multipliers lf, lg.  Returns the point count.
-template <int D>
+// TAB: the caller guarantees a valid row table (no Stencil fallback compiled in).
+template <int D, bool TAB = false>
 __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& c, const Stencil<D>& st,
                                                             const RowTable<D>& tab, const float* lf, const float* lg,
                                                             bool doF, bool doG, float* MF, float* MG) {
@@ -1413,13 +1414,13 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
                 for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] = fmaf(SG[a], yp[b], MG[tix(a, b, MS::PG)]);
         }
     };
-    if (tab.ok) {
+    if (TAB || tab.ok) {
         constexpr float wch = D == 1 ? 0.5f : 0.25f;
         auto child = [&](int p, int cy, int sx, int sy) {
             add_point(tab.tx(p, 0.25f * (float)sx), D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f, wch);
         };
         tab.visit(row, child);
-    } else {
+    } else if constexpr (!TAB) {
         auto leaf = [&](const double* cp, double dC) {
             add_point((float)((cp[0] - c.u[0]) * c.inv_sig), D == 2 ? (float)((cp[D - 1] - c.u[D - 1]) * c.inv_sig) : 0.f,
                       (float)dC);
@@ -1492,7 +1493,7 @@ __device__ __forceinline__ bool solve_fg_mixed(const CellState<D>& c, const Sten
 // the FP32 noise floor of the passes: a tighter stop costs passes and buys nothing.
 // Returns false on a breakdown or at the iteration cap (the caller then runs the FP64
 // EPR).  sf, sg count the FP32 updates; np32 the points of the FP32 passes.
-template <int D>
+template <int D, bool TAB = false>
 __device__ __forceinline__ bool solve_fg32(const CellState<D>& c, const Stencil<D>& st, const RowTable<D>& tab,
                                            const float* cf32, const float* cg32, bool has_g, float* lf32,
                                            float* lg32, int& sf, int& sg, unsigned int& np32) {
@@ -1504,7 +1505,7 @@ __device__ __forceinline__ bool solve_fg32(const CellState<D>& c, const Stencil<
     sg = 0;
     for (int it = 0; fa || ga; it++) {
         float MF32[MS::NF], MG32[MS::NG];
-        np32 += moment_pass32<D>(c, st, tab, lf32, lg32, fa, ga, MF32, MG32);
+        np32 += moment_pass32<D, TAB>(c, st, tab, lf32, lg32, fa, ga, MF32, MG32);
         if (ga) {
             const int r = newton_step32<D, false>(MG32, cg32, lg32, tol32, max32, it);
             if (r < 0) return false;

@@ -95,6 +95,7 @@ struct DevStats {
     unsigned long long mlp_retry;      // cells whose learned start failed and were re-solved from Eq. IID13
     unsigned long long wall_hits;      // streamed populations reflected at a solid face (Sec. III.B)
     unsigned long long mlp_cells;      // cells given the learned warm start
+    unsigned long long points_df;      // stencil points of double-float passes (mixed path)
 };
 
 void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, long long ncell,

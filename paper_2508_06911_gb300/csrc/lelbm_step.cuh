@@ -23,210 +23,12 @@
 #include <cstdint>
 
 #include "lelbm_device.cuh"
+#include "lelbm_df.cuh"
 #include "lelbm_internal.h"
+#include "lelbm_land.cuh"
 #include "lelbm_mlp.cuh"
 
 namespace lbm {
-
-// ---------------------------------------------------------------------------
-// The fused single-cell kernel.
-// ---------------------------------------------------------------------------
-struct LocalStats {
-    unsigned long long q_max;
-    double disp_max2;
-    unsigned long long points;
-    long long walls;  // populations reflected at solid faces (an undone deposit counts -1)
-};
-
-// Landing cell of an integer displacement (dx, dy) from the emitting cell, or -1
-// when the population leaves the interior of its instance (Sec. III: discarded).
-template <int D>
-__device__ __forceinline__ long long land(const Geometry& g, long long cell, long long lo, int n, int ix, int iy,
-                                          int dx, int dy) {
-    if constexpr (D == 1) {
-        int r = (int)(cell - lo) + dx;  // instances are shorter than 2^31 cells
-        if (g.periodic[0]) {
-            r %= n;
-            if (r < 0) r += n;
-            return lo + r;
-        }
-        return (unsigned int)r < (unsigned int)n ? lo + r : -1;
-    } else {
-        int tx = ix + dx, ty = iy + dy;
-        if (g.periodic[0]) {
-            tx %= g.nx;
-            if (tx < 0) tx += g.nx;
-        } else if (tx < g.pad || tx >= g.pad + g.nx) {
-            return -1;
-        }
-        if (g.periodic[1]) {
-            ty %= g.ny;
-            if (ty < 0) ty += g.ny;
-        } else if (ty < g.pad || ty >= g.pad + g.ny) {
-            return -1;
-        }
-        return (long long)ty * g.NX + tx;
-    }
-}
-
-// Is interior cell tgt (a result of land) fluid?  Only 2D grids with solid cells have
-// interior cells that are not, so the others need no load of the cell type.
-template <int D>
-__device__ __forceinline__ bool lands_on_fluid(const Geometry& g, const uint8_t* type, long long tgt) {
-    if constexpr (D == 1) return true;
-    return g.wall_dist == nullptr || type[tgt] == CELL_FLUID;
-}
-
-// ---------------------------------------------------------------------------
-// Solid boundary, Sec. III.B (stationary adiabatic slip wall, 2D).
-// ---------------------------------------------------------------------------
-// Is padded cell (i, j) solid?  Periodic axes wrap; cells off the array are not.
-__device__ __forceinline__ bool solid_at(const Geometry& g, const uint8_t* type, int i, int j) {
-    if (g.periodic[0]) {
-        i %= g.NX;
-        if (i < 0) i += g.NX;
-    }
-    if (g.periodic[1]) {
-        j %= g.NY;
-        if (j < 0) j += g.NY;
-    }
-    if (i < 0 || i >= g.NX || j < 0 || j >= g.NY) return false;
-    return type[(long long)j * g.NX + i] == CELL_SOLID;
-}
-
-// End of the path x -> x + c past solid cells: the path is walked face by face and at
-// a face of a solid cell the velocity component normal to it is reversed (specular
-// reflection), until the displacement |c| is used up.  Positions are exact integers in
-// units of 1/64 cell: along each axis the faces lie at unfolded distances 32 + 64 k,
-// and which of two faces comes first is decided by cross-multiplication, so ties (a
-// path through a cell corner) are exact.  Through a corner whose diagonal cell is
-// solid, only the normal of a flat wall (exactly one side cell solid) is reversed,
-// otherwise both.  The walk ends after at most |c_x| + |c_y| + 2 face events.
-struct WallLanding {
-    int i, j;        // final (fluid) cell, unwrapped padded coordinates
-    double off[2];   // landing point relative to its centre, each in (-1/2, 1/2]
-    double cs[2];    // reflected velocity c*
-    bool touched;    // reflected at least once
-};
-
-__device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8_t* type, int ix, int iy,
-                                                  const double* c) {
-    constexpr long long S = 64;
-    const long long qx = llround((double)S * c[0]), qy = llround((double)S * c[1]);
-    int sx = (qx > 0) - (qx < 0), sy = (qy > 0) - (qy < 0);
-    const long long ax = qx < 0 ? -qx : qx, ay = qy < 0 ? -qy : qy;
-    int i = ix, j = iy;
-    bool touched = false;
-    long long kx = 0, ky = 0;
-    while (true) {
-        const long long Xn = S / 2 + S * kx, Yn = S / 2 + S * ky;
-        const bool hx = ax > 0 && Xn < ax, hy = ay > 0 && Yn < ay;
-        if (!hx && !hy) break;
-        bool stx = hx, sty = hy;
-        if (hx && hy) {
-            const long long l = Xn * ay, r = Yn * ax;
-            stx = l <= r;
-            sty = r <= l;
-        }
-        if (stx && sty) {
-            if (!solid_at(g, type, i + sx, j + sy)) {
-                i += sx;
-                j += sy;
-            } else {
-                const bool sa = solid_at(g, type, i + sx, j), sb = solid_at(g, type, i, j + sy);
-                touched = true;
-                if (sa && !sb) {
-                    sx = -sx;
-                    j += sy;
-                } else if (sb && !sa) {
-                    sy = -sy;
-                    i += sx;
-                } else {
-                    sx = -sx;
-                    sy = -sy;
-                }
-            }
-        } else {
-            const int ti = i + (stx ? sx : 0), tj = j + (sty ? sy : 0);
-            if (solid_at(g, type, ti, tj)) {
-                if (stx) sx = -sx;
-                if (sty) sy = -sy;
-                touched = true;
-            } else {
-                i = ti;
-                j = tj;
-            }
-        }
-        kx += stx;
-        ky += sty;
-    }
-    WallLanding L;
-    L.i = i;
-    L.j = j;
-    L.off[0] = (double)sx * (double)(ax - S * kx) * (1.0 / S);
-    L.off[1] = (double)sy * (double)(ay - S * ky) * (1.0 / S);
-    L.cs[0] = (double)sx * fabs(c[0]);
-    L.cs[1] = (double)sy * fabs(c[1]);
-    L.touched = touched;
-    return L;
-}
-
-// Adds the raw moments T_N(cp) mf and T_N(cp) mg (2D) to cell tgt of Mout.
-__device__ __forceinline__ void add_moments_2d(double* Mout, long long ncell, long long tgt, const double* cp,
-                                               double mf, double mg) {
-    const double csq = cp[0] * cp[0] + cp[1] * cp[1];
-    const double dM[11] = {mf,           cp[0] * mf,          cp[1] * mf,          cp[0] * cp[0] * mf,
-                           cp[0] * cp[1] * mf, cp[1] * cp[1] * mf, csq * cp[0] * mf, csq * cp[1] * mf,
-                           mg,           cp[0] * mg,          cp[1] * mg};
-#pragma unroll
-    for (int mm = 0; mm < 11; mm++) atomicAdd(Mout + mm * ncell + tgt, dM[mm]);
-}
-
-// Streams one population of cell (ix, iy) with velocity cp past the solid cells (2D):
-// its path is traced, the landing point is shared between cells by cloud-in-cell
-// weights, and a share that would fall on a solid cell is mirrored back across the wall
-// with the normal component of its velocity reversed (into the side cell behind a flat
-// wall, into the final cell behind a corner of solid cells).  Returns whether the path
-// was reflected.  Kept out of line: only cells near a solid cell take this path.
-static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8_t* type, double* Mout, int ix, int iy,
-                                           const double* cp, double mf, double mg) {
-    const WallLanding L = trace_path(g, type, ix, iy, cp);
-    const double pos[2] = {(double)L.i + L.off[0], (double)L.j + L.off[1]};
-    int base[2];
-    double w1[2];
-#pragma unroll
-    for (int a = 0; a < 2; a++) {
-        const double fl = floor(pos[a]);
-        base[a] = (int)fl;
-        w1[a] = pos[a] - fl;
-    }
-    const int ncx = w1[0] > 0.0 ? 2 : 1, ncy = w1[1] > 0.0 ? 2 : 1;
-    for (int sy = 0; sy < ncy; sy++)
-        for (int sx = 0; sx < ncx; sx++) {
-            const double w = (sx ? w1[0] : 1.0 - w1[0]) * (sy ? w1[1] : 1.0 - w1[1]);
-            int tx = base[0] + sx, ty = base[1] + sy;
-            double cw[2] = {L.cs[0], L.cs[1]};
-            if (solid_at(g, type, tx, ty)) {
-                bool ox = tx != L.i, oy = ty != L.j;
-                if (ox && oy) {
-                    const bool sa = solid_at(g, type, tx, L.j), sb = solid_at(g, type, L.i, ty);
-                    if (!sa && sb) ox = false;
-                    else if (sa && !sb) oy = false;
-                }
-                if (ox) {
-                    cw[0] = -cw[0];
-                    tx = L.i;
-                }
-                if (oy) {
-                    cw[1] = -cw[1];
-                    ty = L.j;
-                }
-            }
-            const long long tgt = land<2>(g, 0, 0, 0, ix, iy, tx - ix, ty - iy);
-            if (tgt >= 0 && type[tgt] == CELL_FLUID) add_moments_2d(Mout, g.ncell, tgt, cw, w * mf, w * mg);
-        }
-    return L.touched;
-}
 
 // ---------------------------------------------------------------------------
 // FP32 streaming (the FP32 path).  Populations and their moment fractions are
@@ -237,23 +39,6 @@ static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8
 // Newton leaves a residual of about 1e-6) is added at the emitting cell, so the
 // totals are conserved to FP64 rounding.
 // ---------------------------------------------------------------------------
-// Subnormals become zero (before both the deposit and the accounting).
-__device__ __forceinline__ float flush_sub(float v) { return (__float_as_uint(v) & 0x7f800000u) ? v : 0.f; }
-
-// FP32 -> FP64 in integer operations only: the exponent is rebiased from 127 to 1023
-// by one addition and the mantissa shifted into place (no conversion instruction, which
-// would take the FP64 pipe).  Normal numbers widen exactly; zeros and subnormals give
-// zero, so a deposit differs from its accounted fraction by less than 2^-126.
-// Infinities and NaNs, which a converged solve does not produce, come out finite; the
-// emitting cell's accounting of the same fractions still carries them into the state
-// as non-finite mass, momentum or energy.
-__device__ __forceinline__ double widen(float v) {
-    const unsigned int b = __float_as_uint(v);
-    const bool tiny = (b & 0x7f800000u) == 0u;
-    const unsigned int hi = (((b >> 3) & 0x0fffffffu) + 0x38000000u) | (b & 0x80000000u);
-    return __hiloint2double(tiny ? 0 : (int)hi, tiny ? 0 : (int)(b << 29));
-}
-
 // Compensated FP32 sum: hi + lo carries the exact sum to about 1e-14 relative
 // (Knuth's two-sum on every addition).  The explicitly rounded operations keep the
 // compiler from fusing a product that produced v into these additions: the sum must be
@@ -843,7 +628,7 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
 // Per-block counters in shared memory, flushed to DevStats once per block.
 struct BlockCounters {
     unsigned long long hist[64];
-    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls, mlpc;
+    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls, mlpc, pdf;
 };
 
 // Per-thread tallies.
@@ -853,13 +638,14 @@ struct ThreadCounters {
     unsigned int cells, pf, pg, p32, redo, retry;
     LocalStats ls;
     unsigned int mlp_cells;
+    unsigned int pdf;  // stencil points of double-float passes (mixed path)
 };
 
 __device__ __forceinline__ void counters_init(BlockCounters& bc) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
     if (threadIdx.x == 0)
         bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = bc.retry =
-            bc.walls = bc.mlpc = 0;
+            bc.walls = bc.mlpc = bc.pdf = 0;
 }
 
 // Adds the thread tallies to the block counters, then (after a barrier) the block
@@ -876,9 +662,10 @@ __device__ __forceinline__ void counters_to_block(BlockCounters& bc, ThreadCount
     atomicAdd(&bc.pm, tc.ls.points);
     if (tc.ls.walls) atomicAdd(&bc.walls, (ull)tc.ls.walls);
     if (tc.mlp_cells) atomicAdd(&bc.mlpc, (ull)tc.mlp_cells);
+    if (tc.pdf) atomicAdd(&bc.pdf, (ull)tc.pdf);
     atomicMax(&bc.q, tc.ls.q_max);
     atomicMax(&bc.dmax, (ull)__double_as_longlong(sqrt(tc.ls.disp_max2)));
-    tc = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    tc = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0};
 }
 
 __device__ __forceinline__ void counters_flush(BlockCounters& bc, ThreadCounters& tc, DevStats* stats) {
@@ -896,6 +683,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, ThreadCounters
         if (bc.retry) atomicAdd(&stats->mlp_retry, bc.retry);
         if (bc.walls) atomicAdd(&stats->wall_hits, bc.walls);
         if (bc.mlpc) atomicAdd(&stats->mlp_cells, bc.mlpc);
+        if (bc.pdf) atomicAdd(&stats->points_df, bc.pdf);
         if (bc.feq) atomicAdd(&stats->fallback_eq, bc.feq);
         if (bc.fmx) atomicAdd(&stats->fallback_mx, bc.fmx);
         atomicMax(&stats->q_max, bc.q);
@@ -1025,6 +813,157 @@ static __device__ __noinline__ TailCounts fp64_tail_cold(const Model& m, const G
     return t;
 }
 
+// ---------------------------------------------------------------------------
+// The mixed path's finish (LELBM_MIXED): FP32 Newton to the FP32 noise floor, then per
+// population one double-float correction (residual in double-float, Jacobian in FP32 at
+// the same multipliers) and a double-float streaming pass that re-checks the residual of
+// exactly the populations it deposits against the FP64 path's tolerance (Sec. II.D).  A
+// miss takes the deposit back and corrects again; a second miss leaves the cell to the
+// FP64 EPR.
+// ---------------------------------------------------------------------------
+// Corrects and streams one population.  Returns the number of double-float Newton updates
+// (>= 1) once its deposit passed the check, -1 when nothing of it is deposited and the
+// FP64 EPR must solve the cell.
+template <int D, bool FLUON>
+__device__ __forceinline__ int df_population(const Model& m, const CellState<D>& c, const RowTable<D>& tab,
+                                             double* lam, const double* con, const float2* etab, double xm,
+                                             DFStream& ds, ThreadCounters& tc) {
+    using Q = DFPop<D, FLUON>;
+    double r[Q::N];
+    double rmax;
+#pragma unroll 1
+    for (int it = 0; it < 2; it++) {
+        {
+            float MJ[Q::NJ];
+            if (!df_pass<D, FLUON, DF_CORR>(c.u[0], c.u[D - 1], c.inv_sig, tab, lam, con, etab, xm, r, rmax, MJ, ds, tc.ls, tc.pdf, ds.beta)) return -1;
+            // far from the FP32 solution's neighbourhood (or non-finite): the FP64 EPR decides
+            if (!(rmax < 1e-3)) return -1;
+            if (rmax > m.tol && !df_update<D, FLUON>(MJ, r, lam)) return -1;
+        }
+        if (!df_pass<D, FLUON, DF_STREAM>(c.u[0], c.u[D - 1], c.inv_sig, tab, lam, con, etab, xm, r, rmax, nullptr, ds, tc.ls, tc.pdf, ds.beta)) return -1;
+        if (rmax <= m.tol) return it + 1;
+        // the deposited populations miss the tolerance: take them back
+        ds.mh = -ds.mh;
+        ds.ml = -ds.ml;
+        df_pass<D, FLUON, DF_STREAM>(c.u[0], c.u[D - 1], c.inv_sig, tab, lam, con, etab, xm, r, rmax, nullptr, ds, tc.ls, tc.pdf, ds.beta);
+        ds.mh = -ds.mh;
+        ds.ml = -ds.ml;
+        tc.redo++;
+    }
+    return -1;
+}
+
+// Returns true when the cell is solved and streamed; false leaves the cell, with nothing
+// of it deposited, to the FP64 EPR.  Phonons go first: their system is the smaller one, so
+// less of it stays live through the fluon passes.
+template <int D>
+__device__ __forceinline__ bool df_finish(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                          long long cell, BlockCounters& bc, ThreadCounters& tc, const double* conF,
+                                          const double* conG, const CellState<D>& c, const Stencil<D>& st,
+                                          const RowTable<D>& tab, float* lf32, float* lg32, bool learned,
+                                          const float2* etab, long long* bslot) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    const bool has_g = m.K > 0.0;
+    {
+        float cf32[NF], cg32[NG];
+#pragma unroll
+        for (int j = 0; j < NF; j++) cf32[j] = (float)conF[j];
+#pragma unroll
+        for (int j = 0; j < NG; j++) cg32[j] = (float)conG[j];
+        int sf, sg;
+        bool ok32 = solve_fg32<D>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, tc.p32);
+        if (!ok32 && learned) {
+            tc.retry++;
+            maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+            ok32 = solve_fg32<D>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, tc.p32);
+        }
+        if (!ok32) return false;
+    }
+    DFStream ds;
+    ds.g = &g;
+    ds.type = type;
+    ds.Mout = Mout;
+    ds.cell = cell;
+    ds.lo = 0;
+    ds.n = 0;
+    ds.ix = ds.iy = 0;
+    ds.near_wall = false;
+    ds.beta = bslot;
+    if constexpr (D == 1) {
+        const int b = g.inst_of_cell[cell];
+        ds.lo = g.inst_lo[b];
+        ds.n = g.inst_n[b];
+    } else {
+        ds.iy = (int)(cell / g.NX);
+        ds.ix = (int)(cell - (long long)ds.iy * g.NX);
+        // Sec. III.B: trace paths past solid faces where a solid cell lies within reach
+        if (g.wall_dist)
+            ds.near_wall = (double)g.wall_dist[cell] <= fmax(fabs(c.u[0]), fabs(c.u[1])) + (double)st.R + 1.5;
+    }
+    const double xm = (double)st.R + 2.0;  // |X|, |Y| of every stencil offset from floor(u)
+    double lg[NG];
+    int ug = 0;
+    if (has_g) {
+#pragma unroll
+        for (int j = 0; j < NG; j++) lg[j] = (double)lg32[j];
+        df_split(c.rho * m.K * c.RT, ds.mh, ds.ml);
+        ug = df_population<D, false>(m, c, tab, lg, conG, etab, xm, ds, tc);
+        if (ug < 0) return false;
+    }
+    double lf[NF];
+#pragma unroll
+    for (int j = 0; j < NF; j++) lf[j] = (double)lf32[j];
+    df_split(c.rho, ds.mh, ds.ml);
+    const int uf = df_population<D, true>(m, c, tab, lf, conF, etab, xm, ds, tc);
+    if (uf < 0) {
+        if (has_g) {  // take the phonon deposit back too: the FP64 EPR streams both
+            double r[NG], rmax;
+            df_split(-(c.rho * m.K * c.RT), ds.mh, ds.ml);
+            df_pass<D, false, DF_STREAM>(c.u[0], c.u[D - 1], c.inv_sig, tab, lg, conG, etab, xm, r, rmax, nullptr, ds, tc.ls, tc.pdf, ds.beta);
+        }
+        return false;
+    }
+    atomicAdd(&bc.hist[uf], 1ull);
+    if (has_g) atomicAdd(&bc.hist[ug], 1ull);
+    if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
+        const float l0 = (float)maxwell_l0<D>(c.RT);
+#pragma unroll
+        for (int j = 0; j < NF; j++) m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
+#pragma unroll
+        for (int j = 0; j < NG; j++)
+            m.lam_store[(long long)(NF + j) * g.ncell + cell] = has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
+    }
+    return true;
+}
+
+// The FP64 EPR of one cell from Eq. (IID13), with its fallbacks and its FP64 streaming,
+// out of line, for the mixed path's rare cells that the double-float finish leaves.  The
+// collision and the stencil are recomputed from the cell's moments in Min (FP64, as in
+// the prepare step), so no per-cell value of the hot path stays live for this call;
+// conF, conG are the cell's scratch slots.
+template <int D>
+static __device__ __noinline__ TailCounts fp64_cell_cold(const Model& m, const Geometry& g, const uint8_t* type,
+                                                         const double* __restrict__ Min, double* Mout,
+                                                         DevStats* stats, long long cell, BlockCounters* bc,
+                                                         double* conF, double* conG) {
+    TailCounts t{0, 0, 0, {0, 0.0, 0, 0}};
+    double M[Dim<D>::NM];
+#pragma unroll
+    for (int i = 0; i < Dim<D>::NM; i++) M[i] = Min[i * g.ncell + cell];
+    CellState<D> c;
+    Stencil<D> st;
+    collide<D>(M, m, c);
+    st.init(c, m);
+#pragma unroll
+    for (int j = 0; j < Dim<D>::NF; j++) conF[j] = c.cf[j];
+#pragma unroll
+    for (int j = 0; j < Dim<D>::NG; j++) conG[j] = c.cg[j];
+    double lf[Dim<D>::NF], lg[Dim<D>::NG];
+    maxwell_start_fg<D, Dim<D>::NF, Dim<D>::NG>(c.RT, lf, lg);
+    fp64_tail<D>(m, g, type, Mout, stats, cell, *bc, t.pf, t.pg, t.retry, t.ls, conF, conG, c, st, lf, lg, false);
+    return t;
+}
+
 // The single-cell operation of Fig. 5 in two halves around the (warp-wide) warm-start
 // network: prepare_cell loads the moments, runs the collision module and sets up the
 // stencil; finish_cell runs EPR (with the fallbacks) and moment streaming into Mout.
@@ -1054,10 +993,11 @@ __device__ __forceinline__ bool prepare_cell(const Model& m, const Geometry& g, 
 
 // dl: the learned correction of the Maxwellian start (fluons then phonons), or null.
 template <int D, int PREC>
-__device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+__device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, const uint8_t* type,
+                                            const double* __restrict__ Min, double* Mout,
                                             DevStats* stats, long long cell, BlockCounters& bc, ThreadCounters& tc,
                                             Con<PREC>* conF, Con<PREC>* conG, const CellState<D>& c, const Stencil<D>& st,
-                                            const float* dl, char2* rowbuf) {
+                                            const float* dl, char2* rowbuf, const float2* etab, long long* bslot) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     tc.cells++;
     const bool has_g = m.K > 0.0;
@@ -1069,8 +1009,10 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 #pragma unroll
         for (int k = 0; k < MlpDims<D>::NOUT; k++) dl_ok = dl_ok && isfinite(dl[k]);
     }
-    if constexpr (PREC == PREC_FP32) {
-        maxwell_start32<D, NF, NG>(c.RT32, lf32, lg32);
+    // the FP32 Newton's start (FP32 and mixed paths); RT in FP32 (the FP32 path has its own)
+    const float rt32 = PREC == PREC_FP32 ? c.RT32 : (float)c.RT;
+    if constexpr (PREC != PREC_FP64) {
+        maxwell_start32<D, NF, NG>(rt32, lf32, lg32);
         if (dl_ok) {
 #pragma unroll
             for (int j = 0; j < NF; j++) lf32[j] += dl[j];
@@ -1096,7 +1038,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
                 }
             }
             learned = fin;
-            if (!fin) maxwell_start32<D, NF, NG>(c.RT32, lf32, lg32);
+            if (!fin) maxwell_start32<D, NF, NG>(rt32, lf32, lg32);
         }
     } else {
         maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
@@ -1175,33 +1117,195 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
         tc.ls.disp_max2 = fmax(tc.ls.disp_max2, t.ls.disp_max2);
     } else {
         if constexpr (PREC == PREC_MIXED) {
-            if (solve_fg_mixed<D>(c, st, tab, conF, conG, has_g, lf, lg, m, sf, sg, tc.pf, tc.pg, tc.p32)) {
-                // stream and judge in one FP64 pass; on a miss, take the deposit back and
-                // finish the solve in FP64 from the current multipliers
-                if (scatter_cell<D, true>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, 1.0, conF, conG)) {
-                    atomicAdd(&bc.hist[1], has_g ? 2ull : 1ull);  // one FP64 update per population
-                    if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
-                        const float l0 = (float)maxwell_l0<D>(c.RT);
-#pragma unroll
-                        for (int j = 0; j < NF; j++)
-                            m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
-#pragma unroll
-                        for (int j = 0; j < NG; j++)
-                            m.lam_store[(long long)(NF + j) * g.ncell + cell] =
-                                has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
-                    }
-                    return;
-                }
-                scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, tc.ls, -1.0);
-                tc.redo++;
-            } else {
-                if (learned) tc.retry++;
-                maxwell_start_fg<D, NF, NG>(c.RT, lf, lg);
-                learned = false;
-            }
+            // FP32 Newton, double-float correction and streaming judged at the FP64
+            // tolerance; the FP64 EPR (out of line) takes the cells it leaves
+            if (tab.ok && df_finish<D>(m, g, type, Mout, cell, bc, tc, conF, conG, c, st, tab, lf32, lg32, learned,
+                                       etab, bslot))
+                return;
+            tc.redo++;
+            const TailCounts t = fp64_cell_cold<D>(m, g, type, Min, Mout, stats, cell, &bc, conF, conG);
+            tc.pf += t.pf;
+            tc.pg += t.pg;
+            tc.retry += t.retry;
+            if (t.ls.q_max > tc.ls.q_max) tc.ls.q_max = t.ls.q_max;
+            tc.ls.points += t.ls.points;
+            tc.ls.walls += t.ls.walls;
+            tc.ls.disp_max2 = fmax(tc.ls.disp_max2, t.ls.disp_max2);
+            return;
         }
         fp64_tail<D>(m, g, type, Mout, stats, cell, bc, tc.pf, tc.pg, tc.retry, tc.ls, conF, conG, c, st, lf, lg,
                      learned);
+    }
+}
+
+// The mixed path's cell update in block-synchronous phases.  The 128 cells a block claims go
+// together through (1) the collision, stencil set-up, warm start and row table, (2) the
+// FP32 Newton, (3) the phonons' and (4) the fluons' double-float correction and streaming,
+// with a block barrier between phases: the warps of a block then run the same code at the
+// same time, which keeps the instruction working set of an SM to a few phases.  Every
+// thread of the block calls this, active or not.
+template <int D>
+__device__ __forceinline__ void mixed_block(const Model& m, const Geometry& g, const uint8_t* type,
+                                            const double* __restrict__ Min, double* Mout, DevStats* stats,
+                                            long long cell, bool active, BlockCounters& bc, ThreadCounters& tc,
+                                            double* conF, double* conG, char2* rowbuf, const float2* etab,
+                                            long long* bslot, unsigned char* s_mlp, bool mlp) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    const bool has_g = m.K > 0.0;
+    CellState<D> c;
+    Stencil<D> st;
+    bool ok = false;
+    if (active) ok = prepare_cell<D, PREC_MIXED>(m, g, Min, stats, cell, bc, c, st);
+    float lf32[NF], lg32[NG];
+    bool learned = false;
+    {
+        float dl[MlpDims<D>::NOUT];
+        if (mlp) {  // warp-uniform: every lane takes part in the tensor-core inference
+            float xin[MlpDims<D>::NIN];
+            if (ok) mlp_features<D, false>(c, st, xin);
+            warp_mlp<D>(s_mlp, xin, ok, dl);
+            if (ok) tc.mlp_cells++;
+        }
+        if (ok) {
+            tc.cells++;
+            // Eq. (IID13) in FP32, plus the learned or the stored correction
+            maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+            bool fin = true;
+            if (mlp) {
+#pragma unroll
+                for (int k = 0; k < MlpDims<D>::NOUT; k++) fin = fin && isfinite(dl[k]);
+                if (fin) {
+#pragma unroll
+                    for (int j = 0; j < NF; j++) lf32[j] += dl[j];
+                    if (has_g) {
+#pragma unroll
+                        for (int j = 0; j < NG; j++) lg32[j] += dl[NF + j];
+                    }
+                    learned = true;
+                }
+            } else if (m.lam_store) {
+#pragma unroll
+                for (int j = 0; j < NF; j++) {
+                    const float v = m.lam_store[(long long)j * g.ncell + cell];
+                    fin = fin && isfinite(v);
+                    lf32[j] += v;
+                }
+                if (has_g) {
+#pragma unroll
+                    for (int j = 0; j < NG; j++) {
+                        const float v = m.lam_store[(long long)(NF + j) * g.ncell + cell];
+                        fin = fin && isfinite(v);
+                        lg32[j] += v;
+                    }
+                }
+                learned = fin;
+                if (!fin) maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+            }
+#pragma unroll
+            for (int j = 0; j < NF; j++) conF[j] = c.cf[j];
+#pragma unroll
+            for (int j = 0; j < NG; j++) conG[j] = c.cg[j];
+        }
+    }
+    RowTable<D> tab;
+    if (ok) tab.build(c, st, rowbuf);
+    bool alive = ok && tab.ok;
+    __syncthreads();
+    // (2) FP32 Newton to the FP32 noise floor
+    if (alive) {
+        float cf32[NF], cg32[NG];
+#pragma unroll
+        for (int j = 0; j < NF; j++) cf32[j] = (float)conF[j];
+#pragma unroll
+        for (int j = 0; j < NG; j++) cg32[j] = (float)conG[j];
+        int sf, sg;
+        alive = solve_fg32<D, true>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, tc.p32);
+        if (!alive && learned) {
+            tc.retry++;
+            maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
+            alive = solve_fg32<D, true>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, tc.p32);
+        }
+    }
+    __syncthreads();
+    DFStream ds;
+    ds.g = &g;
+    ds.type = type;
+    ds.Mout = Mout;
+    ds.cell = cell;
+    ds.lo = 0;
+    ds.n = 0;
+    ds.ix = ds.iy = 0;
+    ds.near_wall = false;
+    ds.beta = bslot;
+    ds.mh = ds.ml = 0.f;
+    double xm = 0.0;
+    if (alive) {
+        if constexpr (D == 1) {
+            const int b = g.inst_of_cell[cell];
+            ds.lo = g.inst_lo[b];
+            ds.n = g.inst_n[b];
+        } else {
+            ds.iy = (int)(cell / g.NX);
+            ds.ix = (int)(cell - (long long)ds.iy * g.NX);
+            // Sec. III.B: trace paths past solid faces where a solid cell lies within reach
+            if (g.wall_dist)
+                ds.near_wall = (double)g.wall_dist[cell] <= fmax(fabs(c.u[0]), fabs(c.u[1])) + (double)st.R + 1.5;
+        }
+        xm = (double)st.R + 2.0;  // |X|, |Y| of every stencil offset from floor(u)
+    }
+    // (3) phonons
+    double lg[NG];
+    int ug = 0;
+    if (alive && has_g) {
+#pragma unroll
+        for (int j = 0; j < NG; j++) lg[j] = (double)lg32[j];
+        df_split(c.rho * m.K * c.RT, ds.mh, ds.ml);
+        ug = df_population<D, false>(m, c, tab, lg, conG, etab, xm, ds, tc);
+        alive = ug >= 0;
+    }
+    __syncthreads();
+    // (4) fluons
+    double lf[NF];
+    int uf = 0;
+    if (alive) {
+#pragma unroll
+        for (int j = 0; j < NF; j++) lf[j] = (double)lf32[j];
+        df_split(c.rho, ds.mh, ds.ml);
+        uf = df_population<D, true>(m, c, tab, lf, conF, etab, xm, ds, tc);
+        if (uf < 0) {
+            alive = false;
+            if (has_g) {  // take the phonon deposit back too: the FP64 EPR streams both
+                double r[NG], rmax;
+                df_split(-(c.rho * m.K * c.RT), ds.mh, ds.ml);
+                df_pass<D, false, DF_STREAM>(c.u[0], c.u[D - 1], c.inv_sig, tab, lg, conG, etab, xm, r, rmax,
+                                             nullptr, ds, tc.ls, tc.pdf, ds.beta);
+            }
+        }
+    }
+    if (alive) {
+        atomicAdd(&bc.hist[uf], 1ull);
+        if (has_g) atomicAdd(&bc.hist[ug], 1ull);
+        if (m.lam_store) {  // the converged multipliers minus Eq. (IID13), as FP32 corrections
+            const float l0 = (float)maxwell_l0<D>(c.RT);
+#pragma unroll
+            for (int j = 0; j < NF; j++)
+                m.lam_store[(long long)j * g.ncell + cell] = (float)lf[j] - start_base<D>(j, l0);
+#pragma unroll
+            for (int j = 0; j < NG; j++)
+                m.lam_store[(long long)(NF + j) * g.ncell + cell] = has_g ? (float)lg[j] - start_base<D>(j, l0) : 0.f;
+        }
+    } else if (ok) {
+        // the FP64 EPR, out of line, for the rare cells left: no row table (more refinement
+        // levels or rows than it holds), a failed FP32 phase or a missed check
+        tc.redo++;
+        const TailCounts t = fp64_cell_cold<D>(m, g, type, Min, Mout, stats, cell, &bc, conF, conG);
+        tc.pf += t.pf;
+        tc.pg += t.pg;
+        tc.retry += t.retry;
+        if (t.ls.q_max > tc.ls.q_max) tc.ls.q_max = t.ls.q_max;
+        tc.ls.points += t.ls.points;
+        tc.ls.walls += t.ls.walls;
+        tc.ls.disp_max2 = fmax(tc.ls.disp_max2, t.ls.disp_max2);
     }
 }
 
@@ -1213,7 +1317,7 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
 // their hot path for four 128-thread blocks (128 registers); the rest keep the full
 // register file.
 template <int D, int PREC>
-constexpr int min_blocks() { return PREC == PREC_FP32 ? 4 : 1; }
+constexpr int min_blocks() { return PREC == PREC_FP32 ? 4 : (PREC == PREC_MIXED ? 3 : 1); }
 
 template <int D, int PREC>
 __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel(const __grid_constant__ Model m, const __grid_constant__ Geometry g,
@@ -1229,6 +1333,10 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
     Con<PREC>* conF = s_con[threadIdx.x];
     Con<PREC>* conG = conF + NF;
     char2* rowbuf = (D == 2 && PREC != PREC_FP64) ? s_rows[threadIdx.x] : nullptr;
+    // double-float table of 2^(j/512) (mixed path)
+    __shared__ float2 s_exp[PREC == PREC_MIXED ? kExpTab : 1];
+    __shared__ long long s_beta[PREC == PREC_MIXED ? 128 : 1][DFPop<D, true>::NB];  // exponent coefficients
+    if (PREC == PREC_MIXED) exp2_table_init(s_exp);
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
@@ -1236,9 +1344,25 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
     // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
     // the whole cell update would cost the hot path registers or spills
     __shared__ ThreadCounters s_tc[128];
-    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0};
     ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
+    if constexpr (PREC == PREC_MIXED) {  // blocks claim 128-cell chunks and step them in phases
+        __shared__ unsigned long long s_base;
+        for (;;) {
+            if (threadIdx.x == 0) s_base = atomicAdd(work, 128ull);
+            __syncthreads();
+            const unsigned long long base = s_base;
+            __syncthreads();
+            if (base >= (unsigned long long)g.ncell) break;
+            const long long cell = (long long)base + threadIdx.x;
+            const bool active = cell < g.ncell && type[cell] != CELL_SOLID;
+            mixed_block<D>(m, g, type, Min, Mout, stats, cell, active, bc, tc, conF, conG, rowbuf, s_exp,
+                           s_beta[threadIdx.x], s_mlp, mlp);
+        }
+        counters_flush(bc, tc, stats);
+        return;
+    }
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(work, 32ull);
@@ -1260,8 +1384,8 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
             if (ok) tc.mlp_cells++;
         }
         if (ok)
-            finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st, use_mlp ? dl : nullptr,
-                                 rowbuf);
+            finish_cell<D, PREC>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, c, st, use_mlp ? dl : nullptr,
+                                 rowbuf, s_exp, PREC == PREC_MIXED ? s_beta[threadIdx.x] : nullptr);
     }
     counters_flush(bc, tc, stats);
 }
@@ -1289,13 +1413,16 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
     extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
     Con<PREC>* conF = s_con[threadIdx.x];
     Con<PREC>* conG = conF + NF;
+    __shared__ float2 s_exp[PREC == PREC_MIXED ? kExpTab : 1];  // double-float 2^(j/512) (mixed path)
+    __shared__ long long s_beta[PREC == PREC_MIXED ? 128 : 1][DFPop<1, true>::NB];  // exponent coefficients
+    if (PREC == PREC_MIXED) exp2_table_init(s_exp);
     counters_init(bc);
     const bool mlp = m.mlp_w != nullptr;
     if (mlp) mlp_stage_mma<1>(s_mlp, m.mlp_w, m.mlp_nrm);
     // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
     // the whole cell update would cost the hot path registers or spills
     __shared__ ThreadCounters s_tc[128];
-    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0};
+    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0};
     ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
     double Meq[NM];
@@ -1362,8 +1489,8 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
                     if (ok) tc.mlp_cells++;
                 }
                 if (ok)
-                    finish_cell<D, PREC>(m, g, type, Mout, stats, cell, bc, tc, conF, conG, c, st,
-                                         use_mlp ? dl : nullptr, nullptr);
+                    finish_cell<D, PREC>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, c, st,
+                                         use_mlp ? dl : nullptr, nullptr, s_exp, PREC == PREC_MIXED ? s_beta[threadIdx.x] : nullptr);
             }
             counters_to_block(bc, tc);  // keeps the 32-bit tallies of a long launch small
             __syncthreads();

@@ -76,6 +76,7 @@ class lelbm_stats(ctypes.Structure):
         ("mlp_retry", ctypes.c_longlong),
         ("wall_hits", ctypes.c_longlong),
         ("mlp_cells", ctypes.c_longlong),
+        ("points_df", ctypes.c_longlong),
     ]
 
 
