@@ -1,10 +1,13 @@
 #!/usr/bin/env python
 """Throughput benchmark of the LELBM time step on GB300 (one JSON line on rank 0).
 
-Default workload: 4096 seeded 1D Riemann problems of uneven length (256-4096 cells,
-log-uniform), pressure ratios 10-1000, |u| up to Mach 3, one batch handle.  A step is
-one time step of every instance (fluid-boundary fill, collision, LAS, EPR, moment
-streaming).  MLUPS = interior cell updates per second.
+Default workload: the seeded 2D four-quadrant Riemann problem at 4096 x 4096 cells with
+the learned EPR warm start, on the mixed path (FP32 Newton, double-float correction and
+streaming judged at the FP64 tolerance), compared with the plain FP64 path (Eq. IID13
+start) from the same state: MLUPS of both and the L1 density difference between them.
+The FP32 path is reported beside them with its own L1.  A step is one time step of every
+cell (fluid-boundary fill, collision, LAS, EPR, moment streaming).  MLUPS = interior cell
+updates per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload batch1d|hotbox2d|riemann2d|cylinder2d]
@@ -59,11 +62,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch1d", choices=["batch1d", "hotbox2d", "riemann2d", "cylinder2d"])
+    ap.add_argument("--workload", default="riemann2d", choices=["batch1d", "hotbox2d", "riemann2d", "cylinder2d"])
     ap.add_argument("--n-batch", type=int, default=4096)
-    ap.add_argument("--n", type=int, default=1024, help="2D grid size")
+    ap.add_argument("--n", type=int, default=4096, help="2D grid size")
     ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default persistent launch shape")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell", "stored"],
@@ -312,6 +315,9 @@ def run_ours(args):
     from paper_2508_06911_gb300.solver import Solver
 
     B.build()
+    # FMA throughput of this GPU's FP32 and FP64 pipes (the ALU-roofline denominators)
+    fp32_peak = L.lelbm_fma_peak(False)
+    fp64_peak = L.lelbm_fma_peak(True)
     w, desc = make_workload(args, rank)
     # a dedicated stream: the legacy default stream has handle 0, which the ABI reads as
     # "create a stream of your own"
@@ -387,6 +393,7 @@ def run_ours(args):
 
     compare = None
     warm_starts = None
+    fp32_path = None
     if not args.no_compare:
         other = "fp64" if args.precision != "fp64" else "fp32"
         s2 = make(other, "maxwell")  # the plain path: Eq. (IID13) start
@@ -415,36 +422,48 @@ def run_ours(args):
             ms4, st4, _, _ = timed(s4, False)
             compare[start] = summary(ms4, st4)
             s4.close()
+        if args.precision == "mixed":
+            # the FP32 path (FP32 Newton to 3e-4, FP32 streaming) from the same state and start
+            s5 = make("fp32", args.warmstart)
+            ms5, st5, _, _ = timed(s5, False)
+            r5 = s5.get_moments()[0]
+            fp32_path = {**summary(ms5, st5), "warmstart": args.warmstart,
+                         "l1_density_rel": float(np.abs(r5 - r2).sum() / np.abs(r2).sum()),
+                         "note": "L1 against the FP64 path after the same steps"}
+            s5.close()
 
-    # dominant kernel: the fused cell update, ALU bound (FP64 on the FP64 and mixed paths,
-    # FP32 on the FP32 path); one timed launch covers args.steps steps on the persistent path
+    # dominant kernel: the fused cell update, bound by its ALU pipe: FP64 on the FP64 path,
+    # FP32 on the FP32 and mixed paths (the mixed path's double-float passes run on the FP32
+    # pipe).  Algorithmic work (SURVEY-style definition): per stencil point and Newton pass
+    # of a population 2(2N + N(N+1)/2) FLOP (exponent, residual, packed Jacobian), per
+    # streamed point 2 n_mom FLOP; a double-float correction pass counts as a Newton pass,
+    # a double-float streaming pass as streaming.  One timed launch covers args.steps steps
+    # on the persistent path.
     launches = max(st.cell_kernel_launches, 1)
     kern_ms = st.cell_kernel_ms / launches
+    both = newton_flops(N_F[D]) + (newton_flops(N_G[D]) if w.K > 0 else 0)
     flops64 = (st.points_f * newton_flops(N_F[D]) + st.points_g * newton_flops(N_G[D])) / launches
-    flops32 = st.points_32 * (newton_flops(N_F[D]) + newton_flops(N_G[D])) / launches
+    flops32 = st.points_32 * both / launches
+    flops32 += st.points_df_corr * (both / (2 if w.K > 0 else 1)) / launches
     flops_ms = st.points_ms * 2 * N_M[D] / launches
-    if args.precision == "fp32":
-        flops32 += flops_ms
-    else:
+    if args.precision == "fp64":
         flops64 += flops_ms
+    else:
+        flops32 += flops_ms
     steps_per_launch = args.steps if persistent else 1
-    fp64_peak = 1.25e12  # nominal FP64 rate of GB300 (no tensor path for FP64)
-    fp32_peak = 78.2e12  # FP32 FMA probe on this machine's GB300
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     alg_bytes = (2 * s.n_mom * 8 + 1) * interior * steps_per_launch  # read state + write next + type byte
     prec_id = {"fp64": 0, "mixed": 1, "fp32": 2}[args.precision]
     sec = kern_ms / 1e3
-    if args.precision == "fp32":
-        main_side = {"achieved": flops32 / sec / 1e12, "peak": fp32_peak / 1e12,
-                     "peak_source": "FP32 FMA probe on this pool's GB300 (78.2 TFLOP/s)"}
-        other_side = {"fp64_side": {"achieved_tflops": flops64 / sec / 1e12, "peak_tflops": 1.25,
-                                    "note": "FP64 EPR fallback of cells whose FP32 solve failed"}}
+    probe = "lelbm_fma_peak: FMA probe kernel run by this benchmark on this GPU"
+    if args.precision != "fp64":
+        main_side = {"achieved": flops32 / sec / 1e12, "peak": fp32_peak / 1e12, "peak_source": probe + " (FP32)"}
+        other_side = {"fp64_side": {"achieved_tflops": flops64 / sec / 1e12, "peak_tflops": fp64_peak / 1e12,
+                                    "note": "FP64 EPR of the cells the FP32 or double-float finish leaves"}}
     else:
-        main_side = {"achieved": flops64 / sec / 1e12, "peak": fp64_peak / 1e12,
-                     "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.255 measured by an FMA probe)"}
-        other_side = {"fp32_side": {"achieved_tflops": flops32 / sec / 1e12, "peak_tflops": 78.2,
-                                    "peak_source": "FP32 FMA probe on this pool's GB300"}}
+        main_side = {"achieved": flops64 / sec / 1e12, "peak": fp64_peak / 1e12, "peak_source": probe + " (FP64)"}
+        other_side = {"fp32_side": {"achieved_tflops": flops32 / sec / 1e12, "peak_tflops": fp32_peak / 1e12}}
     size = args.n_batch if args.workload == "batch1d" else args.n
     dram = DRAM_PER_STEP.get((args.workload, size, args.precision, args.warmstart))
     roofline = {"bound": "alu", "achieved": main_side["achieved"], "peak": main_side["peak"], "unit": "TFLOP/s",
@@ -496,7 +515,9 @@ def run_ours(args):
                 "config": desc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
                 "speedup_vs_fp64": (value / compare["value"]) if (compare and args.precision != "fp64") else None,
                 "warmstart": args.warmstart if (args.warmstart != "learned" or weights is not None) else "maxwell",
-                "warm_starts": warm_starts, "points_fp32": st.points_32,
+                "warm_starts": warm_starts, "fp32_path": fp32_path, "points_fp32": st.points_32,
+                "points_df_corr": st.points_df_corr, "points_df_stream": st.points_df,
+                "fma_peaks_tflops": {"fp32": fp32_peak / 1e12, "fp64": fp64_peak / 1e12},
                 "points_fp64_newton": st.points_f + st.points_g, "mlp_retry": st.mlp_retry,
                 "mlp_cells_frac": st.mlp_cells / max(st.cells, 1),
                 "gpu_launches": 1 if persistent else int(args.steps * (2 if s.n_cells > interior else 1)),

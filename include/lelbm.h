@@ -84,7 +84,9 @@ extern "C" {
                          totals are conserved to FP64 rounding.  State, macroscopic
                          variables and non-equilibrium moments in FP64.  A cell
                          whose FP32 solve fails is solved by the FP64 EPR.  Error
-                         against LELBM_FP64: about 1e-6 relative per step.  Over
+                         against LELBM_FP64: about 1e-6 relative per step at
+                         moderate temperatures, growing with the velocity set to
+                         about 1e-4 at RT = 32 (q ~ 1700).  Over
                          thousands of 2D steps through the refinement switch
                          (RT = 4/9) the L1 density difference grows to about
                          1e-3, as it does for the FP64 scheme under noise of
@@ -148,7 +150,10 @@ typedef struct {
     long long wall_hits;          /* populations specularly reflected at a solid
                                      face while streaming (Sec. III.B)              */
     long long mlp_cells;          /* cells given the learned warm start             */
-    long long points_df;          /* mixed: stencil points of double-float passes   */
+    long long points_df;          /* mixed: stencil points of double-float streaming
+                                     passes (deposits and take-backs)               */
+    long long points_df_corr;     /* mixed: stencil points of double-float Newton
+                                     correction passes                              */
 } lelbm_stats;
 
 /* Sizes of the structures this library was built with, so a binding can check
@@ -294,6 +299,14 @@ int lelbm_set_mlp(lelbm_t h, const float* params);
  * learned start is set, it takes precedence.  stored = 0 frees the store.
  * Errors: E_NOMEM, E_CUDA. */
 int lelbm_set_warmstart(lelbm_t h, int stored);
+
+/* Measured FMA throughput of the current device in FLOP/s (2 per FMA), FP32 pipe
+ * (fp64 = 0) or FP64 pipe (fp64 = 1): a probe kernel of eight independent FMA
+ * chains per thread on 8 blocks of 256 threads per SM, best of three timed launches
+ * after a warm-up (about 0.1 s).  It is the denominator of the ALU rooflines the
+ * benchmark reports; the paper has no counterpart.  Syncs the device.
+ * Errors: E_INVAL (flops NULL), E_CUDA. */
+int lelbm_fma_peak(int fp64, double* flops);
 
 /* Message of the last failure of h ("" if none; h may be NULL for create). */
 const char* lelbm_last_error(lelbm_t h);

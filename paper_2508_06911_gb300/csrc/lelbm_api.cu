@@ -586,6 +586,7 @@ static int read_stats(lelbm* h, lelbm_stats* s) {
         s->wall_hits = (long long)d.wall_hits;
         s->mlp_cells = (long long)d.mlp_cells;
         s->points_df = (long long)d.points_df;
+        s->points_df_corr = (long long)d.points_df_corr;
     }
     return d.fallback_mx ? LELBM_E_EPR : LELBM_OK;
 }
@@ -864,3 +865,13 @@ extern "C" int lelbm_set_mlp(lelbm_t h, const float* params) {
 }
 
 extern "C" const char* lelbm_last_error(lelbm_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+extern "C" int lelbm_fma_peak(int fp64, double* flops) {
+    if (!flops) return fail(nullptr, LELBM_E_INVAL, "flops is NULL");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, LELBM_E_CUDA, "no CUDA device");
+    const double v = fma_peak(fp64, dev);
+    if (v < 0.0) return fail(nullptr, LELBM_E_CUDA, "FMA probe failed");
+    *flops = v;
+    return LELBM_OK;
+}

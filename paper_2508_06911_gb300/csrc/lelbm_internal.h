@@ -95,7 +95,8 @@ struct DevStats {
     unsigned long long mlp_retry;      // cells whose learned start failed and were re-solved from Eq. IID13
     unsigned long long wall_hits;      // streamed populations reflected at a solid face (Sec. III.B)
     unsigned long long mlp_cells;      // cells given the learned warm start
-    unsigned long long points_df;      // stencil points of double-float passes (mixed path)
+    unsigned long long points_df;      // stencil points of double-float streaming passes (mixed path)
+    unsigned long long points_df_corr; // stencil points of double-float correction passes (mixed path)
 };
 
 void launch_fill_pads(int D, const Model& m, const double inlet[4], double* M, long long ncell,
@@ -115,6 +116,7 @@ void launch_batch_persistent(const Model& m, const Geometry& g, const double inl
                              const int* inst_pad, int* steps_left, int nsteps, int blocks, int threads, int prec,
                              cudaStream_t s);
 int batch_persistent_max_blocks_per_sm(int prec, int threads);
+double fma_peak(int fp64, int device);
 
 // One object file per kernel variant (lelbm_cell.cu, lelbm_batch.cu).
 template <int D, int PREC>

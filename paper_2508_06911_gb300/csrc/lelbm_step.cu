@@ -184,4 +184,55 @@ void launch_macros(int D, double K, const uint8_t* type, const double* M, double
         macros_kernel<2><<<blocks, 256, 0, s>>>(K, type, M, rho, u, RT, ncell);
 }
 
+// ---------------------------------------------------------------------------
+// FMA throughput probe (the denominator of the ALU rooflines): every thread runs eight
+// independent FMA chains, so each scheduler always has independent FMAs to issue.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void fma_probe_kernel(T* out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = fma(x[k], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    if (s == (T)-1.2345e30) out[0] = s;  // keeps the chains live; never true
+}
+
+// Best of three timed launches, in FLOP/s; < 0 on a CUDA error.
+double fma_peak(int fp64, int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1.0;
+    const int blocks = sms * 8, threads = 256;
+    const int iters = fp64 ? 2000 : 100000;
+    void* out = nullptr;
+    if (cudaMalloc(&out, 16) != cudaSuccess) return -1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0);
+        if (fp64)
+            fma_probe_kernel<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-6);
+        else
+            fma_probe_kernel<float><<<blocks, threads>>>((float*)out, iters, 0.9999f, 1e-4f);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+        if (rep > 0 && flops > best) best = flops;  // the first launch is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const bool err = cudaGetLastError() != cudaSuccess;
+    cudaFree(out);
+    return err ? -1.0 : best;
+}
+
 }  // namespace lbm

@@ -628,7 +628,7 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
 // Per-block counters in shared memory, flushed to DevStats once per block.
 struct BlockCounters {
     unsigned long long hist[64];
-    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls, mlpc, pdf;
+    unsigned long long cells, feq, fmx, q, dmax, pf, pg, pm, p32, redo, retry, walls, mlpc, pdf, pdfc;
 };
 
 // Per-thread tallies.
@@ -638,14 +638,15 @@ struct ThreadCounters {
     unsigned int cells, pf, pg, p32, redo, retry;
     LocalStats ls;
     unsigned int mlp_cells;
-    unsigned int pdf;  // stencil points of double-float passes (mixed path)
+    unsigned int pdf;   // stencil points of double-float streaming passes (mixed path)
+    unsigned int pdfc;  // stencil points of double-float correction passes (mixed path)
 };
 
 __device__ __forceinline__ void counters_init(BlockCounters& bc) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) bc.hist[i] = 0;
     if (threadIdx.x == 0)
         bc.cells = bc.feq = bc.fmx = bc.q = bc.dmax = bc.pf = bc.pg = bc.pm = bc.p32 = bc.redo = bc.retry =
-            bc.walls = bc.mlpc = bc.pdf = 0;
+            bc.walls = bc.mlpc = bc.pdf = bc.pdfc = 0;
 }
 
 // Adds the thread tallies to the block counters, then (after a barrier) the block
@@ -663,9 +664,10 @@ __device__ __forceinline__ void counters_to_block(BlockCounters& bc, ThreadCount
     if (tc.ls.walls) atomicAdd(&bc.walls, (ull)tc.ls.walls);
     if (tc.mlp_cells) atomicAdd(&bc.mlpc, (ull)tc.mlp_cells);
     if (tc.pdf) atomicAdd(&bc.pdf, (ull)tc.pdf);
+    if (tc.pdfc) atomicAdd(&bc.pdfc, (ull)tc.pdfc);
     atomicMax(&bc.q, tc.ls.q_max);
     atomicMax(&bc.dmax, (ull)__double_as_longlong(sqrt(tc.ls.disp_max2)));
-    tc = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0};
+    tc = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0, 0};
 }
 
 __device__ __forceinline__ void counters_flush(BlockCounters& bc, ThreadCounters& tc, DevStats* stats) {
@@ -684,6 +686,7 @@ __device__ __forceinline__ void counters_flush(BlockCounters& bc, ThreadCounters
         if (bc.walls) atomicAdd(&stats->wall_hits, bc.walls);
         if (bc.mlpc) atomicAdd(&stats->mlp_cells, bc.mlpc);
         if (bc.pdf) atomicAdd(&stats->points_df, bc.pdf);
+        if (bc.pdfc) atomicAdd(&stats->points_df_corr, bc.pdfc);
         if (bc.feq) atomicAdd(&stats->fallback_eq, bc.feq);
         if (bc.fmx) atomicAdd(&stats->fallback_mx, bc.fmx);
         atomicMax(&stats->q_max, bc.q);
@@ -835,7 +838,9 @@ __device__ __forceinline__ int df_population(const Model& m, const CellState<D>&
     for (int it = 0; it < 2; it++) {
         {
             float MJ[Q::NJ];
-            if (!df_pass<D, FLUON, DF_CORR>(c.u[0], c.u[D - 1], c.inv_sig, tab, lam, con, etab, xm, r, rmax, MJ, ds, tc.ls, tc.pdf, ds.beta)) return -1;
+            if (!df_pass<D, FLUON, DF_CORR>(c.u[0], c.u[D - 1], c.inv_sig, tab, lam, con, etab, xm, r, rmax, MJ, ds,
+                                            tc.ls, tc.pdfc, ds.beta))
+                return -1;
             // far from the FP32 solution's neighbourhood (or non-finite): the FP64 EPR decides
             if (!(rmax < 1e-3)) return -1;
             if (rmax > m.tol && !df_update<D, FLUON>(MJ, r, lam)) return -1;
@@ -1344,7 +1349,7 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
     // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
     // the whole cell update would cost the hot path registers or spills
     __shared__ ThreadCounters s_tc[128];
-    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0};
+    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0, 0};
     ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
     if constexpr (PREC == PREC_MIXED) {  // blocks claim 128-cell chunks and step them in phases
@@ -1422,7 +1427,7 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
     // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
     // the whole cell update would cost the hot path registers or spills
     __shared__ ThreadCounters s_tc[128];
-    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0};
+    s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0, 0};
     ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
     double Meq[NM];
@@ -1468,7 +1473,25 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
                 for (int q = 0; q < NM; q++) Mout[q * g.ncell + first + i] = 0.0;
             if (threadIdx.x == 0) s_next = 0;
             __syncthreads();
-            for (;;) {
+            if constexpr (PREC == PREC_MIXED) {  // block-wide chunks, stepped in phases
+                for (;;) {
+                    __shared__ unsigned int s_base;
+                    if (threadIdx.x == 0) {
+                        s_base = s_next;
+                        s_next += blockDim.x;
+                    }
+                    __syncthreads();
+                    const unsigned int base = s_base;
+                    __syncthreads();
+                    if (base >= (unsigned int)nblk) break;
+                    const int i = (int)base + (int)threadIdx.x;
+                    const long long cell = first + i;
+                    const bool active = i < nblk && type[cell] != CELL_SOLID;
+                    mixed_block<D>(m, g, type, Min, Mout, stats, cell, active, bc, tc, conF, conG, nullptr, s_exp,
+                                   s_beta[threadIdx.x], s_mlp, mlp);
+                }
+            }
+            for (; PREC != PREC_MIXED;) {
                 unsigned int base = 0;
                 if (lane == 0) base = atomicAdd(&s_next, 32u);
                 base = __shfl_sync(0xffffffffu, base, 0);

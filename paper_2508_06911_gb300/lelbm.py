@@ -77,6 +77,7 @@ class lelbm_stats(ctypes.Structure):
         ("wall_hits", ctypes.c_longlong),
         ("mlp_cells", ctypes.c_longlong),
         ("points_df", ctypes.c_longlong),
+        ("points_df_corr", ctypes.c_longlong),
     ]
 
 
@@ -87,7 +88,7 @@ EXPORTS = [
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
     "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
     "lelbm_mlp_size", "lelbm_mlp_init", "lelbm_mlp_loss_grad", "lelbm_mlp_train", "lelbm_step_record",
-    "lelbm_set_mlp", "lelbm_set_warmstart",
+    "lelbm_set_mlp", "lelbm_set_warmstart", "lelbm_fma_peak",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_get_stats.argtypes = [_H, ctypes.POINTER(lelbm_stats)]
         L.lelbm_reset_stats.argtypes = [_H]
         L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
+        L.lelbm_fma_peak.argtypes = [ctypes.c_int, _DP]
         L.lelbm_last_error.argtypes = [_H]
         L.lelbm_last_error.restype = ctypes.c_char_p
         L.lelbm_set_steps.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
@@ -271,6 +273,13 @@ def lelbm_reset_stats(h) -> None:
 
 def lelbm_set_timing(h, on: bool) -> None:
     _check(load().lelbm_set_timing(h, int(on)), h)
+
+
+def lelbm_fma_peak(fp64: bool) -> float:
+    """Measured FMA throughput (FLOP/s) of the current device's FP32 or FP64 pipe."""
+    v = ctypes.c_double(0.0)
+    _check(load().lelbm_fma_peak(int(fp64), ctypes.byref(v)), None)
+    return v.value
 
 
 def lelbm_set_steps(h, steps) -> None:

@@ -16,7 +16,7 @@ def test_reference_arm_prints_one_json_line():
     assert len(lines) == 1
     j = json.loads(lines[0])
     assert j["impl"] == "reference" and j["unit"] == "MLUPS" and j["value"] > 0
-    assert j["config"]["workload"] == "riemann1d_batch_4096"
+    assert j["config"]["workload"] == "riemann2d_4096x4096"  # the GPU arm's default workload
     for k in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling", "dtype",
               "cpu_baseline", "e2e"):
         assert k in j
