@@ -1355,13 +1355,12 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
         }
         q++;
     };
-    auto row = [&](int cy, int xa, int xb) {
-        const float y = D == 2 ? tab.ty(cy) : 0.f;
+    // np points at thermal x = x0 + k dx on the row at thermal y, each of weight wgt
+    auto sweep = [&](float y, float x0, float dx, int np, float wgt) {
         float cfv[4], cgv[3];
         row_coeffs32<D>(lf, lg, y, cfv, cgv);
         const float cf0 = cfv[0], cf1 = cfv[1], cf2 = cfv[2], cf3 = cfv[3];
         const float cg0 = cgv[0], cg1 = cgv[1], cg2 = cgv[2];
-        const float x0 = tab.tx(xa);
         float SF[MS::PF + 1], SG[MS::PG + 1];
 #pragma unroll
         for (int a = 0; a <= MS::PF; a++) SF[a] = 0.f;
@@ -1385,15 +1384,20 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
                 for (int a = 0; a <= MS::PG; a++) SG[a] = fmaf(pw[a], g, SG[a]);
             }
         };
-        const int np = xb - xa + 1;
         float kf = 0.f;  // the point index as a float (exact), with no conversion per point
         int k = 0;
         for (; k + 2 <= np; k += 2, kf += 2.f) {
-            point(fmaf(kf, s32, x0));
-            point(fmaf(kf + 1.f, s32, x0));
+            point(fmaf(kf, dx, x0));
+            point(fmaf(kf + 1.f, dx, x0));
         }
-        if (k < np) point(fmaf(kf, s32, x0));
+        if (k < np) point(fmaf(kf, dx, x0));
         q += (unsigned long long)np;
+        if (wgt != 1.f) {
+#pragma unroll
+            for (int a = 0; a <= MS::PF; a++) SF[a] *= wgt;
+#pragma unroll
+            for (int a = 0; a <= MS::PG; a++) SG[a] *= wgt;
+        }
         if constexpr (D == 1) {
 #pragma unroll
             for (int a = 0; a <= MS::PF; a++) MF[a] += SF[a];
@@ -1414,12 +1418,34 @@ __device__ __forceinline__ unsigned long long moment_pass32(const CellState<D>& 
                 for (int a = 0; a + b <= MS::PG; a++) MG[tix(a, b, MS::PG)] = fmaf(SG[a], yp[b], MG[tix(a, b, MS::PG)]);
         }
     };
+    auto row = [&](int cy, int xa, int xb) { sweep(D == 2 ? tab.ty(cy) : 0.f, tab.tx(xa), s32, xb - xa + 1, 1.f); };
     if (TAB || tab.ok) {
+        // level-0 runs as rows; the children of the split points a..b of a row as child rows
+        // (cy -/+ 1/4) of 2 (b - a + 1) points at p -/+ 1/4, spacing 1/2, weight 2^-D each
         constexpr float wch = D == 1 ? 0.5f : 0.25f;
-        auto child = [&](int p, int cy, int sx, int sy) {
-            add_point(tab.tx(p, 0.25f * (float)sx), D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f, wch);
-        };
-        tab.visit(row, child);
+#pragma unroll 1
+        for (int r = 0; r < (D == 2 ? tab.nrows : 1); r++) {
+            int rx0, rx1, ra, rb, cy = 0;
+            if constexpr (D == 2) {
+                tab.row_ext(r, rx0, rx1, ra, rb);
+                cy = tab.y_first + r;
+            } else {
+                rx0 = tab.x0;
+                rx1 = tab.x1;
+                ra = tab.a;
+                rb = tab.b;
+            }
+            if (ra <= rb) {
+                if (rx0 <= ra - 1) row(cy, rx0, ra - 1);
+                if (rb + 1 <= rx1) row(cy, rb + 1, rx1);
+#pragma unroll 1
+                for (int sy = (D == 2 ? -1 : 0); sy <= (D == 2 ? 1 : 0); sy += 2)
+                    sweep(D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f, tab.tx(ra, -0.25f), 0.5f * s32,
+                          2 * (rb - ra + 1), wch);
+            } else if (rx0 <= rx1) {
+                row(cy, rx0, rx1);
+            }
+        }
     } else if constexpr (!TAB) {
         auto leaf = [&](const double* cp, double dC) {
             add_point((float)((cp[0] - c.u[0]) * c.inv_sig), D == 2 ? (float)((cp[D - 1] - c.u[D - 1]) * c.inv_sig) : 0.f,

@@ -463,6 +463,10 @@ static __device__ __noinline__ bool df_pass(double ux, double uy, double inv_sig
             for (int a = 0; a <= PJ; a++) SJ[a] = fmaf(pw[a], fh, SJ[a]);
         }
     };
+    // Every segment of a row -- its level-0 runs (lattice step 1) and, for split points, its
+    // child rows (children at p -/+ 1/4, step 1/2, weight 2^-D) -- is one arithmetic
+    // progression of points along x, swept by the same loop: the exponent advances by exact
+    // forward differences D0..D3 (int64, kFixBits fractional bits) from its first point.
     const int nrows = D == 2 ? tab.nrows : 1;
 #pragma unroll 1
     for (int rr = 0; rr < nrows; rr++) {
@@ -477,25 +481,22 @@ static __device__ __noinline__ bool df_pass(double ux, double uy, double inv_sig
             rb = tab.b;
         }
         const int Y = cy - tab.yc;
-        if (rx0 <= rx1) {
-            long long gm[P + 1];
-            fix_row<D, FLUON>(beta, Y, gm);
-            DFAcc S[P + 1];
-            float SJ[PJ + 1];
-#pragma unroll
-            for (int a = 0; a <= P; a++) S[a].zero();
-#pragma unroll
-            for (int a = 0; a <= PJ; a++) SJ[a] = 0.f;
-            // level-0 segments: rx0..ra-1 and rb+1..rx1 (the whole row when ra > rb)
+        const bool split = ra <= rb;
+        long long gm[P + 1];
+        if (rx0 <= rx1) fix_row<D, FLUON>(beta, Y, gm);
+        // segments 0, 1: level-0 runs rx0..ra-1 and rb+1..rx1 (the whole row when no point
+        // splits); 2 (and 3 in 2D): the child rows at cy - 1/4 and cy + 1/4
 #pragma unroll 1
-            for (int seg = 0; seg < 2; seg++) {
+        for (int seg = 0; seg < (D == 2 ? 4 : 3); seg++) {
+            long long D0, D1, D2 = 0, D3 = 0;
+            float Xf, h, Yf, y32;
+            int np, dn;
+            if (seg < 2) {
+                if (rx0 > rx1 || (seg == 1 && !split)) continue;
                 const int xa = seg == 0 ? rx0 : rb + 1;
-                const int xb = seg == 0 ? (ra <= rb ? ra - 1 : rx1) : rx1;
-                if (seg == 1 && ra > rb) break;
+                const int xb = seg == 0 ? (split ? ra - 1 : rx1) : rx1;
                 if (xa > xb) continue;
                 const long long x0 = xa - tab.xc;
-                // forward differences of the row polynomial from X = x0 (exact integers)
-                long long D0, D1, D2, D3 = 0;
                 if constexpr (P == 3) {
                     D3 = 6 * gm[3];
                     D2 = 2 * gm[2] + 6 * gm[3] * (x0 + 1);
@@ -506,53 +507,55 @@ static __device__ __noinline__ bool df_pass(double ux, double uy, double inv_sig
                     D1 = gm[1] + gm[2] * (2 * x0 + 1);
                     D0 = (gm[2] * x0 + gm[1]) * x0 + gm[0];
                 }
-                float Xf = (float)x0;
-                const int np = xb - xa + 1;
-#pragma unroll 1
-                for (int k = 0; k < np; k++) {
-                    float fh, fl;
-                    exp2_fix(D0, etab, 0, fh, fl);
-                    accumulate(S, SJ, Xf, fh, fl);
-                    if constexpr (MODE == DF_STREAM)
-                        stream_point((float)tab.xc + Xf, (float)cy, fh, fl, false);
-                    D0 += D1;
-                    D1 += D2;
-                    if constexpr (P == 3) D2 += D3;
-                    Xf += 1.f;
-                }
-                q += (unsigned long long)np;
+                Xf = (float)x0;
+                h = 1.f;
+                np = xb - xa + 1;
+                dn = 0;
+                Yf = (float)Y;
+                y32 = D == 2 ? tab.ty(cy) : 0.f;
                 const int ex = max(abs(xa), abs(xb));
                 dmax = max(dmax, ex * ex + cy * cy);
-            }
-            fold(S, SJ, (float)Y, D == 2 ? tab.ty(cy) : 0.f);
-        }
-        if (ra <= rb) {
-            // split points ra..rb: children at (p +- 1/4, cy +- 1/4), weight 2^-D each
-#pragma unroll 1
-            for (int sy = (D == 2 ? -1 : 0); sy <= (D == 2 ? 1 : 0); sy += 2) {
+            } else {
+                if (!split) break;
+                const int sy = D == 2 ? (seg == 2 ? -1 : 1) : 0;
                 const int n4 = 4 * Y + sy;
                 long long B[P + 1];
                 fix_child_row<D, FLUON>(beta, n4, B);
-                DFAcc S[P + 1];
-                float SJ[PJ + 1];
-#pragma unroll
-                for (int a = 0; a <= P; a++) S[a].zero();
-#pragma unroll
-                for (int a = 0; a <= PJ; a++) SJ[a] = 0.f;
-                const float Yc = 0.25f * (float)n4;
-#pragma unroll 1
-                for (int h = 0; h < 2 * (rb - ra + 1); h++) {
-                    const int m4 = 4 * (ra + (h >> 1) - tab.xc) + ((h & 1) ? 1 : -1);
-                    float fh, fl;
-                    exp2_fix(fix_child_w<P>(B, m4), etab, -D, fh, fl);
-                    const float Xf = 0.25f * (float)m4;
-                    accumulate(S, SJ, Xf, fh, fl);
-                    if constexpr (MODE == DF_STREAM)
-                        stream_point((float)tab.xc + Xf, D == 2 ? (float)tab.yc + Yc : 0.f, fh, fl, true);
-                }
-                q += (unsigned long long)(2 * (rb - ra + 1));
-                fold(S, SJ, Yc, D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f);
+                // N(m) = 64 w at the quarter offsets m = m0, m0 + 2, ... (exact integers)
+                const int m0 = 4 * (ra - tab.xc) - 1;
+                const long long N0 = fix_child_w<P>(B, m0), N1 = fix_child_w<P>(B, m0 + 2),
+                                N2 = fix_child_w<P>(B, m0 + 4);
+                D0 = N0;
+                D1 = N1 - N0;
+                D2 = N2 - 2 * N1 + N0;
+                if constexpr (P == 3) D3 = fix_child_w<P>(B, m0 + 6) - 3 * N2 + 3 * N1 - N0;
+                Xf = 0.25f * (float)m0;
+                h = 0.5f;
+                np = 2 * (rb - ra + 1);
+                dn = -D;
+                Yf = 0.25f * (float)n4;
+                y32 = D == 2 ? tab.ty(cy, 0.25f * (float)sy) : 0.f;
             }
+            DFAcc S[P + 1];
+            float SJ[PJ + 1];
+#pragma unroll
+            for (int a = 0; a <= P; a++) S[a].zero();
+#pragma unroll
+            for (int a = 0; a <= PJ; a++) SJ[a] = 0.f;
+            const float cyf = (float)tab.yc + Yf;  // c_y of the segment's points
+#pragma unroll 1
+            for (int k = 0; k < np; k++) {
+                float fh, fl;
+                exp2_fix(D0, etab, dn, fh, fl);
+                accumulate(S, SJ, Xf, fh, fl);
+                if constexpr (MODE == DF_STREAM) stream_point((float)tab.xc + Xf, cyf, fh, fl, dn != 0);
+                D0 += D1;
+                D1 += D2;
+                if constexpr (P == 3) D2 += D3;
+                Xf += h;
+            }
+            q += (unsigned long long)np;
+            fold(S, SJ, Yf, y32);
         }
     }
     npts += (unsigned int)q;

@@ -1143,6 +1143,44 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     }
 }
 
+// The mixed path's FP32 Newton phase (row table only), out of line: its moment
+// accumulators then have the register file to themselves.  Constraints come from the
+// cell's FP64 scratch slots; lf32, lg32 hold the start and receive the solution.
+template <int D>
+static __device__ __noinline__ bool fp32_phase(const RowTable<D>& tab_in, const double* conF, const double* conG,
+                                               bool has_g, float* lf32_io, float* lg32_io, float rt32, bool learned,
+                                               unsigned int& np32, unsigned int& retry) {
+    constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
+    const RowTable<D> tab = tab_in;
+    CellState<D> c;  // not read: the row table carries the geometry
+    Stencil<D> st;
+    float cf32[NF], cg32[NG], lf32[NF], lg32[NG];
+#pragma unroll
+    for (int j = 0; j < NF; j++) {
+        cf32[j] = (float)conF[j];
+        lf32[j] = lf32_io[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NG; j++) {
+        cg32[j] = (float)conG[j];
+        lg32[j] = lg32_io[j];
+    }
+    unsigned int np = 0;
+    int sf, sg;
+    bool ok = solve_fg32<D, true>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, np);
+    if (!ok && learned) {
+        retry++;
+        maxwell_start32<D, NF, NG>(rt32, lf32, lg32);
+        ok = solve_fg32<D, true>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, np);
+    }
+    np32 += np;
+#pragma unroll
+    for (int j = 0; j < NF; j++) lf32_io[j] = lf32[j];
+#pragma unroll
+    for (int j = 0; j < NG; j++) lg32_io[j] = lg32[j];
+    return ok;
+}
+
 // The mixed path's cell update in block-synchronous phases.  The 128 cells a block claims go
 // together through (1) the collision, stencil set-up, warm start and row table, (2) the
 // FP32 Newton, (3) the phonons' and (4) the fluons' double-float correction and streaming,
@@ -1217,20 +1255,7 @@ __device__ __forceinline__ void mixed_block(const Model& m, const Geometry& g, c
     bool alive = ok && tab.ok;
     __syncthreads();
     // (2) FP32 Newton to the FP32 noise floor
-    if (alive) {
-        float cf32[NF], cg32[NG];
-#pragma unroll
-        for (int j = 0; j < NF; j++) cf32[j] = (float)conF[j];
-#pragma unroll
-        for (int j = 0; j < NG; j++) cg32[j] = (float)conG[j];
-        int sf, sg;
-        alive = solve_fg32<D, true>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, tc.p32);
-        if (!alive && learned) {
-            tc.retry++;
-            maxwell_start32<D, NF, NG>((float)c.RT, lf32, lg32);
-            alive = solve_fg32<D, true>(c, st, tab, cf32, cg32, has_g, lf32, lg32, sf, sg, tc.p32);
-        }
-    }
+    if (alive) alive = fp32_phase<D>(tab, conF, conG, has_g, lf32, lg32, (float)c.RT, learned, tc.p32, tc.retry);
     __syncthreads();
     DFStream ds;
     ds.g = &g;
