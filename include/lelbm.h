@@ -285,6 +285,15 @@ int lelbm_mlp_train(int dims, float* params_dev, const float* X_dev, const float
  * arrays over the padded cells; other rows are left untouched). */
 int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev);
 
+/* The warm-start network's inference as lelbm_step runs it (BF16 weights and BF16
+ * activations between the layers on the tensor cores, FP32 accumulation, SiLU in FP32
+ * rounded to BF16; the persistent batch of lelbm_run_batch uses the packed BF16 tanh
+ * for SiLU instead) on n caller-supplied feature rows: X_dev[n][n_in] (device) ->
+ * Y_dev[n][n_out] (device, predicted targets in raw units).  params: host, n_params
+ * floats, as for lelbm_set_mlp.  Allocates two small device buffers; syncs the stream
+ * (NULL: the legacy default stream).  Errors: E_INVAL, E_NOMEM, E_CUDA. */
+int lelbm_mlp_infer(int dims, const float* params, const float* X_dev, long long n, float* Y_dev, void* stream);
+
 /* Use the network params (host, n_params floats) as warm start; NULL: the plain
  * Maxwellian start. */
 int lelbm_set_mlp(lelbm_t h, const float* params);

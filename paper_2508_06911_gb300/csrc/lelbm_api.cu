@@ -50,6 +50,7 @@ struct lelbm {
     __nv_bfloat16* d_mlp_w = nullptr;  // learned warm start: BF16 weights
     float* d_mlp_nrm = nullptr;        // and normalisation
     float* d_lam = nullptr;            // stored warm start (lelbm_set_warmstart)
+    float* d_mlp_start = nullptr;      // learned start of the current step (cell-update path)
     cudaGraphExec_t graph = nullptr;  // captured lelbm_run_batch launch
     int graph_n = -1, graph_cur = -1;
     bool graph_budgets = false;
@@ -183,6 +184,7 @@ static void free_all(lelbm* h) {
     cudaFree(h->d_mlp_w);
     cudaFree(h->d_mlp_nrm);
     cudaFree(h->d_lam);
+    cudaFree(h->d_mlp_start);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -544,8 +546,17 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
             if (rc) return rc;
             CUDA_TRY(h, cudaEventRecord(ev.first, h->stream));
         }
-        launch_cell_update(h->model, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks,
-                           h->p.precision, h->stream);
+        // the learned warm start runs as its own kernel; the cell update reads its output
+        // (timed with the cell update: it is part of the learned start's cost)
+        Model mc = h->model;
+        if (mc.mlp_w) {
+            launch_mlp_start(mc, h->geo, h->d_type, Min, h->d_mlp_start, h->device, h->stream);
+            mc.mlp_start = h->d_mlp_start;
+            mc.mlp_w = nullptr;
+            mc.mlp_nrm = nullptr;
+        }
+        launch_cell_update(mc, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks, h->p.precision,
+                           h->stream);
         if (h->timing) {
             CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
             h->ev_used.push_back(ev);
@@ -845,6 +856,9 @@ extern "C" int lelbm_set_mlp(lelbm_t h, const float* params) {
     if (!params) {
         h->model.mlp_w = nullptr;
         h->model.mlp_nrm = nullptr;
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_mlp_start);
+        h->d_mlp_start = nullptr;
         if (h->graph) cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
         return LELBM_OK;
@@ -855,6 +869,7 @@ extern "C" int lelbm_set_mlp(lelbm_t h, const float* params) {
     for (long long i = 0; i < nw; i++) w[i] = __float2bfloat16(params[i]);
     if (!h->d_mlp_w) CUDA_TRY(h, cudaMalloc((void**)&h->d_mlp_w, sizeof(__nv_bfloat16) * nw));
     if (!h->d_mlp_nrm) CUDA_TRY(h, cudaMalloc((void**)&h->d_mlp_nrm, sizeof(float) * (ntot - nw)));
+    if (!h->d_mlp_start) CUDA_TRY(h, cudaMalloc((void**)&h->d_mlp_start, sizeof(float) * (size_t)nout * h->ncell));
     CUDA_TRY(h, cudaMemcpy(h->d_mlp_w, w.data(), sizeof(__nv_bfloat16) * nw, cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_mlp_nrm, params + nw, sizeof(float) * (ntot - nw), cudaMemcpyHostToDevice));
     h->model.mlp_w = h->d_mlp_w;
@@ -873,5 +888,32 @@ extern "C" int lelbm_fma_peak(int fp64, double* flops) {
     const double v = fma_peak(fp64, dev);
     if (v < 0.0) return fail(nullptr, LELBM_E_CUDA, "FMA probe failed");
     *flops = v;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_mlp_infer(int dims, const float* params, const float* X_dev, long long n, float* Y_dev,
+                               void* stream) {
+    int nin, nout;
+    long long ntot, nw;
+    if (lelbm_mlp_size(dims, &nin, &nout, &ntot, &nw) != LELBM_OK) return fail(nullptr, LELBM_E_INVAL, "bad dims");
+    if (!params || n < 0 || (n > 0 && (!X_dev || !Y_dev))) return fail(nullptr, LELBM_E_INVAL, "bad argument");
+    if (n == 0) return LELBM_OK;
+    std::vector<__nv_bfloat16> w(nw);
+    for (long long i = 0; i < nw; i++) w[i] = __float2bfloat16(params[i]);
+    __nv_bfloat16* dw = nullptr;
+    float* dn = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMalloc((void**)&dw, sizeof(__nv_bfloat16) * nw) != cudaSuccess ||
+        cudaMalloc((void**)&dn, sizeof(float) * (ntot - nw)) != cudaSuccess) {
+        cudaFree(dw);
+        return fail(nullptr, LELBM_E_NOMEM, "device allocation failed");
+    }
+    cudaMemcpyAsync(dw, w.data(), sizeof(__nv_bfloat16) * nw, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dn, params + nw, sizeof(float) * (ntot - nw), cudaMemcpyHostToDevice, s);
+    launch_mlp_infer(dims, dw, dn, X_dev, n, Y_dev, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(dw);
+    cudaFree(dn);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(nullptr, LELBM_E_CUDA, "MLP inference failed");
     return LELBM_OK;
 }

@@ -40,6 +40,8 @@ struct Model {
     const float* mlp_nrm;          // learned warm start: normalisation
     float* lam_store;              // stored warm start: per-cell multiplier corrections, SoA
                                    // [NF + NG][ncell], or null
+    const float* mlp_start;        // learned warm start of this step: per-cell corrections from
+                                   // mlp_start_kernel, SoA [NF + NG][ncell] (NaN: none), or null
     // FP32 copies for the FP32 path (set by set_fp32_params)
     float K32, nu_s32, nu_b32, Pr32, n_conf32, r_min32, refine_div32;
     double rad2_32[5];  // squared refinement radii, FP32 arithmetic: (refine_rad / 2^L)^2
@@ -117,6 +119,10 @@ void launch_batch_persistent(const Model& m, const Geometry& g, const double inl
                              cudaStream_t s);
 int batch_persistent_max_blocks_per_sm(int prec, int threads);
 double fma_peak(int fp64, int device);
+void launch_mlp_infer(int D, const __nv_bfloat16* W, const float* nrm, const float* X, long long n, float* Y,
+                      cudaStream_t s);
+void launch_mlp_start(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, float* out,
+                      int device, cudaStream_t s);
 
 // One object file per kernel variant (lelbm_cell.cu, lelbm_batch.cu).
 template <int D, int PREC>

@@ -224,12 +224,22 @@ __device__ __forceinline__ unsigned silu_half_bf16x2(float h0, float h1) {
     return *reinterpret_cast<const unsigned*>(&s);
 }
 
+// The same SiLU in FP32, z sigmoid(z) = 2h / (1 + exp(-2h)) (the training kernels' SiLU),
+// rounded once to BF16: for the inference kernels off the hot path.
+__device__ __forceinline__ unsigned silu_half_f32x2(float h0, float h1) {
+    const float s0 = __fdividef(2.f * h0, 1.f + __expf(fminf(-2.f * h0, 80.f)));
+    const float s1 = __fdividef(2.f * h1, 1.f + __expf(fminf(-2.f * h1, 80.f)));
+    const __nv_bfloat162 s = __floats2bfloat162_rn(s0, s1);
+    return *reinterpret_cast<const unsigned*>(&s);
+}
+
 // Whole-warp inference: lane i supplies the raw features x of its cell (ignored when
-// !valid) and receives the raw prediction y.  All 32 lanes must call it.
+// !valid) and receives the raw prediction y.  All 32 lanes must call it.  EXACT: SiLU in
+// FP32 (silu_half_f32x2), else the packed BF16 tanh (silu_half_bf16x2, the hot path).
 // The accumulator fragment of an m16n8 tile holds rows (g, g + 8) x columns (2t, 2t+1)
 // of lane (g, t) -- exactly the operand fragment of the next layer's k-slice -- so
 // the hidden activations stay in registers as BF16 pairs: h[m-tile][k-slice][4].
-template <int D>
+template <int D, bool EXACT = false>
 __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bool valid, float* y) {
     using Md = MlpDims<D>;
     using Mm = MlpMma<D>;
@@ -271,8 +281,8 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
             for (int mt = 0; mt < 2; mt++) {
                 float d[4] = {c0, c1, c0, c1};  // the accumulator starts at the (halved) bias
                 mma_bf16_16x8x16(d, ax[mt][0], ax[mt][1], ax[mt][2], ax[mt][3], bb[u][0], bb[u][1]);
-                h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_half_bf16x2(d[0], d[1]);
-                h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_half_bf16x2(d[2], d[3]);
+                h1[mt][nt >> 1][(nt & 1) * 2 + 0] = EXACT ? silu_half_f32x2(d[0], d[1]) : silu_half_bf16x2(d[0], d[1]);
+                h1[mt][nt >> 1][(nt & 1) * 2 + 1] = EXACT ? silu_half_f32x2(d[2], d[3]) : silu_half_bf16x2(d[2], d[3]);
             }
         }
     }
@@ -297,8 +307,10 @@ __device__ __forceinline__ void warp_mlp(unsigned char* smem, const float* x, bo
         }
 #pragma unroll
         for (int mt = 0; mt < 2; mt++) {
-            h2[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_half_bf16x2(d[mt][0], d[mt][1]);
-            h2[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_half_bf16x2(d[mt][2], d[mt][3]);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 0] =
+                EXACT ? silu_half_f32x2(d[mt][0], d[mt][1]) : silu_half_bf16x2(d[mt][0], d[mt][1]);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 1] =
+                EXACT ? silu_half_f32x2(d[mt][2], d[mt][3]) : silu_half_bf16x2(d[mt][2], d[mt][3]);
         }
     }
     // layer 3: y = h2 W3^T + b3, transposed to one row per lane through shared memory

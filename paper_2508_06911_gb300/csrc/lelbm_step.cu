@@ -159,7 +159,7 @@ void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, 
     long long need = (g.ncell + 127) / 128;
     int blocks = (int)(need < grid_blocks ? need : grid_blocks);
     if (blocks < 1) blocks = 1;
-    const size_t sm = m.mlp_w ? (g.D == 1 ? MlpMma<1>::BYTES : MlpMma<2>::BYTES) : 0;
+    const size_t sm = 0;  // the learned start runs in mlp_start_kernel, not in the cell update
     if (g.D == 1)
         cell_launch<1>(prec, m, g, type, Min, Mout, st, work, blocks, sm, s);
     else
@@ -182,6 +182,109 @@ void launch_macros(int D, double K, const uint8_t* type, const double* M, double
         macros_kernel<1><<<blocks, 256, 0, s>>>(K, type, M, rho, u, RT, ncell);
     else
         macros_kernel<2><<<blocks, 256, 0, s>>>(K, type, M, rho, u, RT, ncell);
+}
+
+// ---------------------------------------------------------------------------
+// Learned warm start as its own kernel (the cell-update kernels read its output the way
+// they read the stored start).  Each warp takes 32 consecutive cells: the FP32 collision
+// module gives the features, and the network (2 x 64 SiLU, BF16 weights staged in shared
+// memory, FP32 accumulation, SiLU in FP32) runs on the tensor cores for the warp's 32
+// cells at once.
+// out[k][cell] (SoA, NOUT rows) receives the predicted correction of Eq. (IID13); NaN
+// where the cell gets no learned start (solid, non-physical).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(128) mlp_start_kernel(const __grid_constant__ Model m,
+                                                        const __grid_constant__ Geometry g,
+                                                        const uint8_t* __restrict__ type,
+                                                        const double* __restrict__ Min, float* __restrict__ out) {
+    constexpr int NM = Dim<D>::NM;
+    extern __shared__ __align__(16) unsigned char s_mlp[];
+    mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long base = ((long long)blockIdx.x * 4 + warp) * 32; base < g.ncell;
+         base += (long long)gridDim.x * 128) {  // warp-uniform
+        const long long cell = base + lane;
+        const bool active = cell < g.ncell && type[cell] != CELL_SOLID;
+        CellState<D> c;
+        Stencil<D> st;
+        bool ok = false;
+        if (active) {
+            double M[NM];
+#pragma unroll
+            for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
+            collide32<D>(M, m, c);
+            ok = c.ok;
+            if (ok) st.init32(c, m);
+        }
+        float xin[MlpDims<D>::NIN], dl[MlpDims<D>::NOUT];
+#pragma unroll
+        for (int k = 0; k < MlpDims<D>::NIN; k++) xin[k] = 0.f;
+        if (ok) mlp_features<D, true>(c, st, xin);
+        warp_mlp<D, true>(s_mlp, xin, ok, dl);
+        if (cell < g.ncell) {
+#pragma unroll
+            for (int k = 0; k < MlpDims<D>::NOUT; k++) out[(long long)k * g.ncell + cell] = ok ? dl[k] : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+void launch_mlp_start(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, float* out,
+                      int device, cudaStream_t s) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const long long warps = (g.ncell + 31) / 32;
+    long long blocks = (warps + 3) / 4;
+    const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (g.D == 1) {
+        cudaFuncSetAttribute(mlp_start_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MlpMma<1>::BYTES);
+        mlp_start_kernel<1><<<(int)blocks, 128, MlpMma<1>::BYTES, s>>>(m, g, type, Min, out);
+    } else {
+        cudaFuncSetAttribute(mlp_start_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MlpMma<2>::BYTES);
+        mlp_start_kernel<2><<<(int)blocks, 128, MlpMma<2>::BYTES, s>>>(m, g, type, Min, out);
+    }
+}
+
+// The same tensor-core inference on caller-supplied feature rows X[n][NIN] -> Y[n][NOUT]
+// (lelbm_mlp_infer).
+template <int D>
+__global__ void __launch_bounds__(128) mlp_infer_kernel(const __nv_bfloat16* W, const float* nrm,
+                                                        const float* __restrict__ X, long long n,
+                                                        float* __restrict__ Y) {
+    constexpr int NIN = MlpDims<D>::NIN, NOUT = MlpDims<D>::NOUT;
+    extern __shared__ __align__(16) unsigned char s_mlp[];
+    mlp_stage_mma<D>(s_mlp, W, nrm);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long base = ((long long)blockIdx.x * 4 + warp) * 32; base < n; base += (long long)gridDim.x * 128) {
+        const long long row = base + lane;
+        const bool valid = row < n;
+        float xin[NIN], dl[NOUT];
+#pragma unroll
+        for (int k = 0; k < NIN; k++) xin[k] = valid ? X[row * NIN + k] : 0.f;
+        warp_mlp<D, true>(s_mlp, xin, valid, dl);
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < NOUT; k++) Y[row * NOUT + k] = dl[k];
+        }
+    }
+}
+
+void launch_mlp_infer(int D, const __nv_bfloat16* W, const float* nrm, const float* X, long long n, float* Y,
+                      cudaStream_t s) {
+    long long blocks = (n + 127) / 128;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    if (D == 1) {
+        cudaFuncSetAttribute(mlp_infer_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MlpMma<1>::BYTES);
+        mlp_infer_kernel<1><<<(int)blocks, 128, MlpMma<1>::BYTES, s>>>(W, nrm, X, n, Y);
+    } else {
+        cudaFuncSetAttribute(mlp_infer_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MlpMma<2>::BYTES);
+        mlp_infer_kernel<2><<<(int)blocks, 128, MlpMma<2>::BYTES, s>>>(W, nrm, X, n, Y);
+    }
 }
 
 // ---------------------------------------------------------------------------

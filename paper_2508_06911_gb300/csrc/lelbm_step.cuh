@@ -1006,6 +1006,13 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     tc.cells++;
     const bool has_g = m.K > 0.0;
+    float dls[MlpDims<D>::NOUT];
+    if (!dl && m.mlp_start) {  // the learned start of this step, from mlp_start_kernel
+#pragma unroll
+        for (int k = 0; k < MlpDims<D>::NOUT; k++) dls[k] = m.mlp_start[(long long)k * g.ncell + cell];
+        dl = dls;
+        tc.mlp_cells++;
+    }
     double lf[NF], lg[NG];
     float lf32[NF], lg32[NG];  // the FP32 path's multipliers
     bool learned = false;
@@ -1187,7 +1194,9 @@ static __device__ __noinline__ bool fp32_phase(const RowTable<D>& tab_in, const 
 // with a block barrier between phases: the warps of a block then run the same code at the
 // same time, which keeps the instruction working set of an SM to a few phases.  Every
 // thread of the block calls this, active or not.
-template <int D>
+// INLINE_MLP: the warm-start network runs here, warp-wide (the persistent 1D batch); the
+// cell-update kernel instead reads the corrections mlp_start_kernel wrote (m.mlp_start).
+template <int D, bool INLINE_MLP>
 __device__ __forceinline__ void mixed_block(const Model& m, const Geometry& g, const uint8_t* type,
                                             const double* __restrict__ Min, double* Mout, DevStats* stats,
                                             long long cell, bool active, BlockCounters& bc, ThreadCounters& tc,
@@ -1203,11 +1212,20 @@ __device__ __forceinline__ void mixed_block(const Model& m, const Geometry& g, c
     bool learned = false;
     {
         float dl[MlpDims<D>::NOUT];
-        if (mlp) {  // warp-uniform: every lane takes part in the tensor-core inference
-            float xin[MlpDims<D>::NIN];
-            if (ok) mlp_features<D, false>(c, st, xin);
-            warp_mlp<D>(s_mlp, xin, ok, dl);
-            if (ok) tc.mlp_cells++;
+        if constexpr (INLINE_MLP) {
+            if (mlp) {  // warp-uniform: every lane takes part in the tensor-core inference
+                float xin[MlpDims<D>::NIN];
+                if (ok) mlp_features<D, false>(c, st, xin);
+                warp_mlp<D>(s_mlp, xin, ok, dl);
+                if (ok) tc.mlp_cells++;
+            }
+        } else {
+            mlp = m.mlp_start != nullptr && ok;
+            if (mlp) {
+#pragma unroll
+                for (int k = 0; k < MlpDims<D>::NOUT; k++) dl[k] = m.mlp_start[(long long)k * g.ncell + cell];
+                tc.mlp_cells++;
+            }
         }
         if (ok) {
             tc.cells++;
@@ -1359,7 +1377,6 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
     __shared__ Con<PREC> s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
     // 2D row tables of the FP32 passes (one per thread)
     __shared__ char2 s_rows[(D == 2 && PREC != PREC_FP64) ? 128 : 1][(D == 2 && PREC != PREC_FP64) ? kRowsMax : 1];
-    extern __shared__ __align__(16) unsigned char s_mlp[];  // warm-start network (when set)
     Con<PREC>* conF = s_con[threadIdx.x];
     Con<PREC>* conG = conF + NF;
     char2* rowbuf = (D == 2 && PREC != PREC_FP64) ? s_rows[threadIdx.x] : nullptr;
@@ -1368,8 +1385,6 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
     __shared__ long long s_beta[PREC == PREC_MIXED ? 128 : 1][DFPop<D, true>::NB];  // exponent coefficients
     if (PREC == PREC_MIXED) exp2_table_init(s_exp);
     counters_init(bc);
-    const bool mlp = m.mlp_w != nullptr;
-    if (mlp) mlp_stage_mma<D>(s_mlp, m.mlp_w, m.mlp_nrm);
     __syncthreads();
     // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
     // the whole cell update would cost the hot path registers or spills
@@ -1387,8 +1402,8 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
             if (base >= (unsigned long long)g.ncell) break;
             const long long cell = (long long)base + threadIdx.x;
             const bool active = cell < g.ncell && type[cell] != CELL_SOLID;
-            mixed_block<D>(m, g, type, Min, Mout, stats, cell, active, bc, tc, conF, conG, rowbuf, s_exp,
-                           s_beta[threadIdx.x], s_mlp, mlp);
+            mixed_block<D, false>(m, g, type, Min, Mout, stats, cell, active, bc, tc, conF, conG, rowbuf, s_exp,
+                                  s_beta[threadIdx.x], nullptr, false);
         }
         counters_flush(bc, tc, stats);
         return;
@@ -1404,18 +1419,9 @@ __global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel
         Stencil<D> st;
         bool ok = false;
         if (active) ok = prepare_cell<D, PREC>(m, g, Min, stats, cell, bc, c, st);
-        float dl[MlpDims<D>::NOUT];
-        // warp-uniform: every lane takes part in the tensor-core inference
-        const bool use_mlp = mlp;
-        if (use_mlp) {
-            float xin[MlpDims<D>::NIN];
-            if (ok) mlp_features<D, PREC == PREC_FP32>(c, st, xin);
-            warp_mlp<D>(s_mlp, xin, ok, dl);
-            if (ok) tc.mlp_cells++;
-        }
         if (ok)
-            finish_cell<D, PREC>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, c, st, use_mlp ? dl : nullptr,
-                                 rowbuf, s_exp, PREC == PREC_MIXED ? s_beta[threadIdx.x] : nullptr);
+            finish_cell<D, PREC>(m, g, type, Min, Mout, stats, cell, bc, tc, conF, conG, c, st, nullptr, rowbuf, s_exp,
+                                 PREC == PREC_MIXED ? s_beta[threadIdx.x] : nullptr);
     }
     counters_flush(bc, tc, stats);
 }
@@ -1512,8 +1518,8 @@ __global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_k
                     const int i = (int)base + (int)threadIdx.x;
                     const long long cell = first + i;
                     const bool active = i < nblk && type[cell] != CELL_SOLID;
-                    mixed_block<D>(m, g, type, Min, Mout, stats, cell, active, bc, tc, conF, conG, nullptr, s_exp,
-                                   s_beta[threadIdx.x], s_mlp, mlp);
+                    mixed_block<D, true>(m, g, type, Min, Mout, stats, cell, active, bc, tc, conF, conG, nullptr,
+                                         s_exp, s_beta[threadIdx.x], s_mlp, mlp);
                 }
             }
             for (; PREC != PREC_MIXED;) {

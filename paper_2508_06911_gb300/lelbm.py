@@ -88,7 +88,7 @@ EXPORTS = [
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
     "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
     "lelbm_mlp_size", "lelbm_mlp_init", "lelbm_mlp_loss_grad", "lelbm_mlp_train", "lelbm_step_record",
-    "lelbm_set_mlp", "lelbm_set_warmstart", "lelbm_fma_peak",
+    "lelbm_set_mlp", "lelbm_set_warmstart", "lelbm_fma_peak", "lelbm_mlp_infer",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -136,6 +136,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_reset_stats.argtypes = [_H]
         L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
         L.lelbm_fma_peak.argtypes = [ctypes.c_int, _DP]
+        L.lelbm_mlp_infer.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
+                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
         L.lelbm_last_error.argtypes = [_H]
         L.lelbm_last_error.restype = ctypes.c_char_p
         L.lelbm_set_steps.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
@@ -280,6 +282,13 @@ def lelbm_fma_peak(fp64: bool) -> float:
     v = ctypes.c_double(0.0)
     _check(load().lelbm_fma_peak(int(fp64), ctypes.byref(v)), None)
     return v.value
+
+
+def lelbm_mlp_infer(dims: int, params: np.ndarray, X_dev: int, n: int, Y_dev: int, stream: int = 0) -> None:
+    """The network's in-kernel inference on n device feature rows (pointers), into Y_dev."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().lelbm_mlp_infer(dims, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), X_dev, n, Y_dev,
+                                  stream), None)
 
 
 def lelbm_set_steps(h, steps) -> None:

@@ -52,6 +52,67 @@ def test_gpu_gradient_matches_fp64_reference(dims):
     assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
 
 
+@pytest.mark.parametrize("dims", [1, 2])
+def test_inference_matches_fp64_forward(dims):
+    """The tensor-core inference lelbm_step runs (standardised inputs and hidden activations
+    in BF16, BF16 weights, FP32 accumulation, SiLU in FP32) against the FP64 reference
+    forward at the same BF16-rounded weights, element by element, on random features over
+    the training range and on features recorded by the plain solver.  BF16 keeps 8 bits:
+    every layer's inputs (standardised features, hidden activations) carry up to 2^-9
+    relative rounding.  Each output is held to twice the first-order propagation of those
+    roundings, |W3| |h2| + |W3| |SiLU'(z2)| |W2| |h1| + ... times 2^-9, computed from the
+    reference's own activations (measured: at most a tenth of it), and the mean error to
+    0.03 of the output scale ys (measured: 1.4e-3 in 1D, 8e-3 to 1.2e-2 in 2D, whose weights
+    give larger sums |W| |h|).  A wrong weight, bias or index is off by O(0.3-1) of ys."""
+    import os
+
+    import torch
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = np.load(os.path.join(root, "paper_2508_06911_gb300", "weights", f"warmstart_{dims}d.npy"))
+    nin, nout, ntot, nw = L.lelbm_mlp_size(dims)
+    q = OM.unpack(dims, p)
+    rng = np.random.default_rng(40 + dims)
+    X_rand = (q["xm"] + q["xs"] * rng.standard_normal((4096, nin))).astype(np.float32)
+    w = (W.riemann_1d(n=300, seed_index=5) if dims == 1
+         else W.random_smooth_2d(24, 20, seed_index=41, RT_lo=0.25, RT_hi=2.0, umag=1.0))
+    s = Solver.riemann1d(w) if dims == 1 else Solver.grid2d(w)
+    X_rec, _ = record_pairs(s, steps=1)
+    s.close()
+    pr = p.astype(np.float64)
+    pr[:nw] = bf16_round(p[:nw])
+    errs = []
+    for name, X in (("random", X_rand), ("recorded", X_rec.cpu().numpy())):
+        Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        Yd = torch.empty((X.shape[0], nout), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        L.lelbm_mlp_infer(dims, p, Xd.data_ptr(), X.shape[0], Yd.data_ptr(), 0)
+        got = Yd.cpu().numpy().astype(np.float64)
+        ref = OM.forward(dims, pr, X.astype(np.float64))
+        err = np.abs(got - ref) / q["ys"]
+        # first-order bound of the BF16 roundings of the three layers' inputs (standardised units)
+        u = OM.unpack(dims, pr)
+        x = (X.astype(np.float64) - u["xm"]) / u["xs"]
+        z1 = x @ u["W1"].T + u["b1"]
+        h1 = OM.silu(z1)
+        z2 = h1 @ u["W2"].T + u["b2"]
+        h2 = OM.silu(z2)
+        a3 = np.abs(u["W3"])
+        d2 = np.abs(OM.silu_grad(z2))
+        d1 = np.abs(OM.silu_grad(z1))
+        e_h2 = np.abs(h2) @ a3.T
+        e_h1 = ((np.abs(h1) @ np.abs(u["W2"]).T) * d2) @ a3.T
+        e_x = ((((np.abs(x) @ np.abs(u["W1"]).T) * d1) @ np.abs(u["W2"]).T) * d2) @ a3.T
+        bound = 2.0 * 2.0 ** -9 * (e_h2 + e_h1 + e_x) + 1e-6
+        print(f"{dims}D inference vs FP64 forward, {name} features ({X.shape[0]}): max {err.max():.3e}, "
+              f"mean {err.mean():.3e} of the output scale, max error / bound {(err / bound).max():.2f}")
+        assert np.all(np.isfinite(got))
+        errs.append((err, bound))
+    for err, bound in errs:
+        assert err.mean() <= 0.03
+        assert np.all(err <= bound)
+
+
 def test_recorded_targets_are_the_oracle_multipliers():
     import torch
 
