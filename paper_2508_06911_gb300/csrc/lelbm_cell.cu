@@ -16,13 +16,13 @@ void CellVariant<D, PREC>::launch(const Model& m, const Geometry& g, const uint8
                                    cudaStream_t s) {
     auto kern = cell_update_kernel<D, PREC>;
     if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<blocks, 128, smem, s>>>(m, g, type, Min, Mout, st, work);
+    kern<<<blocks, cell_threads<PREC>(), smem, s>>>(m, g, type, Min, Mout, st, work);
 }
 
 template <int D, int PREC>
 int CellVariant<D, PREC>::blocks_per_sm() {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_update_kernel<D, PREC>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_update_kernel<D, PREC>, cell_threads<PREC>(), 0);
     return per_sm;
 }
 

@@ -491,7 +491,7 @@ struct Stencil {
 // A cell with more levels, rows or split-point rows, or offsets beyond int8, uses
 // Stencil directly.
 // ---------------------------------------------------------------------------
-constexpr int kRowsMax = 48;
+constexpr int kRowsMax = 56;
 constexpr int kBandMax = 4;  // rows with split points: |y - u_y| <= 3/2 spans at most 4
 
 template <int D>

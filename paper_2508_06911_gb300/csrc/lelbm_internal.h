@@ -18,6 +18,11 @@ enum : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32 = 2 };
 // storage type of a cell's normalised constraints: the FP32 path computes them in FP32
 template <int PREC>
 using Con = typename std::conditional<PREC == PREC_FP32, float, double>::type;
+// Threads per block of the cell update.  The mixed path runs one block of twelve warps per
+// SM: its block-synchronous phases then hold every scheduler of the SM at the same code
+// (one phase's instructions in the instruction caches at a time).
+template <int PREC>
+constexpr int cell_threads() { return PREC == PREC_MIXED ? 384 : 128; }
 
 // Physical and numerical constants of one handle (Sec. II, App. C, App. D).
 struct Model {

@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(128) noalloc_cell_kernel(Model m, Topo t, cons
     double my_dmax = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < t.ncell; cell += stride) {
-        // where this cell's moments come from (Sec. III.A fill, done on the fly)
+        // where this cell's moments come from (Sec. III.A fill, done on the fly); the same
+        // rules as fill_pads_kernel and the pad-source lists the handle builds at create
         long long src = cell;
         bool inflow = false;
         long long lo = 0;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(128) noalloc_cell_kernel(Model m, Topo t, cons
             for (int i = 0; i < NM; i++) M[i] = Min[i * t.ncell + src];
         }
         CellState<D> c;
-        collide<D>(M, m, c);
+        collide<D>(M, m, c);  // as prepare_cell (lelbm_step.cuh) on the FP64 path
         if (!c.ok) {
             atomicAdd(&s_fmx, 1ull);
             atomicMin(&stats->first_fail, (unsigned long long)cell);
@@ -192,6 +193,8 @@ __global__ void __launch_bounds__(128) noalloc_cell_kernel(Model m, Topo t, cons
             atomicAdd(&s_hist[sf < 63 ? sf : 63], 1ull);
             if (has_g) atomicAdd(&s_hist[sg < 63 ? sg : 63], 1ull);
         } else {
+            // the fallback chain of fp64_tail (lelbm_step.cuh): equilibrium constraints, then
+            // normalised Maxwellian weights; a change there must be made here too
             double ef[NF], eg[NG];
 #pragma unroll
             for (int j = 0; j < NF; j++) ef[j] = 0.0;
@@ -244,7 +247,8 @@ __global__ void __launch_bounds__(128) noalloc_cell_kernel(Model m, Topo t, cons
                 atomicMin(&stats->first_fail, (unsigned long long)cell);
             }
         }
-        // moment streaming (Eq. IIE3) with the landing rules of the padded layout
+        // moment streaming (Eq. IIE3) with the landing rules of the padded layout: those of
+        // land() (lelbm_land.cuh) and the cloud-in-cell sharing of scatter_cell (lelbm_step.cuh)
         const double mfs = c.rho, mgs = c.rho * m.K * c.RT;
         unsigned long long q = 0;
         double dmax2 = 0.0;

@@ -156,7 +156,8 @@ static void cell_launch(int prec, const Model& m, const Geometry& g, const uint8
 
 void launch_cell_update(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, double* Mout,
                         DevStats* st, unsigned long long* work, int grid_blocks, int prec, cudaStream_t s) {
-    long long need = (g.ncell + 127) / 128;
+    const int nt = prec == PREC_MIXED ? cell_threads<PREC_MIXED>() : 128;
+    long long need = (g.ncell + nt - 1) / nt;
     int blocks = (int)(need < grid_blocks ? need : grid_blocks);
     if (blocks < 1) blocks = 1;
     const size_t sm = 0;  // the learned start runs in mlp_start_kernel, not in the cell update

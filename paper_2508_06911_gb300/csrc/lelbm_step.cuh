@@ -1365,37 +1365,38 @@ __device__ __forceinline__ void mixed_block(const Model& m, const Geometry& g, c
 // their hot path for four 128-thread blocks (128 registers); the rest keep the full
 // register file.
 template <int D, int PREC>
-constexpr int min_blocks() { return PREC == PREC_FP32 ? 4 : (PREC == PREC_MIXED ? 3 : 1); }
+constexpr int min_blocks() { return PREC == PREC_FP32 ? 4 : (PREC == PREC_MIXED ? 1 : 1); }
 
 template <int D, int PREC>
-__global__ void __launch_bounds__(128, min_blocks<D, PREC>()) cell_update_kernel(const __grid_constant__ Model m, const __grid_constant__ Geometry g,
+__global__ void __launch_bounds__(cell_threads<PREC>(), min_blocks<D, PREC>()) cell_update_kernel(const __grid_constant__ Model m, const __grid_constant__ Geometry g,
                                                           const uint8_t* __restrict__ type,
                                                           const double* __restrict__ Min, double* Mout,
                                                           DevStats* stats, unsigned long long* work) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     __shared__ BlockCounters bc;
-    __shared__ Con<PREC> s_con[128][NF + NG];  // constraints of each thread's cell (out of registers)
+    constexpr int NT = cell_threads<PREC>();
+    __shared__ Con<PREC> s_con[NT][NF + NG];  // constraints of each thread's cell (out of registers)
     // 2D row tables of the FP32 passes (one per thread)
-    __shared__ char2 s_rows[(D == 2 && PREC != PREC_FP64) ? 128 : 1][(D == 2 && PREC != PREC_FP64) ? kRowsMax : 1];
+    __shared__ char2 s_rows[(D == 2 && PREC != PREC_FP64) ? NT : 1][(D == 2 && PREC != PREC_FP64) ? kRowsMax : 1];
     Con<PREC>* conF = s_con[threadIdx.x];
     Con<PREC>* conG = conF + NF;
     char2* rowbuf = (D == 2 && PREC != PREC_FP64) ? s_rows[threadIdx.x] : nullptr;
     // double-float table of 2^(j/512) (mixed path)
     __shared__ float2 s_exp[PREC == PREC_MIXED ? kExpTab : 1];
-    __shared__ long long s_beta[PREC == PREC_MIXED ? 128 : 1][DFPop<D, true>::NB];  // exponent coefficients
+    __shared__ long long s_beta[PREC == PREC_MIXED ? NT : 1][DFPop<D, true>::NB];  // exponent coefficients
     if (PREC == PREC_MIXED) exp2_table_init(s_exp);
     counters_init(bc);
     __syncthreads();
     // per-thread tallies in shared memory: a dozen 64-bit counters kept in registers across
     // the whole cell update would cost the hot path registers or spills
-    __shared__ ThreadCounters s_tc[128];
+    __shared__ ThreadCounters s_tc[NT];
     s_tc[threadIdx.x] = ThreadCounters{0, 0, 0, 0, 0, 0, {0, 0.0, 0, 0}, 0, 0, 0};
     ThreadCounters& tc = s_tc[threadIdx.x];
     const int lane = threadIdx.x & 31;
-    if constexpr (PREC == PREC_MIXED) {  // blocks claim 128-cell chunks and step them in phases
+    if constexpr (PREC == PREC_MIXED) {  // blocks claim NT-cell chunks and step them in phases
         __shared__ unsigned long long s_base;
         for (;;) {
-            if (threadIdx.x == 0) s_base = atomicAdd(work, 128ull);
+            if (threadIdx.x == 0) s_base = atomicAdd(work, (unsigned long long)NT);
             __syncthreads();
             const unsigned long long base = s_base;
             __syncthreads();

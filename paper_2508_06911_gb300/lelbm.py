@@ -373,17 +373,19 @@ def lelbm_step_noalloc(p: lelbm_params, m_in_ptr: int, m_out_ptr: int, stats: le
                        lengths=None, pads=None) -> int:
     """One allocation-free step on caller-owned device buffers (returns the status code).
 
-    ``lengths``/``pads`` (1D batch) are host arrays kept alive for the call.
+    ``lengths``/``pads`` (1D batch) are host arrays kept alive for the call; they go into a
+    copy of ``p``, so the caller's parameters never point at them afterwards.
     """
+    q = lelbm_params.from_buffer_copy(p)
     keep = []
     if lengths is not None:
         arr = np.ascontiguousarray(lengths, dtype=np.int32)
         keep.append(arr)
-        p.lengths = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        p.n_batch = len(arr)
+        q.lengths = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        q.n_batch = len(arr)
     if pads is not None:
         pa = np.ascontiguousarray(pads, dtype=np.int32)
         keep.append(pa)
-        p.pads = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        q.pads = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     sp = ctypes.byref(stats) if stats is not None else ctypes.POINTER(lelbm_stats)()
-    return load().lelbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(m_in_ptr), ctypes.c_void_p(m_out_ptr), sp)
+    return load().lelbm_step_noalloc(ctypes.byref(q), ctypes.c_void_p(m_in_ptr), ctypes.c_void_p(m_out_ptr), sp)

@@ -174,6 +174,62 @@ def test_knudsen_limiter_piecewise():
     assert O.limit_omega(0.05, 0.5) == pytest.approx(0.5 + 0.5 * (np.log10(0.05) + 2))
 
 
+def knudsen_of(D, K, M):
+    rho, u, RT = O.macros(D, K, M)
+    P, Q, G0n, Gn = O.neq(D, K, M)
+    return O.knudsen(D, K, rho, RT, P, Q, G0n, Gn)
+
+
+@pytest.mark.parametrize("D,K", [(1, 4.0), (2, 3.0)])
+def test_knudsen_number_is_dimensionless_and_frame_independent(D, K):
+    """Eq. (D2) pinned by its dimension, not by its formula.  Dividing every velocity of a
+    cell's populations by s is a change of the time unit (the acoustic scaling of Eq. VIB2):
+    the internal energy carried by g scales with RT as s^-2, second-order central moments
+    as s^-2 and third-order ones as s^-3, and a Knudsen number must not change.  A
+    denominator with the wrong power of RT (the two denominators of Eq. D2 swapped, or
+    RT^(3/2) written RT) fails.  A common shift of every velocity (Galilean) leaves the
+    central moments, and Kn, unchanged."""
+    c, f, g = random_population(D)
+    k = knudsen_of(D, K, brute_raw(D, c, f, g * K))
+    assert k > 1e-3
+    for sc in (0.3, 2.5, 11.0):
+        assert knudsen_of(D, K, brute_raw(D, c / sc, f, g * K / sc ** 2)) == pytest.approx(k, rel=1e-10)
+    U = np.array([3.7, -1.2])[:D]
+    assert knudsen_of(D, K, brute_raw(D, c + U, f, g * K)) == pytest.approx(k, rel=1e-9)
+
+
+@pytest.mark.parametrize("D,K", [(1, 4.0), (2, 3.0)])
+def test_knudsen_number_sees_every_nonequilibrium_part(D, K):
+    """Each non-equilibrium part of Eq. (D2) alone gives Kn > 0 (a term dropped from the sums
+    would give 0 for it): the traceless stress, the heat flux of the fluons, the phonons'
+    heat flux, and the bulk mode (energy moved between translational and internal degrees,
+    trace of the stress = -G0^neq).  The weight of |G0^neq| against the stress trace in the
+    same sum is fixed by reading only (nothing independent of Eq. D2 sets it)."""
+    rho, u, RT = 1.1, np.array([0.4, -0.7])[:D], 0.8
+    M0 = O.eq_moments(D, K, rho, u, RT)
+    iM2 = [2] if D == 1 else [3, 4, 5]
+    iMD = [3] if D == 1 else [6, 7]
+    iG0, iG1 = (4, [5]) if D == 1 else (8, [9, 10])
+    cases = []
+    if D == 2:
+        M = M0.copy()
+        M[4] += 0.05  # xy shear stress
+        cases.append(("shear", M))
+    M = M0.copy()
+    M[iMD[0]] += 0.07  # fluon heat flux
+    cases.append(("fluon heat flux", M))
+    M = M0.copy()
+    M[iG1[0]] += 0.06  # phonon heat flux
+    cases.append(("phonon heat flux", M))
+    M = M0.copy()  # bulk mode: translational energy up, internal energy down by as much
+    for i in iM2[::2] if D == 2 else iM2:
+        M[i] += 0.03
+    M[iG0] -= 0.03 * D
+    cases.append(("bulk", M))
+    for name, M in cases:
+        assert knudsen_of(D, K, M) > 1e-3, name
+
+
 @pytest.mark.parametrize("D,K", [(1, 4.0), (2, 3.0)])
 def test_knudsen_number_properties(D, K):
     """Eq. (D2): zero at equilibrium, linear in the non-equilibrium part, invariant under rho scaling."""

@@ -83,6 +83,43 @@ def test_noalloc_2d_outflow_inflow_two_calls():
     s.close()
 
 
+def test_noalloc_1d_periodic_batch_two_calls():
+    """Periodic 1D instances: populations leaving one end of an instance re-enter at the other."""
+    lengths = np.array([24, 40, 31])
+    n = int(lengths.sum())
+    x = np.arange(n) / n
+    rho = 1.0 + 0.2 * np.sin(6 * np.pi * x)
+    u = 0.6 * np.cos(4 * np.pi * x)
+    RT = 0.8 + 0.3 * np.sin(10 * np.pi * x)
+    s = Solver(1, int(lengths[0]), 1, K=4.0, nu=1e-3, Pr=0.71, bc=(2, 2, 2, 2), pad=0, lengths=lengths)
+    s.set_state(rho, u[None], RT)
+    p = params_like(1, int(lengths[0]), 1, (2, 2, 2, 2), 0, 4.0, 1e-3, 0.71)
+    run_pair(s, p, lengths=lengths)
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["random", "hot"])
+def test_noalloc_2d_periodic_two_calls(case):
+    """Fully periodic 2D grids: a smooth random field, and the hot box (u = (10, 10), RT = 2)
+    whose populations wrap around several cells."""
+    w = (W.random_smooth_2d(14, 10, seed_index=19, RT_lo=0.4, RT_hi=1.5, umag=1.5) if case == "random"
+         else W.hot_box(2, 10, 2.0))
+    s = Solver.grid2d(w)
+    p = params_like(2, w.nx, w.ny, (2, 2, 2, 2), 0, w.K, w.nu, w.Pr)
+    run_pair(s, p)
+    s.close()
+
+
+def test_noalloc_2d_periodic_x_padded_y_two_calls():
+    """x periodic (no pads, NX = nx), y with outflow pads."""
+    w = W.random_smooth_2d(16, 12, seed_index=20, RT_lo=0.4, RT_hi=1.4, umag=0.8, periodic=False)
+    w.bc = (2, 2, 0, 0)
+    s = Solver.grid2d(w)
+    p = params_like(2, w.nx, w.ny, w.bc, w.pad, w.K, w.nu, w.Pr, w.inlet)
+    run_pair(s, p)
+    s.close()
+
+
 def test_noalloc_rejects_too_many_instances():
     import torch
 
