@@ -328,7 +328,10 @@ def run_ours(args):
     prec = {"fp32": L.LELBM_FP32, "mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
 
     weights = None
-    wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", f"warmstart_{D}d.npy")
+    # the four-quadrant workload uses the network trained along the config-3 run (the same
+    # generator at 1024^2), the others the network trained on diverse 2D states
+    wname = "warmstart_2d_config3.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
+    wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", wname)
     if args.warmstart == "learned" or not args.no_compare:
         if os.path.exists(wpath):
             weights = np.load(wpath)

@@ -170,74 +170,14 @@ __device__ __forceinline__ void collide(const double* M, const Model& m, CellSta
     }
 }
 
-// The collision module of the FP32 path: the macroscopic variables and the
-// non-equilibrium central moments (differences of nearly equal numbers) in FP64, the
-// relaxation frequencies, the Knudsen limiter and the normalised constraints in FP32
-// (they feed an FP32 Newton solve).  Same equations as collide.
+// The FP32 part of collide32 (App. C, App. D, Eq. IIB10-IIB18 in thermal units) from the
+// non-equilibrium central moments P, Q, G0n, Gn.
 template <int D>
-__device__ __forceinline__ void collide32(const double* M, const Model& m, CellState<D>& c) {
+__device__ __forceinline__ void collide32_tail(const Model& m, CellState<D>& c, const float (&P)[D][D],
+                                               const float* Q, float G0n, const float* Gn) {
     constexpr int NG = Dim<D>::NG;
-    const double K = m.K;
-    const double rho = M[0];
-    // 1 / rho from the FP32 reciprocal and two Newton steps (24 -> 48 -> 53 bits), not
-    // an FP64 division; 1 / (D + K) is a constant of the handle
-    double irho;
-    if (rho > 1e-30 && rho < 1e30) {
-        irho = (double)(1.f / (float)rho);
-        irho = fma(irho, fma(-rho, irho, 1.0), irho);
-        irho = fma(irho, fma(-rho, irho, 1.0), irho);
-    } else {
-        irho = 1.0 / rho;
-    }
-    double usq = 0.0, tr = 0.0;
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        c.u[a] = M[1 + a] * irho;
-        usq += c.u[a] * c.u[a];
-        tr += M[iM2<D>(a, a)];
-    }
-    const double RT = ((tr + M[iG0<D>()]) * irho - usq) * m.inv_dk;
-    c.rho = rho;
-    c.RT = RT;
-    c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
-    if (!c.ok) return;
-    {
-        c.RT32 = (float)RT;
-        const float sf = sqrtf(c.RT32);  // FP32 is enough: it only scales FP32 coordinates
-        c.sig32 = sf;
-        c.isig32 = 1.f / sf;
-        c.sig = (double)sf;
-        c.inv_sig = (double)c.isig32;
-    }
-    // Eq. (IIB9) in FP64
-    float P[D][D];
-    double trP = 0.0;
-    double Pd[D][D];
-#pragma unroll
-    for (int a = 0; a < D; a++)
-#pragma unroll
-        for (int b = 0; b < D; b++) {
-            Pd[a][b] = M[iM2<D>(a, b)] - rho * (c.u[a] * c.u[b] + (a == b ? RT : 0.0));
-            P[a][b] = (float)Pd[a][b];
-        }
-#pragma unroll
-    for (int a = 0; a < D; a++) trP += Pd[a][a];
-    float Q[D];
-#pragma unroll
-    for (int g = 0; g < D; g++) {
-        double s = 0.0;
-#pragma unroll
-        for (int a = 0; a < D; a++) s += c.u[a] * Pd[a][g];
-        Q[g] = (float)(M[iMD<D>(g)] - 2.0 * s - c.u[g] * trP - rho * (usq + (D + 2) * RT) * c.u[g]);
-    }
-    const double G0 = M[iG0<D>()];
-    const float G0n = (float)(G0 - rho * K * RT);
-    float Gn[D];
-#pragma unroll
-    for (int g = 0; g < D; g++) Gn[g] = (float)(M[iG1<D>(g)] - c.u[g] * G0);
-
     // App. C and App. D in FP32
-    const float rf = (float)rho, RTf = c.RT32, sf = c.sig32, Kf = m.K32;
+    const float rf = (float)c.rho, RTf = c.RT32, sf = c.sig32, Kf = m.K32;
     const float inv_f = m.nu_s32 / RTf + 0.5f;
     float wf = 1.f / inv_f;
     const float fb = 2.f / D - 2.f / (D + Kf);
@@ -303,6 +243,123 @@ __device__ __forceinline__ void collide32(const double* M, const Model& m, CellS
 #pragma unroll
         for (int k = 0; k < NG; k++) c.cg32[k] = 0.f;
     }
+}
+
+// The collision module of the FP32 path: the macroscopic variables and the
+// non-equilibrium central moments (differences of nearly equal numbers) in FP64, the
+// relaxation frequencies, the Knudsen limiter and the normalised constraints in FP32
+// (they feed an FP32 Newton solve).  Same equations as collide.
+// ALL32: every step in FP32, from the moments rounded to FP32 once (the warm-start
+// network's inputs, where the FP32 cancellation in the non-equilibrium moments is far below
+// the network's own error).
+template <int D, bool ALL32 = false>
+__device__ __forceinline__ void collide32(const double* M, const Model& m, CellState<D>& c) {
+    constexpr int NG = Dim<D>::NG;
+    if constexpr (ALL32) {
+        float Mf[Dim<D>::NM];
+#pragma unroll
+        for (int i = 0; i < Dim<D>::NM; i++) Mf[i] = (float)M[i];
+        const float rf = Mf[0], irf = 1.f / rf;
+        float uf[D], usq = 0.f, tr = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            uf[a] = Mf[1 + a] * irf;
+            usq = fmaf(uf[a], uf[a], usq);
+            tr += Mf[iM2<D>(a, a)];
+        }
+        const float RTf = ((tr + Mf[iG0<D>()]) * irf - usq) / ((float)D + m.K32);
+        c.rho = (double)rf;
+        c.RT = (double)RTf;
+#pragma unroll
+        for (int a = 0; a < D; a++) c.u[a] = (double)uf[a];
+        c.ok = rf > 0.f && RTf > 0.f && isfinite(rf) && isfinite(RTf);
+        if (!c.ok) return;
+        c.RT32 = RTf;
+        c.sig32 = sqrtf(RTf);
+        c.isig32 = 1.f / c.sig32;
+        c.sig = (double)c.sig32;
+        c.inv_sig = (double)c.isig32;
+        float P[D][D], Q[D], Gn[D];
+        float trP = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = 0; b < D; b++) {
+                P[a][b] = Mf[iM2<D>(a, b)] - rf * (uf[a] * uf[b] + (a == b ? RTf : 0.f));
+                if (a == b) trP += P[a][b];
+            }
+#pragma unroll
+        for (int g = 0; g < D; g++) {
+            float s = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; a++) s += uf[a] * P[a][g];
+            Q[g] = Mf[iMD<D>(g)] - 2.f * s - uf[g] * trP - rf * (usq + (D + 2) * RTf) * uf[g];
+            Gn[g] = Mf[iG1<D>(g)] - uf[g] * Mf[iG0<D>()];
+        }
+        const float G0n = Mf[iG0<D>()] - rf * m.K32 * RTf;
+        collide32_tail<D>(m, c, P, Q, G0n, Gn);
+        return;
+    }
+    const double K = m.K;
+    const double rho = M[0];
+    // 1 / rho from the FP32 reciprocal and two Newton steps (24 -> 48 -> 53 bits), not
+    // an FP64 division; 1 / (D + K) is a constant of the handle
+    double irho;
+    if (rho > 1e-30 && rho < 1e30) {
+        irho = (double)(1.f / (float)rho);
+        irho = fma(irho, fma(-rho, irho, 1.0), irho);
+        irho = fma(irho, fma(-rho, irho, 1.0), irho);
+    } else {
+        irho = 1.0 / rho;
+    }
+    double usq = 0.0, tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        c.u[a] = M[1 + a] * irho;
+        usq += c.u[a] * c.u[a];
+        tr += M[iM2<D>(a, a)];
+    }
+    const double RT = ((tr + M[iG0<D>()]) * irho - usq) * m.inv_dk;
+    c.rho = rho;
+    c.RT = RT;
+    c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
+    if (!c.ok) return;
+    {
+        c.RT32 = (float)RT;
+        const float sf = sqrtf(c.RT32);  // FP32 is enough: it only scales FP32 coordinates
+        c.sig32 = sf;
+        c.isig32 = 1.f / sf;
+        c.sig = (double)sf;
+        c.inv_sig = (double)c.isig32;
+    }
+    // Eq. (IIB9) in FP64
+    float P[D][D];
+    double trP = 0.0;
+    double Pd[D][D];
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = 0; b < D; b++) {
+            Pd[a][b] = M[iM2<D>(a, b)] - rho * (c.u[a] * c.u[b] + (a == b ? RT : 0.0));
+            P[a][b] = (float)Pd[a][b];
+        }
+#pragma unroll
+    for (int a = 0; a < D; a++) trP += Pd[a][a];
+    float Q[D];
+#pragma unroll
+    for (int g = 0; g < D; g++) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) s += c.u[a] * Pd[a][g];
+        Q[g] = (float)(M[iMD<D>(g)] - 2.0 * s - c.u[g] * trP - rho * (usq + (D + 2) * RT) * c.u[g]);
+    }
+    const double G0 = M[iG0<D>()];
+    const float G0n = (float)(G0 - rho * K * RT);
+    float Gn[D];
+#pragma unroll
+    for (int g = 0; g < D; g++) Gn[g] = (float)(M[iG1<D>(g)] - c.u[g] * G0);
+
+    collide32_tail<D>(m, c, P, Q, G0n, Gn);
 }
 
 // ---------------------------------------------------------------------------
@@ -533,38 +590,53 @@ struct RowTable {
         }
     }
 
+    // The membership decisions are those of the FP64 stencil (Stencil::dist2 against
+    // (R + 1/2)^2 and the refinement radius), taken in FP32 first: a test whose FP32 value
+    // lies more than 1e-3 + 1e-5 thr from the threshold thr is decided there (the FP32
+    // rounding of (k - u_x)^2 + dy^2 is below 3e-4 for offsets up to 30), and only the
+    // others are recomputed in FP64 exactly as the stencil computes them.  GB300's FP64
+    // pipe is slow, and a cell makes a few dozen of these tests.
     __device__ __forceinline__ void build(const CellState<D>& c, const Stencil<D>& st, char2* buf) {
         xc = (int)floor(c.u[0]);
         yc = D == 2 ? (int)floor(c.u[D - 1]) : 0;
         s32 = (float)c.inv_sig;
-        fux = (float)((c.u[0] - (double)xc) * c.inv_sig);
-        fuy = D == 2 ? (float)((c.u[D - 1] - (double)yc) * c.inv_sig) : 0.f;
+        const double ux = c.u[0] - (double)xc, uy = D == 2 ? c.u[D - 1] - (double)yc : 0.0;
+        fux = (float)(ux * c.inv_sig);
+        fuy = D == 2 ? (float)(uy * c.inv_sig) : 0.f;
         rows = buf;
         band_first = band_n = 0;
         band = 0ull;
         ok = st.Nr <= 1;
         if (!ok) return;
-        const double rr = sqrt(st.rr2), r1 = sqrt(st.rad2[1]);
-        auto extents = [&](double cy, double s, int& e0, int& e1, int& ea, int& eb) {
+        const float uxf = (float)ux, uyf = (float)uy;
+        const float rr2f = (float)st.rr2, r12f = (float)st.rad2[1];
+        const float rrf = sqrtf(rr2f), r1f = sqrtf(r12f);
+        // is the level-0 point (xc + k, yc + ky) within distance^2 thr of u?
+        auto inside = [&](int k, int ky, float dy2f, double thr, float thrf) -> bool {
+            const float d = (float)k - uxf;
+            const float v = fmaf(d, d, dy2f);
+            const float mg = 1e-3f + 1e-5f * thrf;
+            if (v < thrf - mg) return true;
+            if (v > thrf + mg) return false;
             double p[D];
-            if constexpr (D == 2) p[1] = cy;
-            e0 = (int)floor(c.u[0] - s) - 1;
-            e1 = (int)ceil(c.u[0] + s) + 1;
-            p[0] = (double)e0;
-            while (e0 <= e1 && st.dist2(p) > st.rr2) p[0] = (double)(++e0);
-            p[0] = (double)e1;
-            while (e1 >= e0 && st.dist2(p) > st.rr2) p[0] = (double)(--e1);
+            p[0] = (double)(xc + k);
+            if constexpr (D == 2) p[1] = (double)(yc + ky);
+            return st.dist2(p) <= thr;
+        };
+        // offsets from xc of the row ky: level-0 points e0..e1, split points ea..eb
+        auto extents = [&](int ky, float dy2f, int& e0, int& e1, int& ea, int& eb) {
+            const float sr = sqrtf(fmaxf(rr2f - dy2f, 0.f));
+            e0 = (int)floorf(uxf - sr) - 1;
+            e1 = (int)ceilf(uxf + sr) + 1;
+            while (e0 <= e1 && !inside(e0, ky, dy2f, st.rr2, rr2f)) ++e0;
+            while (e1 >= e0 && !inside(e1, ky, dy2f, st.rr2, rr2f)) --e1;
             ea = 1;
             eb = 0;
             if (st.Nr == 1 && e0 <= e1) {
-                ea = (int)floor(c.u[0] - r1) - 1;
-                eb = (int)ceil(c.u[0] + r1) + 1;
-                ea = ea < e0 ? e0 : ea;
-                eb = eb > e1 ? e1 : eb;
-                p[0] = (double)ea;
-                while (ea <= eb && st.dist2(p) > st.rad2[1]) p[0] = (double)(++ea);
-                p[0] = (double)eb;
-                while (eb >= ea && st.dist2(p) > st.rad2[1]) p[0] = (double)(--eb);
+                ea = max((int)floorf(uxf - r1f) - 1, e0);
+                eb = min((int)ceilf(uxf + r1f) + 1, e1);
+                while (ea <= eb && !inside(ea, ky, dy2f, st.rad2[1], r12f)) ++ea;
+                while (eb >= ea && !inside(eb, ky, dy2f, st.rad2[1], r12f)) --eb;
                 if (ea > eb) {
                     ea = 1;
                     eb = 0;
@@ -572,40 +644,46 @@ struct RowTable {
             }
         };
         if constexpr (D == 1) {
-            extents(0.0, rr, x0, x1, a, b);
-            if (a > b) {
+            int e0, e1, ea, eb;
+            extents(0, 0.f, e0, e1, ea, eb);
+            x0 = xc + e0;
+            x1 = xc + e1;
+            if (ea > eb) {
                 a = x1 + 1;
                 b = x1;
+            } else {
+                a = xc + ea;
+                b = xc + eb;
             }
         } else {
-            y_first = (int)floor(c.u[1] - rr) - 1;
-            const int y_last = (int)ceil(c.u[1] + rr) + 1;
-            nrows = y_last - y_first + 1;
+            const int k_first = (int)floorf(uyf - rrf) - 1, k_last = (int)ceilf(uyf + rrf) + 1;
+            y_first = yc + k_first;
+            nrows = k_last - k_first + 1;
             if (nrows > kRowsMax) {
                 ok = false;
                 return;
             }
             for (int r = 0; r < nrows; r++) {
-                const int cy = y_first + r;
-                const double dy = __dsub_rn((double)cy, c.u[1]);
-                const double dy2 = __dmul_rn(dy, dy);
+                const int ky = k_first + r;
+                const float dy = (float)ky - uyf;
+                const float dy2f = dy * dy;
                 int e0 = 1, e1 = 0, ea = 1, eb = 0;
-                if (dy2 <= st.rr2) extents((double)cy, sqrt(fmax(st.rr2 - dy2, 0.0)), e0, e1, ea, eb);
+                // a row clearly beyond the radius is empty; any other is tested point by point
+                if (dy2f <= rr2f + 1e-3f + 1e-5f * rr2f) extents(ky, dy2f, e0, e1, ea, eb);
                 if (e0 > e1) {
-                    e0 = xc + 1;
-                    e1 = xc;
+                    e0 = 1;
+                    e1 = 0;
                 }
                 if (ea > eb) {
                     ea = e1 + 1;
                     eb = e1;
                 }
-                const int lo = e0 - xc, hi = e1 - xc;
-                if (lo < -127 || hi > 127 || ea - xc < -127 || eb - xc > 127) {
+                if (e0 < -127 || e1 > 127 || ea < -127 || eb > 127) {
                     ok = false;
                     return;
                 }
-                buf[r] = make_char2((signed char)lo, (signed char)hi);
-                if (ea <= eb && !add_band(r, ea - xc, eb - xc)) {
+                buf[r] = make_char2((signed char)e0, (signed char)e1);
+                if (ea <= eb && !add_band(r, ea, eb)) {
                     ok = false;
                     return;
                 }

@@ -187,8 +187,8 @@ void launch_macros(int D, double K, const uint8_t* type, const double* M, double
 
 // ---------------------------------------------------------------------------
 // Learned warm start as its own kernel (the cell-update kernels read its output the way
-// they read the stored start).  Each warp takes 32 consecutive cells: the FP32 collision
-// module gives the features, and the network (2 x 64 SiLU, BF16 weights staged in shared
+// they read the stored start).  Each warp takes 32 consecutive cells: the collision module
+// in FP32 alone gives the features, and the network (2 x 64 SiLU, BF16 weights staged in shared
 // memory, FP32 accumulation, SiLU in FP32) runs on the tensor cores for the warp's 32
 // cells at once.
 // out[k][cell] (SoA, NOUT rows) receives the predicted correction of Eq. (IID13); NaN
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) mlp_start_kernel(const __grid_constant__ 
             double M[NM];
 #pragma unroll
             for (int i = 0; i < NM; i++) M[i] = Min[i * g.ncell + cell];
-            collide32<D>(M, m, c);
+            collide32<D, true>(M, m, c);  // features in FP32 only
             ok = c.ok;
             if (ok) st.init32(c, m);
         }

@@ -1434,8 +1434,13 @@ __global__ void __launch_bounds__(cell_threads<PREC>(), min_blocks<D, PREC>()) c
 // a shared counter.  An instance that ends on an odd step copies its block back, so
 // every instance finishes in buffer A.  steps_left[] (may be null: unlimited) caps
 // each instance and is decremented.
+// The persistent batch keeps 128-thread blocks (a block per instance); on the mixed path
+// three of them per SM (168 registers), as many as the FP32 variant fits at 128.
 template <int PREC>
-__global__ void __launch_bounds__(128, min_blocks<1, PREC>()) batch_persistent_kernel(const __grid_constant__ Model m,
+constexpr int batch_min_blocks() { return PREC == PREC_MIXED ? 3 : min_blocks<1, PREC>(); }
+
+template <int PREC>
+__global__ void __launch_bounds__(128, batch_min_blocks<PREC>()) batch_persistent_kernel(const __grid_constant__ Model m,
                                                                const __grid_constant__ Geometry g, double in0, double in1,
                                                                double in3, int bc_left_inflow, int bc_right_inflow,
                                                                const uint8_t* __restrict__ type, double* A, double* B,

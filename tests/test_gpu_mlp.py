@@ -196,3 +196,37 @@ def test_shipped_networks_save_newton_updates(dims, case):
     assert_close(b.get_moments(), a.get_moments(), 5e-12, "learned vs plain start")
     a.close()
     b.close()
+
+
+def test_learned_start_gains_time_on_the_fp64_path():
+    """What the 2D network trained along the config-3 run (weights/warmstart_2d_config3.npy)
+    gains in time, not only in Newton updates: on the FP64 path, where every Newton update
+    is an FP64 pass over the velocity set, the learned start (the network's kernel included)
+    makes the step faster than Eq. (IID13), with the same results.  The 1024^2 four-quadrant
+    problem, whose run the network was trained on (at other times), steps 3-6; kernel time
+    by CUDA events."""
+    import os
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    params = np.load(os.path.join(here, "..", "paper_2508_06911_gb300", "weights", "warmstart_2d_config3.npy"))
+    w = W.riemann_2d(n=1024, seed_index=2)
+    res = {}
+    for start in ("maxwell", "learned"):
+        s = Solver.grid2d(w)
+        if start == "learned":
+            L.lelbm_set_mlp(s.h, params)
+        s.step(2)
+        s.synchronize()
+        L.lelbm_reset_stats(s.h)
+        L.lelbm_set_timing(s.h, True)
+        s.step(4)
+        st = s.stats()
+        h = np.array(st.newton_hist)
+        res[start] = (st.cell_kernel_ms, float((np.arange(64) * h).sum() / h.sum()), s.get_moments())
+        s.close()
+    (tm, um, Mm), (tl, ul, Ml) = res["maxwell"], res["learned"]
+    print(f"FP64 path, 1024^2 four-quadrant: {um:.2f} -> {ul:.2f} Newton updates per solve, "
+          f"{tm:.1f} -> {tl:.1f} ms for 4 steps (learned start)")
+    assert ul < um - 0.3
+    assert tl < 0.9 * tm
+    assert_close(Ml, Mm, 5e-12, "learned vs plain start")
