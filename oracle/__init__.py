@@ -58,17 +58,17 @@ class Params(ctypes.Structure):
 class Collision(ctypes.Structure):
     _fields_ = [
         ("rho", ctypes.c_double),
-        ("u", ctypes.c_double * 2),
+        ("u", ctypes.c_double * 3),
         ("RT", ctypes.c_double),
-        ("cf", ctypes.c_double * 10),
-        ("cg", ctypes.c_double * 6),
+        ("cf", ctypes.c_double * 19),
+        ("cg", ctypes.c_double * 10),
         ("omega", ctypes.c_double * 3),
         ("Kn", ctypes.c_double),
     ]
 
 
 class Point(ctypes.Structure):
-    _fields_ = [("c", ctypes.c_double * 2), ("dC", ctypes.c_double), ("level", ctypes.c_int)]
+    _fields_ = [("c", ctypes.c_double * 3), ("dC", ctypes.c_double), ("level", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -88,10 +88,11 @@ class Grid(ctypes.Structure):
         ("D", ctypes.c_int),
         ("nx", ctypes.c_int),
         ("ny", ctypes.c_int),
-        ("periodic", ctypes.c_int * 2),
+        ("nz", ctypes.c_int),
+        ("periodic", ctypes.c_int * 3),
         ("pad", ctypes.c_int),
-        ("bc", ctypes.c_int * 4),
-        ("inlet", ctypes.c_double * 4),
+        ("bc", ctypes.c_int * 6),
+        ("inlet", ctypes.c_double * 5),
         ("solid", ctypes.POINTER(ctypes.c_ubyte)),
     ]
 
@@ -146,15 +147,15 @@ def _dp(a: np.ndarray):
 
 
 def nmom(D: int) -> int:
-    return 6 if D == 1 else 11
+    return 2 + 3 * D + D * (D + 1) // 2
 
 
 def nf(D: int) -> int:
-    return 4 if D == 1 else 10
+    return 1 + D + D * (D + 1) // 2 + D * D
 
 
 def ng(D: int) -> int:
-    return 3 if D == 1 else 6
+    return 1 + D + D * (D + 1) // 2
 
 
 def params(D: int, K: float, nu_s: float = 1e-3, nu_b: float = -1.0, Pr: float = 0.71,
@@ -168,7 +169,7 @@ def params(D: int, K: float, nu_s: float = 1e-3, nu_b: float = -1.0, Pr: float =
 def eq_moments(D, K, rho, u, RT) -> np.ndarray:
     """Equilibrium raw moments, Eq. (IIB7) with App. A Eq. (A3), (A7)."""
     out = np.zeros(nmom(D))
-    uu = np.zeros(2)
+    uu = np.zeros(3)
     uu[:D] = np.asarray(u, dtype=np.float64).reshape(-1)[:D]
     lib().orc_eq_moments(D, K, rho, _dp(uu), RT, _dp(out))
     return out
@@ -178,7 +179,7 @@ def macros(D, K, M):
     """Density, velocity, temperature, Eq. (IIB6)."""
     M = np.ascontiguousarray(M, dtype=np.float64)
     rho, RT = ctypes.c_double(), ctypes.c_double()
-    u = np.zeros(2)
+    u = np.zeros(3)
     lib().orc_macros(D, K, _dp(M), ctypes.byref(rho), _dp(u), ctypes.byref(RT))
     return rho.value, u[:D].copy(), RT.value
 
@@ -187,12 +188,12 @@ def neq(D, K, M):
     """Non-equilibrium central moments, Eq. (IIB9): (P[D,D], Q[D], G0n, Gn[D])."""
     M = np.ascontiguousarray(M, dtype=np.float64)
     rho, u, RT = macros(D, K, M)
-    uu = np.zeros(2)
+    uu = np.zeros(3)
     uu[:D] = u
-    P, Q, Gn = np.zeros(4), np.zeros(2), np.zeros(2)
+    P, Q, Gn = np.zeros(9), np.zeros(3), np.zeros(3)
     G0n = ctypes.c_double()
     lib().orc_neq(D, K, _dp(M), rho, _dp(uu), RT, _dp(P), _dp(Q), ctypes.byref(G0n), _dp(Gn))
-    return P.reshape(2, 2)[:D, :D].copy(), Q[:D].copy(), G0n.value, Gn[:D].copy()
+    return P.reshape(3, 3)[:D, :D].copy(), Q[:D].copy(), G0n.value, Gn[:D].copy()
 
 
 def omegas(D, K, RT, nu_s, nu_b, Pr) -> np.ndarray:
@@ -204,9 +205,9 @@ def omegas(D, K, RT, nu_s, nu_b, Pr) -> np.ndarray:
 
 def knudsen(D, K, rho, RT, P, Q, G0n, Gn) -> float:
     """Local Knudsen number, App. D Eq. (D2)."""
-    PP = np.zeros(4)
-    PP.reshape(2, 2)[:D, :D] = P
-    QQ, GG = np.zeros(2), np.zeros(2)
+    PP = np.zeros(9)
+    PP.reshape(3, 3)[:D, :D] = P
+    QQ, GG = np.zeros(3), np.zeros(3)
     QQ[:D] = Q
     GG[:D] = Gn
     return lib().orc_knudsen(D, K, rho, RT, _dp(PP), _dp(QQ), G0n, _dp(GG))
@@ -239,7 +240,7 @@ def refine_levels(p: Params, RT: float) -> int:
 
 def las(D, u, RT, p: Params):
     """LAS velocity set: (c[q,D], dC[q], level[q]), Eq. (IIC6), (IIC9)-(IIC11)."""
-    uu = np.zeros(2)
+    uu = np.zeros(3)
     uu[:D] = np.asarray(u, dtype=np.float64).reshape(-1)[:D]
     cap = 256
     while True:
@@ -256,9 +257,9 @@ def las(D, u, RT, p: Params):
 
 def basis(D, kind, ct):
     """Moment basis T_j(c~) of the EPR constraints and the order of each entry."""
-    T = np.zeros(10)
-    o = (ctypes.c_int * 10)()
-    cc = np.zeros(2)
+    T = np.zeros(19)
+    o = (ctypes.c_int * 19)()
+    cc = np.zeros(3)
     cc[:D] = ct
     n = nf(D) if kind == 0 else ng(D)
     (lib().orc_basis_f if kind == 0 else lib().orc_basis_g)(D, _dp(cc), _dp(T), o)
@@ -267,7 +268,7 @@ def basis(D, kind, ct):
 
 def maxwell_lambda(D, kind, RT) -> np.ndarray:
     """Maxwellian start of the Lagrange multipliers, Eq. (IID13)."""
-    lam = np.zeros(10)
+    lam = np.zeros(19)
     lib().orc_maxwell_lambda(D, kind, RT, _dp(lam))
     return lam[: (nf(D) if kind == 0 else ng(D))].copy()
 
@@ -277,15 +278,15 @@ def epr(D, kind, c, dC, u, RT, con, p: Params, lam0=None):
     q = len(dC)
     buf = (Point * max(q, 1))()
     for i in range(q):
-        buf[i].c[0] = c[i][0]
-        buf[i].c[1] = c[i][1] if D == 2 else 0.0
+        for a in range(3):
+            buf[i].c[a] = c[i][a] if a < D else 0.0
         buf[i].dC = dC[i]
-    uu = np.zeros(2)
+    uu = np.zeros(3)
     uu[:D] = np.asarray(u, dtype=np.float64).reshape(-1)[:D]
     n = nf(D) if kind == 0 else ng(D)
-    lam = np.zeros(10)
+    lam = np.zeros(19)
     lam[:n] = maxwell_lambda(D, kind, RT) if lam0 is None else lam0
-    cc = np.zeros(10)
+    cc = np.zeros(19)
     cc[:n] = con
     pop = np.zeros(max(q, 1))
     st = lib().orc_epr(D, kind, q, buf, _dp(uu), RT, _dp(cc), ctypes.byref(p), _dp(lam), _dp(pop))
@@ -315,15 +316,22 @@ def cell_populations(p: Params, M):
 
 
 def grid(D, nx, ny=1, periodic=(False, False), pad=0, bc=(0, 0, 0, 0), inlet=(1.0, 0.0, 0.0, 1.0),
-         solid=None):
-    """Grid description; ``solid`` is a uint8 array over the padded grid (kept alive on the Grid)."""
+         solid=None, nz=1):
+    """Grid description; ``solid`` is a uint8 array over the padded grid (kept alive on the Grid).
+    bc: per side (x-, x+, y-, y+[, z-, z+]); inlet: (rho, ux, uy, RT) or (rho, ux, uy, uz, RT);
+    periodic: per axis (2 or 3 entries)."""
     g = Grid()
-    g.D, g.nx, g.ny = D, nx, (ny if D == 2 else 1)
-    g.periodic[0], g.periodic[1] = int(periodic[0]), int(periodic[1] if D == 2 else 0)
+    g.D, g.nx, g.ny, g.nz = D, nx, (ny if D >= 2 else 1), (nz if D == 3 else 1)
+    per = tuple(periodic) + (False,) * (3 - len(periodic))
+    for a in range(3):
+        g.periodic[a] = int(per[a]) if a < D else 0
     g.pad = pad
-    for i in range(4):
-        g.bc[i] = bc[i]
-        g.inlet[i] = inlet[i]
+    bcs = tuple(bc) + (0,) * (6 - len(bc))
+    for i in range(6):
+        g.bc[i] = bcs[i]
+    inl = tuple(inlet) if len(inlet) == 5 else (inlet[0], inlet[1], inlet[2], 0.0, inlet[3])
+    for i in range(5):
+        g.inlet[i] = inl[i]
     if solid is not None:
         s = np.ascontiguousarray(solid, dtype=np.uint8)
         g._solid_keep = s
@@ -337,6 +345,13 @@ def padded_shape(g: Grid):
     NX = g.nx + (0 if g.periodic[0] else 2 * g.pad)
     NY = 1 if g.D == 1 else g.ny + (0 if g.periodic[1] else 2 * g.pad)
     return NY, NX
+
+
+def padded_shape3(g: Grid):
+    """(NZ, NY, NX) of the padded grid (NZ = 1 below 3D)."""
+    NY, NX = padded_shape(g)
+    NZ = 1 if g.D < 3 else g.nz + (0 if g.periodic[2] else 2 * g.pad)
+    return NZ, NY, NX
 
 
 def fill_pads(g: Grid, p: Params, M: np.ndarray) -> np.ndarray:
@@ -384,9 +399,12 @@ def run(g: Grid, p: Params, M: np.ndarray, nsteps: int, stats: Stats | None = No
 def state_from_primitives(g: Grid, p: Params, rho, u, RT) -> np.ndarray:
     """Equilibrium moments (Eq. IIB7) of interior primitive fields; pads left zero.
 
-    rho, RT: arrays of the interior shape (ny, nx) (1D: (nx,)); u: (D, ...) components.
+    rho, RT: arrays of the interior shape (ny, nx) (1D: (nx,); 3D: (nz, ny, nx)); u: (D, ...)
+    components.
     """
     D = g.D
+    if D == 3:
+        return _state_from_primitives_3d(g, p, rho, u, RT)
     NY, NX = padded_shape(g)
     px = 0 if g.periodic[0] else g.pad
     py = 0 if (D == 1 or g.periodic[1]) else g.pad
@@ -398,3 +416,19 @@ def state_from_primitives(g: Grid, p: Params, rho, u, RT) -> np.ndarray:
         for i in range(rho.shape[1]):
             M[:, py + j, px + i] = eq_moments(D, p.K, rho[j, i], u[:, j, i], RT[j, i])
     return M.reshape(nmom(D), NY * NX)
+
+
+def _state_from_primitives_3d(g: Grid, p: Params, rho, u, RT) -> np.ndarray:
+    NZ, NY, NX = padded_shape3(g)
+    px = 0 if g.periodic[0] else g.pad
+    py = 0 if g.periodic[1] else g.pad
+    pz = 0 if g.periodic[2] else g.pad
+    M = np.zeros((nmom(3), NZ, NY, NX))
+    rho = np.asarray(rho, dtype=np.float64).reshape(g.nz, g.ny, g.nx)
+    RT = np.asarray(RT, dtype=np.float64).reshape(rho.shape)
+    u = np.asarray(u, dtype=np.float64).reshape(3, *rho.shape)
+    for k in range(rho.shape[0]):
+        for j in range(rho.shape[1]):
+            for i in range(rho.shape[2]):
+                M[:, pz + k, py + j, px + i] = eq_moments(3, p.K, rho[k, j, i], u[:, k, j, i], RT[k, j, i])
+    return M.reshape(nmom(3), NZ * NY * NX)

@@ -33,15 +33,16 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_MAXF 10 /* N_f in 2D: 1 + D + D(D+1)/2 + D^2 (Eq. IIB14-16) */
-#define ORC_MAXG 6  /* N_g in 2D: 1 + D + D(D+1)/2 (Eq. IIB16-17)        */
-#define ORC_MAXM 11 /* stored moments in 2D: 8 fluon + 3 phonon (Eq. IIB5) */
+#define ORC_MAXD 3  /* translational dimensions D = 1, 2, 3                  */
+#define ORC_MAXF 19 /* N_f in 3D: 1 + D + D(D+1)/2 + D^2 (Eq. IIB14-16) */
+#define ORC_MAXG 10 /* N_g in 3D: 1 + D + D(D+1)/2 (Eq. IIB16-17)        */
+#define ORC_MAXM 17 /* stored moments in 3D: 13 fluon + 4 phonon (Eq. IIB5) */
 
 /* ------------------------------------------------------------------------ */
 /* parameters and results shared with the Python loader (ctypes layout)      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int D;             /* translational dimensions, 1 or 2                   */
+    int D;             /* translational dimensions, 1, 2 or 3                */
     double K;          /* internal degrees of freedom                        */
     double nu_s;       /* kinematic shear viscosity, lattice units           */
     double nu_b;       /* kinematic bulk viscosity; < 0 selects omega_b = 1  */
@@ -57,7 +58,7 @@ typedef struct {
 } orc_params;
 
 typedef struct {
-    double rho, u[2], RT;
+    double rho, u[ORC_MAXD], RT;
     double cf[ORC_MAXF]; /* normalised post-collision fluon constraints    */
     double cg[ORC_MAXG]; /* normalised post-collision phonon constraints   */
     double omega[3];     /* omega_f, omega_b, omega_h after the limiter    */
@@ -65,7 +66,7 @@ typedef struct {
 } orc_collision;
 
 typedef struct {
-    double c[2]; /* particle velocity c_i (lattice frame)                    */
+    double c[ORC_MAXD]; /* particle velocity c_i (lattice frame)             */
     double dC;   /* velocity volume Delta C_i (Eq. IIA8, IIC11)              */
     int level;   /* refinement level of the point                           */
 } orc_point;
@@ -81,30 +82,33 @@ typedef struct {
 } orc_stats;
 
 typedef struct {
-    int D, nx, ny;           /* interior size (ny = 1 in 1D)                */
-    int periodic[2];         /* per axis                                    */
+    int D, nx, ny, nz;       /* interior size (ny = 1 in 1D, nz = 1 below 3D) */
+    int periodic[3];         /* per axis                                    */
     int pad;                 /* pad layers on every non-periodic side       */
-    int bc[4];               /* x-, x+, y-, y+: 0 outflow, 1 inflow         */
-    double inlet[4];         /* rho, ux, uy, RT of the inflow state         */
-    const unsigned char* solid; /* padded-grid solid flags or NULL          */
+    int bc[6];               /* x-, x+, y-, y+, z-, z+: 0 outflow, 1 inflow */
+    double inlet[5];         /* rho, ux, uy, uz, RT of the inflow state     */
+    const unsigned char* solid; /* padded-grid solid flags or NULL (1D, 2D) */
 } orc_grid;
 
-int orc_nmom(int D) { return D == 1 ? 6 : 11; }
-int orc_nf(int D) { return D == 1 ? 4 : 10; }
-int orc_ng(int D) { return D == 1 ? 3 : 6; }
+/* N_M = 1 + D + D(D+1)/2 + D (fluons) plus 1 + D (phonons), Eq. (IIB5) */
+int orc_nmom(int D) { return 2 + 3 * D + D * (D + 1) / 2; }
+int orc_nf(int D) { return 1 + D + D * (D + 1) / 2 + D * D; }
+int orc_ng(int D) { return 1 + D + D * (D + 1) / 2; }
 
-/* Stored-moment positions (Eq. IIB5): 1D {M0,Mx,Mxx,MDx,G0,Gx},
- * 2D {M0,Mx,My,Mxx,Mxy,Myy,MDx,MDy,G0,Gx,Gy}.                              */
-static int iM1(int D, int a) { (void)D; return 1 + a; }
-static int iM2(int D, int a, int b) {
-    if (D == 1) return 2;
-    if (a == 0 && b == 0) return 3;
-    if (a == 1 && b == 1) return 5;
-    return 4;
+/* Stored-moment positions (Eq. IIB5): M0, M_a, M_ab (a <= b, row by row),
+ * M_Dg, G0, G_g.  1D {M0,Mx,Mxx,MDx,G0,Gx},
+ * 2D {M0,Mx,My,Mxx,Mxy,Myy,MDx,MDy,G0,Gx,Gy},
+ * 3D {M0,Mx,My,Mz,Mxx,Mxy,Mxz,Myy,Myz,Mzz,MDx,MDy,MDz,G0,Gx,Gy,Gz}.        */
+static int tri(int D, int a, int b) /* position of (a <= b) among the pairs */
+{
+    if (a > b) { int t = a; a = b; b = t; }
+    return a * D - a * (a - 1) / 2 + (b - a);
 }
-static int iMD(int D, int g) { return D == 1 ? 3 : 6 + g; }
-static int iG0(int D) { return D == 1 ? 4 : 8; }
-static int iG1(int D, int g) { return D == 1 ? 5 : 9 + g; }
+static int iM1(int D, int a) { (void)D; return 1 + a; }
+static int iM2(int D, int a, int b) { return 1 + D + tri(D, a, b); }
+static int iMD(int D, int g) { return 1 + D + D * (D + 1) / 2 + g; }
+static int iG0(int D) { return 1 + 2 * D + D * (D + 1) / 2; }
+static int iG1(int D, int g) { return iG0(D) + 1 + g; }
 
 /* ------------------------------------------------------------------------ */
 /* Eq. (IIB7) with App. A Eq. (A3a-b), (A3g), (A7a-b): equilibrium raw moments */
@@ -142,18 +146,18 @@ void orc_macros(int D, double K, const double* M, double* rho, double* u, double
 /* Eq. (IIB9): non-equilibrium central moments.
  * out: P[a][b] = M~neq_ab, Q[g] = M~neq_Dg, *G0n = G~neq_0, Gn[g] = G~neq_g. */
 void orc_neq(int D, double K, const double* M, double rho, const double* u, double RT,
-             double* P /* [2][2] */, double* Q, double* G0n, double* Gn)
+             double* P /* [3][3] */, double* Q, double* G0n, double* Gn)
 {
     double usq = 0.0;
     for (int a = 0; a < D; a++) usq += u[a] * u[a];
     for (int a = 0; a < D; a++)                               /* (IIB9a) */
         for (int b = 0; b < D; b++)
-            P[2 * a + b] = M[iM2(D, a, b)] - rho * (u[a] * u[b] + (a == b ? RT : 0.0));
+            P[3 * a + b] = M[iM2(D, a, b)] - rho * (u[a] * u[b] + (a == b ? RT : 0.0));
     double trP = 0.0;
-    for (int a = 0; a < D; a++) trP += P[2 * a + a];
+    for (int a = 0; a < D; a++) trP += P[3 * a + a];
     for (int g = 0; g < D; g++) {                             /* (IIB9b) */
         double s = 0.0;
-        for (int a = 0; a < D; a++) s += u[a] * P[2 * a + g];
+        for (int a = 0; a < D; a++) s += u[a] * P[3 * a + g];
         Q[g] = M[iMD(D, g)] - 2.0 * s - u[g] * trP - rho * (usq + (D + 2) * RT) * u[g];
     }
     *G0n = M[iG0(D)] - rho * K * RT;                          /* (IIB9c) */
@@ -184,7 +188,7 @@ double orc_knudsen(int D, double K, double rho, double RT, const double* P, cons
 {
     double s2 = 0.0, s3 = 0.0;
     for (int a = 0; a < D; a++)
-        for (int b = 0; b < D; b++) s2 += fabs(P[2 * a + b] / rho);
+        for (int b = 0; b < D; b++) s2 += fabs(P[3 * a + b] / rho);
     s2 += fabs(G0n / rho);
     for (int g = 0; g < D; g++) s3 += fabs(Q[g] / rho) + fabs(Gn[g] / rho);
     double k2 = s2 / ((D + K) * RT);
@@ -211,9 +215,9 @@ void orc_collide(const orc_params* p, const double* M, orc_collision* out)
 {
     int D = p->D;
     double K = p->K;
-    double rho, u[2] = {0, 0}, RT;
+    double rho, u[ORC_MAXD] = {0, 0, 0}, RT;
     orc_macros(D, K, M, &rho, u, &RT);
-    double P[4] = {0, 0, 0, 0}, Q[2] = {0, 0}, G0n, Gn[2] = {0, 0};
+    double P[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, Q[ORC_MAXD] = {0, 0, 0}, G0n, Gn[ORC_MAXD] = {0, 0, 0};
     orc_neq(D, K, M, rho, u, RT, P, Q, &G0n, Gn);
 
     double om[3];
@@ -225,12 +229,12 @@ void orc_collide(const orc_params* p, const double* M, orc_collision* out)
 
     /* Eq. (IIB10)-(IIB11): bulk and shear parts of M~neq_ab. */
     double bulk = -G0n / D;
-    double shear[4];
+    double shear[9];
     for (int a = 0; a < D; a++)
-        for (int b = 0; b < D; b++) shear[2 * a + b] = P[2 * a + b] - (a == b ? bulk : 0.0);
+        for (int b = 0; b < D; b++) shear[3 * a + b] = P[3 * a + b] - (a == b ? bulk : 0.0);
 
     /* Eq. (IIB14): per-dimension heat-flux constraints M~neq_{aa|g}. */
-    double h[2][2];
+    double h[ORC_MAXD][ORC_MAXD];
     for (int a = 0; a < D; a++)
         for (int g = 0; g < D; g++) h[a][g] = (1.0 + 2.0 * (a == g)) / (D + 2) * Q[g];
 
@@ -244,7 +248,7 @@ void orc_collide(const orc_params* p, const double* M, orc_collision* out)
     int j = 1 + D;
     for (int a = 0; a < D; a++)
         for (int b = a; b < D; b++) {      /* (IIB16c)                     */
-            double m = rho * RT * (a == b) + (1.0 - wf) * shear[2 * a + b] +
+            double m = rho * RT * (a == b) + (1.0 - wf) * shear[3 * a + b] +
                        (1.0 - wb) * (a == b ? bulk : 0.0);
             cf[j++] = m / rho;
         }
@@ -261,8 +265,7 @@ void orc_collide(const orc_params* p, const double* M, orc_collision* out)
                 cg[k++] = (a == b) ? rho * K * RT * RT / nrm : 0.0;
     }
     out->rho = rho;
-    out->u[0] = u[0];
-    out->u[1] = D == 2 ? u[1] : 0.0;
+    for (int a = 0; a < ORC_MAXD; a++) out->u[a] = a < D ? u[a] : 0.0;
     out->RT = RT;
     out->omega[0] = wf;
     out->omega[1] = wb;
@@ -312,15 +315,16 @@ static double dist2(int D, const double* c, const double* u)
  * points of Fig. 4.  Returns q, or -q_needed when max_pts is too small. */
 int orc_las(int D, const double* u_in, double RT, const orc_params* p, orc_point* pts, int max_pts)
 {
-    double u[2] = {u_in[0], D == 2 ? u_in[1] : 0.0};
+    double u[ORC_MAXD];
+    for (int a = 0; a < ORC_MAXD; a++) u[a] = a < D ? u_in[a] : 0.0;
     int R = orc_acoustic_radius(p, RT);
     double rr = R + 0.5;
     double rr2 = rr * rr;
     int Nr = orc_refine_levels(p, RT);
 
-    /* level 0: scan the bounding box, keep the disk */
-    int lo[2], hi[2];
-    for (int a = 0; a < 2; a++) {
+    /* level 0: scan the bounding box, keep the disk (ball in 3D) */
+    int lo[ORC_MAXD], hi[ORC_MAXD];
+    for (int a = 0; a < ORC_MAXD; a++) {
         if (a < D) {
             lo[a] = (int)floor(u[a] - rr) - 1;
             hi[a] = (int)ceil(u[a] + rr) + 1;
@@ -331,21 +335,21 @@ int orc_las(int D, const double* u_in, double RT, const orc_params* p, orc_point
     int cap = 64;
     orc_point* cur = (orc_point*)malloc(sizeof(orc_point) * cap);
     int n = 0;
-    for (int cy = lo[1]; cy <= hi[1]; cy++)
-        for (int cx = lo[0]; cx <= hi[0]; cx++) {
-            double c[2] = {(double)cx, (double)cy};
-            if (dist2(D, c, u) <= rr2) {
-                if (n == cap) {
-                    cap *= 2;
-                    cur = (orc_point*)realloc(cur, sizeof(orc_point) * cap);
+    for (int cz = lo[2]; cz <= hi[2]; cz++)
+        for (int cy = lo[1]; cy <= hi[1]; cy++)
+            for (int cx = lo[0]; cx <= hi[0]; cx++) {
+                double c[ORC_MAXD] = {(double)cx, (double)cy, (double)cz};
+                if (dist2(D, c, u) <= rr2) {
+                    if (n == cap) {
+                        cap *= 2;
+                        cur = (orc_point*)realloc(cur, sizeof(orc_point) * cap);
+                    }
+                    for (int a = 0; a < ORC_MAXD; a++) cur[n].c[a] = a < D ? c[a] : 0.0;
+                    cur[n].dC = 1.0;
+                    cur[n].level = 0;
+                    n++;
                 }
-                cur[n].c[0] = c[0];
-                cur[n].c[1] = D == 2 ? c[1] : 0.0;
-                cur[n].dC = 1.0;
-                cur[n].level = 0;
-                n++;
             }
-        }
 
     /* internal refinement, one level at a time */
     double h = 1.0;
@@ -362,7 +366,8 @@ int orc_las(int D, const double* u_in, double RT, const orc_params* p, orc_point
                 for (int k = 0; k < nch; k++) {
                     orc_point ch = cur[i];
                     ch.c[0] = cur[i].c[0] + ((k & 1) ? q4 : -q4);
-                    if (D == 2) ch.c[1] = cur[i].c[1] + ((k & 2) ? q4 : -q4);
+                    if (D >= 2) ch.c[1] = cur[i].c[1] + ((k & 2) ? q4 : -q4);
+                    if (D == 3) ch.c[2] = cur[i].c[2] + ((k & 4) ? q4 : -q4);
                     ch.dC = cur[i].dC * pow(0.5, D);
                     ch.level = L;
                     nxt[m++] = ch;
@@ -390,7 +395,8 @@ int orc_las(int D, const double* u_in, double RT, const orc_params* p, orc_point
 /* ------------------------------------------------------------------------ */
 
 /* Fluon basis T_j(c~): 1, c~_a, c~_a c~_b (a <= b), c~_a^2 c~_g (Eq. IIB14-16),
- * ordered g-major: (xx|x, yy|x, xx|y, yy|y) in 2D. Order of each in ord. */
+ * ordered g-major: (xx|x, yy|x, xx|y, yy|y) in 2D, (xx|x, yy|x, zz|x, xx|y, ...)
+ * in 3D. Order of each in ord. */
 void orc_basis_f(int D, const double* ct, double* T, int* ord)
 {
     int j = 0;
@@ -471,7 +477,7 @@ int orc_epr(int D, int kind, int q, const orc_point* pts, const double* u, doubl
     int ord[ORC_MAXF];
     double T[ORC_MAXF];
     double scale[ORC_MAXF];
-    double ct0[2] = {0.0, 0.0};
+    double ct0[ORC_MAXD] = {0.0, 0.0, 0.0};
     if (kind == 0) orc_basis_f(D, ct0, T, ord); else orc_basis_g(D, ct0, T, ord);
     for (int j = 0; j < n; j++) scale[j] = pow(sqrt(RT), ord[j]);
 
@@ -480,7 +486,8 @@ int orc_epr(int D, int kind, int q, const orc_point* pts, const double* u, doubl
         double r[ORC_MAXF];
         for (int j = 0; j < n; j++) r[j] = 0.0;
         for (int k = 0; k < q; k++) {
-            double ct[2] = {pts[k].c[0] - u[0], D == 2 ? pts[k].c[1] - u[1] : 0.0};
+            double ct[ORC_MAXD];
+            for (int a = 0; a < ORC_MAXD; a++) ct[a] = a < D ? pts[k].c[a] - u[a] : 0.0;
             if (kind == 0) orc_basis_f(D, ct, T, NULL); else orc_basis_g(D, ct, T, NULL);
             double e = 1.0;
             for (int j = 0; j < n; j++) e += lam[j] * T[j];
@@ -501,7 +508,8 @@ int orc_epr(int D, int kind, int q, const orc_point* pts, const double* u, doubl
         double A[ORC_MAXF * ORC_MAXF];                          /* (IID11a) */
         for (int i = 0; i < n * n; i++) A[i] = 0.0;
         for (int k = 0; k < q; k++) {
-            double ct[2] = {pts[k].c[0] - u[0], D == 2 ? pts[k].c[1] - u[1] : 0.0};
+            double ct[ORC_MAXD];
+            for (int a = 0; a < ORC_MAXD; a++) ct[a] = a < D ? pts[k].c[a] - u[a] : 0.0;
             if (kind == 0) orc_basis_f(D, ct, T, NULL); else orc_basis_g(D, ct, T, NULL);
             for (int i = 0; i < n; i++)
                 for (int j = 0; j < n; j++) A[i * n + j] += T[i] * pop[k] * T[j];
@@ -571,8 +579,9 @@ static int solve_cell(const orc_params* p, int q, const orc_point* pts, const or
     }
     double s = 0.0;
     for (int k = 0; k < q; k++) {
-        double ct[2] = {pts[k].c[0] - co->u[0], D == 2 ? pts[k].c[1] - co->u[1] : 0.0};
-        double w = pts[k].dC * exp(-dist2(D, ct, (double[2]){0.0, 0.0}) / (2.0 * co->RT));
+        double ct[ORC_MAXD];
+        for (int a = 0; a < ORC_MAXD; a++) ct[a] = a < D ? pts[k].c[a] - co->u[a] : 0.0;
+        double w = pts[k].dC * exp(-dist2(D, ct, (double[ORC_MAXD]){0.0, 0.0, 0.0}) / (2.0 * co->RT));
         popf[k] = w;
         s += w;
     }
@@ -618,6 +627,11 @@ static int grid_NY(const orc_grid* g)
     if (g->D == 1) return 1;
     return g->ny + (g->periodic[1] ? 0 : 2 * g->pad);
 }
+static int grid_NZ(const orc_grid* g)
+{
+    if (g->D < 3) return 1;
+    return g->nz + (g->periodic[2] ? 0 : 2 * g->pad);
+}
 
 /* Sec. III.A fluid boundary: pad cells take, on an inflow side, the
  * equilibrium moments of the prescribed state (non-equilibrium dropped),
@@ -626,34 +640,41 @@ static int grid_NY(const orc_grid* g)
  * side wins at corners (x sides before y sides). */
 void orc_fill_pads(const orc_grid* g, const orc_params* p, double* M)
 {
-    int D = g->D, NX = grid_NX(g), NY = grid_NY(g), nm = orc_nmom(D);
-    long ncell = (long)NX * NY;
+    int D = g->D, NX = grid_NX(g), NY = grid_NY(g), NZ = grid_NZ(g), nm = orc_nmom(D);
+    long ncell = (long)NX * NY * NZ;
     int px = g->periodic[0] ? 0 : g->pad;
     int py = (D == 1 || g->periodic[1]) ? 0 : g->pad;
+    int pz = (D < 3 || g->periodic[2]) ? 0 : g->pad;
     int ny = D == 1 ? 1 : g->ny;
+    int nz = D < 3 ? 1 : g->nz;
     double Meq[ORC_MAXM];
-    double uin[2] = {g->inlet[1], g->inlet[2]};
-    orc_eq_moments(D, p->K, g->inlet[0], uin, g->inlet[3], Meq);
-    for (int iy = 0; iy < NY; iy++)
-        for (int ix = 0; ix < NX; ix++) {
-            int inx = ix >= px && ix < px + g->nx;
-            int iny = iy >= py && iy < py + ny;
-            if (inx && iny) continue;
-            int inflow = 0;
-            if (ix < px && g->bc[0] == 1) inflow = 1;
-            if (ix >= px + g->nx && g->bc[1] == 1) inflow = 1;
-            if (D == 2 && iy < py && g->bc[2] == 1) inflow = 1;
-            if (D == 2 && iy >= py + ny && g->bc[3] == 1) inflow = 1;
-            long dst = (long)iy * NX + ix;
-            if (inflow) {
-                for (int m = 0; m < nm; m++) M[m * ncell + dst] = Meq[m];
-            } else {
-                int sx = ix < px ? px : (ix >= px + g->nx ? px + g->nx - 1 : ix);
-                int sy = iy < py ? py : (iy >= py + ny ? py + ny - 1 : iy);
-                long src = (long)sy * NX + sx;
-                for (int m = 0; m < nm; m++) M[m * ncell + dst] = M[m * ncell + src];
+    double uin[ORC_MAXD] = {g->inlet[1], g->inlet[2], g->inlet[3]};
+    orc_eq_moments(D, p->K, g->inlet[0], uin, g->inlet[4], Meq);
+    for (int iz = 0; iz < NZ; iz++)
+        for (int iy = 0; iy < NY; iy++)
+            for (int ix = 0; ix < NX; ix++) {
+                int inx = ix >= px && ix < px + g->nx;
+                int iny = iy >= py && iy < py + ny;
+                int inz = iz >= pz && iz < pz + nz;
+                if (inx && iny && inz) continue;
+                int inflow = 0;
+                if (ix < px && g->bc[0] == 1) inflow = 1;
+                if (ix >= px + g->nx && g->bc[1] == 1) inflow = 1;
+                if (D >= 2 && iy < py && g->bc[2] == 1) inflow = 1;
+                if (D >= 2 && iy >= py + ny && g->bc[3] == 1) inflow = 1;
+                if (D == 3 && iz < pz && g->bc[4] == 1) inflow = 1;
+                if (D == 3 && iz >= pz + nz && g->bc[5] == 1) inflow = 1;
+                long dst = ((long)iz * NY + iy) * NX + ix;
+                if (inflow) {
+                    for (int m = 0; m < nm; m++) M[m * ncell + dst] = Meq[m];
+                } else {
+                    int sx = ix < px ? px : (ix >= px + g->nx ? px + g->nx - 1 : ix);
+                    int sy = iy < py ? py : (iy >= py + ny ? py + ny - 1 : iy);
+                    int sz = iz < pz ? pz : (iz >= pz + nz ? pz + nz - 1 : iz);
+                    long src = ((long)sz * NY + sy) * NX + sx;
+                    for (int m = 0; m < nm; m++) M[m * ncell + dst] = M[m * ncell + src];
+                }
             }
-        }
 }
 
 /* Landing cell along one axis; returns -1 when the population leaves the
@@ -764,11 +785,14 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
  * Returns 0, or -1 on allocation failure. */
 int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* Mout, orc_stats* st)
 {
-    int D = g->D, NX = grid_NX(g), NY = grid_NY(g), nm = orc_nmom(D);
-    long ncell = (long)NX * NY;
+    int D = g->D, NX = grid_NX(g), NY = grid_NY(g), NZ = grid_NZ(g), nm = orc_nmom(D);
+    long ncell = (long)NX * NY * NZ;
     int px = g->periodic[0] ? 0 : g->pad;
     int py = (D == 1 || g->periodic[1]) ? 0 : g->pad;
+    int pz = (D < 3 || g->periodic[2]) ? 0 : g->pad;
     int ny = D == 1 ? 1 : g->ny;
+    int nz = D < 3 ? 1 : g->nz;
+    const unsigned char* solid = D <= 2 ? g->solid : NULL; /* solid cells: 1D and 2D only */
     double* W = (double*)malloc(sizeof(double) * nm * ncell);
     if (!W) return -1;
     memcpy(W, Min, sizeof(double) * nm * ncell);
@@ -779,10 +803,11 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
     orc_point* pts = (orc_point*)malloc(sizeof(orc_point) * cap);
     double* popf = (double*)malloc(sizeof(double) * cap);
     double* popg = (double*)malloc(sizeof(double) * cap);
+    for (int iz = 0; iz < NZ; iz++)
     for (int iy = 0; iy < NY; iy++)
         for (int ix = 0; ix < NX; ix++) {
-            long cell = (long)iy * NX + ix;
-            if (g->solid && g->solid[cell]) continue;
+            long cell = ((long)iz * NY + iy) * NX + ix;
+            if (solid && solid[cell]) continue;
             double M[ORC_MAXM];
             for (int m = 0; m < nm; m++) M[m] = W[m * ncell + cell];
             orc_collision co;
@@ -805,46 +830,51 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
             for (int k = 0; k < q; k++) {
                 const double* c = pts[k].c;
                 if (st) {
-                    double cm = sqrt(dist2(D, c, (double[2]){0.0, 0.0}));
+                    double cm = sqrt(dist2(D, c, (double[ORC_MAXD]){0.0, 0.0, 0.0}));
                     if (cm > st->disp_max) st->disp_max = cm;
                 }
                 /* landing point: x + c, or the end of the reflected path (Sec. III.B) */
-                double cl[2] = {c[0], D == 2 ? c[1] : 0.0}, pos[2];
+                double cl[ORC_MAXD] = {c[0], D >= 2 ? c[1] : 0.0, D == 3 ? c[2] : 0.0}, pos[ORC_MAXD];
                 int fi = ix, fj = iy;
-                if (g->solid) {
+                if (solid) {
                     double off[2];
                     int touched = orc_trace_path(g, NX, NY, ix, iy, c, &fi, &fj, off, cl);
                     if (st && touched) st->wall_hits++;
                     pos[0] = fi + off[0];
                     pos[1] = fj + off[1];
+                    pos[2] = 0.0;
                 } else {
                     pos[0] = ix + c[0];
-                    pos[1] = iy + (D == 2 ? c[1] : 0.0);
+                    pos[1] = iy + (D >= 2 ? c[1] : 0.0);
+                    pos[2] = iz + (D == 3 ? c[2] : 0.0);
                 }
                 double mf = mscale * popf[k], mg = p->K > 0.0 ? gscale * popg[k] : 0.0;
                 /* cloud-in-cell split of the landing position */
-                int i0[2] = {0, 0};
-                double w1[2] = {0.0, 0.0};
+                int i0[ORC_MAXD] = {0, 0, 0};
+                double w1[ORC_MAXD] = {0.0, 0.0, 0.0};
                 for (int a = 0; a < D; a++) {
                     double fl = floor(pos[a]);
                     i0[a] = (int)fl;
                     w1[a] = pos[a] - fl;
                 }
                 int ncx = w1[0] > 0.0 ? 2 : 1;
-                int ncy = (D == 2 && w1[1] > 0.0) ? 2 : 1;
+                int ncy = (D >= 2 && w1[1] > 0.0) ? 2 : 1;
+                int ncz = (D == 3 && w1[2] > 0.0) ? 2 : 1;
+                for (int sz = 0; sz < ncz; sz++)
                 for (int sy = 0; sy < ncy; sy++)
                     for (int sx = 0; sx < ncx; sx++) {
                         double w = (sx ? w1[0] : 1.0 - w1[0]);
-                        if (D == 2) w *= (sy ? w1[1] : 1.0 - w1[1]);
-                        int cx_ = i0[0] + sx, cy_ = D == 2 ? i0[1] + sy : 0;
-                        double cw[2] = {cl[0], cl[1]};
+                        if (D >= 2) w *= (sy ? w1[1] : 1.0 - w1[1]);
+                        if (D == 3) w *= (sz ? w1[2] : 1.0 - w1[2]);
+                        int cx_ = i0[0] + sx, cy_ = D >= 2 ? i0[1] + sy : 0, cz_ = D == 3 ? i0[2] + sz : 0;
+                        double cw[ORC_MAXD] = {cl[0], cl[1], cl[2]};
                         /* reading: a share that would fall on a solid cell is the mirror
                          * image of one arriving from the image lattice, so it is mirrored
                          * back across the wall with the normal velocity component reversed
                          * (exact for flat walls, Sec. III.B).  A diagonal share behind a
                          * flat wall (one side cell fluid) goes to that side cell; behind a
                          * corner of solid cells it goes to the final cell, both reversed. */
-                        if (solid_at(g, NX, NY, cx_, cy_)) {
+                        if (solid && solid_at(g, NX, NY, cx_, cy_)) {
                             int ox = cx_ != fi, oy = cy_ != fj;
                             if (ox && oy) {
                                 int sa = solid_at(g, NX, NY, cx_, fj), sb = solid_at(g, NX, NY, fi, cy_);
@@ -865,12 +895,13 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
                         }
                         double dM[ORC_MAXM];
                         raw_contrib(D, cw, mf, mg, dM);
-                        /* px = 0 on a periodic axis, py likewise */
+                        /* px = 0 on a periodic axis, py and pz likewise */
                         int tx = land_axis(cx_, g->nx, px, g->periodic[0]);
-                        int ty = 0;
-                        if (D == 2) ty = land_axis(cy_, ny, py, g->periodic[1]);
-                        if (tx < 0 || ty < 0) continue;
-                        long tgt = (long)ty * NX + tx;
+                        int ty = 0, tz = 0;
+                        if (D >= 2) ty = land_axis(cy_, ny, py, g->periodic[1]);
+                        if (D == 3) tz = land_axis(cz_, nz, pz, g->periodic[2]);
+                        if (tx < 0 || ty < 0 || tz < 0) continue;
+                        long tgt = ((long)tz * NY + ty) * NX + tx;
                         for (int m = 0; m < nm; m++) Mout[m * ncell + tgt] += w * dM[m];
                     }
             }
