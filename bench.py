@@ -49,6 +49,9 @@ DRAM_PER_STEP = {
     ("batch1d", 4096, "fp32", "learned"): (1366.3e6, "profiles/batch_persistent_fp32_riemann1d_batch4096.md"),
     ("batch1d", 4096, "fp64", "maxwell"): (1008.8e6, "profiles/batch_persistent_fp64_riemann1d_batch4096.md"),
     ("riemann2d", 1024, "fp32", "learned"): (339.8e6, "profiles/cell_update_fp32_riemann2d_1024.md"),
+    ("riemann2d", 1024, "mixed", "learned"): (1115.8e6, "profiles/cell_update_mixed_riemann2d_1024.md"),
+    # one-pass capture (dram bytes only) of the full 4096^2 workload
+    ("riemann2d", 4096, "mixed", "learned"): (18.34e9, "profiles/cell_update_mixed_riemann2d_1024.md (4096^2 capture)"),
 }
 
 
@@ -481,6 +484,8 @@ def run_ours(args):
                 "hbm": {"achieved_gbs": alg_bytes / sec / 1e9, "peak_gbs": hbm_peak,
                         "frac": alg_bytes / sec / 1e9 / hbm_peak,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}}
+    # per step: pad fill (padded grids), the warm-start network (learned start), the cell update
+    launches_per_step = 1 + (s.n_cells > interior) + (args.warmstart == "learned" and weights is not None)
     hist = list(st.newton_hist)
     solves = sum(hist)
     mean_updates = sum(i * h for i, h in enumerate(hist)) / max(solves, 1)
@@ -523,7 +528,7 @@ def run_ours(args):
                 "fma_peaks_tflops": {"fp32": fp32_peak / 1e12, "fp64": fp64_peak / 1e12},
                 "points_fp64_newton": st.points_f + st.points_g, "mlp_retry": st.mlp_retry,
                 "mlp_cells_frac": st.mlp_cells / max(st.cells, 1),
-                "gpu_launches": 1 if persistent else int(args.steps * (2 if s.n_cells > interior else 1)),
+                "gpu_launches": 1 if persistent else int(args.steps * launches_per_step),
                 "clocks": clocks, "status": L.STATUS.get(status, status),
                 "newton_mean_updates": mean_updates, "fallback_eq": st.fallback_eq,
                 "fallback_mx": st.fallback_mx, "judge_redo": st.judge_redo, "q_max": st.q_max,

@@ -317,6 +317,20 @@ int lelbm_set_warmstart(lelbm_t h, int stored);
  * Errors: E_INVAL (flops NULL), E_CUDA. */
 int lelbm_fma_peak(int fp64, double* flops);
 
+/* Checks of the mixed path's double-float building blocks on caller data (host
+ * arrays, copied in and out; the call allocates device memory and syncs the
+ * device).  The paper has no counterpart: they let a test hold the FP32-pipe
+ * arithmetic of LELBM_MIXED against FP64.
+ * lelbm_df_exp2: out[i] = 2^(w[i] 2^-54) by the table-driven double-float
+ *   exponential of the mixed path's EPR passes (Tang's method), as FP64;
+ *   w[i] in [-120, 200] 2^54.
+ * lelbm_df_dot: out[r] = sum_t k[r*n_terms + t] v[r*n_terms + t], each v split
+ *   into a double-float and accumulated in the double-float accumulator of the
+ *   streaming and correction passes, in index order, one row per thread.
+ * Errors: E_INVAL (sizes, NULL, w out of range), E_NOMEM, E_CUDA. */
+int lelbm_df_exp2(const long long* w, long long n, double* out);
+int lelbm_df_dot(const float* k, const double* v, long long n_terms, long long n_rows, double* out);
+
 /* Message of the last failure of h ("" if none; h may be NULL for create). */
 const char* lelbm_last_error(lelbm_t h);
 

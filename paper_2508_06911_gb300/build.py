@@ -16,6 +16,7 @@ UNITS = [
     ("lelbm_api.cu", "lelbm_api.o", []),
     ("lelbm_noalloc.cu", "lelbm_noalloc.o", []),
     ("lelbm_mlp.cu", "lelbm_mlp.o", []),
+    ("lelbm_check.cu", "lelbm_check.o", []),
     ("lelbm_cell.cu", "lelbm_cell_1d_fp64.o", ["-DLBM_D=1", "-DLBM_PREC=0"]),
     ("lelbm_cell.cu", "lelbm_cell_1d_mixed.o", ["-DLBM_D=1", "-DLBM_PREC=1"]),
     ("lelbm_cell.cu", "lelbm_cell_1d_fp32.o", ["-DLBM_D=1", "-DLBM_PREC=2"]),

@@ -20,23 +20,31 @@ template <>
 struct Dim<2> {
     static constexpr int NM = 11, NF = 10, NG = 6;
 };
+template <>
+struct Dim<3> {
+    static constexpr int NM = 17, NF = 19, NG = 10;
+};
 
-// Stored-moment positions, Eq. (IIB5).
+// Position of the pair (a <= b) among the D(D+1)/2 second-order entries, row by row.
+__device__ __forceinline__ constexpr int pair3(int a, int b) {
+    return a > b ? pair3(b, a) : a * 3 - a * (a - 1) / 2 + (b - a);
+}
+// Stored-moment positions, Eq. (IIB5): M0, M_a, M_ab (a <= b, row by row), MD_g, G0, G_g.
 template <int D>
 __device__ __forceinline__ constexpr int iM2(int a, int b) {
-    return D == 1 ? 2 : (a == 0 && b == 0 ? 3 : (a == 1 && b == 1 ? 5 : 4));
+    return D == 1 ? 2 : (D == 2 ? (a == 0 && b == 0 ? 3 : (a == 1 && b == 1 ? 5 : 4)) : 4 + pair3(a, b));
 }
 template <int D>
 __device__ __forceinline__ constexpr int iMD(int g) {
-    return D == 1 ? 3 : 6 + g;
+    return D == 1 ? 3 : (D == 2 ? 6 + g : 10 + g);
 }
 template <int D>
 __device__ __forceinline__ constexpr int iG0() {
-    return D == 1 ? 4 : 8;
+    return D == 1 ? 4 : (D == 2 ? 8 : 13);
 }
 template <int D>
 __device__ __forceinline__ constexpr int iG1(int g) {
-    return D == 1 ? 5 : 9 + g;
+    return D == 1 ? 5 : (D == 2 ? 9 + g : 14 + g);
 }
 
 // ---------------------------------------------------------------------------

@@ -88,7 +88,7 @@ EXPORTS = [
     "lelbm_get_stats", "lelbm_reset_stats", "lelbm_set_timing", "lelbm_last_error",
     "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
     "lelbm_mlp_size", "lelbm_mlp_init", "lelbm_mlp_loss_grad", "lelbm_mlp_train", "lelbm_step_record",
-    "lelbm_set_mlp", "lelbm_set_warmstart", "lelbm_fma_peak", "lelbm_mlp_infer",
+    "lelbm_set_mlp", "lelbm_set_warmstart", "lelbm_fma_peak", "lelbm_mlp_infer", "lelbm_df_exp2", "lelbm_df_dot",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -136,6 +136,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_reset_stats.argtypes = [_H]
         L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
         L.lelbm_fma_peak.argtypes = [ctypes.c_int, _DP]
+        L.lelbm_df_exp2.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong, _DP]
+        L.lelbm_df_dot.argtypes = [ctypes.POINTER(ctypes.c_float), _DP, ctypes.c_longlong, ctypes.c_longlong, _DP]
         L.lelbm_mlp_infer.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
                                       ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
         L.lelbm_last_error.argtypes = [_H]
@@ -282,6 +284,27 @@ def lelbm_fma_peak(fp64: bool) -> float:
     v = ctypes.c_double(0.0)
     _check(load().lelbm_fma_peak(int(fp64), ctypes.byref(v)), None)
     return v.value
+
+
+def lelbm_df_exp2(w: np.ndarray) -> np.ndarray:
+    """The mixed path's double-float 2^(w 2^-54) of int64 fixed-point exponents, as FP64."""
+    w = np.ascontiguousarray(w, dtype=np.int64)
+    out = np.empty(w.shape[0])
+    _check(load().lelbm_df_exp2(w.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), w.shape[0],
+                                out.ctypes.data_as(_DP)), None)
+    return out
+
+
+def lelbm_df_dot(k: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Row sums of k * v (k FP32, v FP64 split into double-floats) in the mixed path's
+    double-float accumulator; k and v are [rows, terms]."""
+    k = np.ascontiguousarray(k, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert k.shape == v.shape and k.ndim == 2
+    out = np.empty(k.shape[0])
+    _check(load().lelbm_df_dot(k.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), v.ctypes.data_as(_DP),
+                               k.shape[1], k.shape[0], out.ctypes.data_as(_DP)), None)
+    return out
 
 
 def lelbm_mlp_infer(dims: int, params: np.ndarray, X_dev: int, n: int, Y_dev: int, stream: int = 0) -> None:
