@@ -37,9 +37,9 @@ METRIC = "MLUPS and % HBM roofline, FP32+learned-EPR vs plain FP64, at matched L
 # Algorithmic FP64 work per stencil point and Newton pass: exponent (N FMA), residual (N FMA)
 # and the packed Jacobian (N(N+1)/2 FMA) for N constraints; moment streaming: one multiply and
 # one add per stored moment.  Exponentials are not counted.
-N_F = {1: 4, 2: 10}
-N_G = {1: 3, 2: 6}
-N_M = {1: 6, 2: 11}
+N_F = {1: 4, 2: 10, 3: 19}
+N_G = {1: 3, 2: 6, 3: 10}
+N_M = {1: 6, 2: 11, 3: 17}
 
 
 # DRAM bytes (read + write) per time step of the timed kernel, from one ncu capture of the
@@ -65,9 +65,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann2d", choices=["batch1d", "hotbox2d", "riemann2d", "cylinder2d"])
+    ap.add_argument("--workload", default="riemann2d",
+                    choices=["batch1d", "hotbox2d", "riemann2d", "cylinder2d", "hotbox3d", "riemann3d"])
     ap.add_argument("--n-batch", type=int, default=4096)
-    ap.add_argument("--n", type=int, default=4096, help="2D grid size")
+    ap.add_argument("--n", type=int, default=None, help="grid size (default 4096 in 2D, 128 in 3D)")
     ap.add_argument("--rt", type=float, default=0.5, help="hot-box temperature")
     ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
@@ -78,7 +79,12 @@ def parse():
                     "persistent batch kernel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.n is None:
+        a.n = 128 if a.workload.endswith("3d") else 4096
+    if a.workload.endswith("3d"):  # the 3D step is the FP64 path from Eq. (IID13)
+        a.precision, a.warmstart, a.no_compare = "fp64", "maxwell", True
+    return a
 
 
 def measured_peaks():
@@ -126,6 +132,14 @@ def make_workload(args, rank):
         fluid = int((w.solid == 0).sum())
         return w, {"workload": w.name, "dims": 2, "interior_cells": fluid, "solid_cells": int(w.solid.sum()),
                    "mach": 3.0, "boundary": "inflow x-, outflow elsewhere, slip-wall cylinder"}
+    if args.workload == "hotbox3d":
+        w = W.hot_box_3d(args.n, args.rt)
+        return w, {"workload": f"hotbox3d_{args.n}^3_RT{args.rt}", "dims": 3, "u": [10, 10, 10],
+                   "interior_cells": args.n ** 3}
+    if args.workload == "riemann3d":
+        w = W.riemann_3d(n=args.n, seed_index=6 + 1000 * rank)
+        return w, {"workload": f"riemann3d_{args.n}^3", "dims": 3, "interior_cells": args.n ** 3,
+                   "octants": "rho U[0.1,1.5], |u| <= 1.5, p U[0.03,1.5], RT_max/RT_min <= 8"}
     w = W.riemann_2d(n=args.n, seed_index=2 + 1000 * rank)
     return w, {"workload": f"riemann2d_{args.n}x{args.n}", "dims": 2, "interior_cells": args.n * args.n}
 
@@ -173,9 +187,13 @@ def clock_sampler_stop(state, gpu_index=0):
 
 
 def small_2d(args, n):
-    """An n x n (cylinder: 2n x n) instance of the 2D workload for the CPU oracle."""
+    """An n x n (cylinder: 2n x n; 3D: 8^3) instance of the workload for the CPU oracle."""
     from paper_2508_06911_gb300 import workloads as W
 
+    if args.workload == "hotbox3d":
+        return W.hot_box_3d(8, args.rt), 8 ** 3
+    if args.workload == "riemann3d":  # the same octant states on a periodic 8^3 box (no pad cells)
+        return W.riemann_3d(n=8, periodic=True), 8 ** 3
     if args.workload == "hotbox2d":
         return W.hot_box(2, n, args.rt), n * n
     if args.workload == "cylinder2d":
@@ -206,10 +224,10 @@ def _pool_init(workload, n_batch, n2d, rt):
 
 def _pool_task(b):
     """One time step of instance b (1D) or of the small 2D instance; returns interior cells."""
-    from parity_util import oracle_1d_instance, oracle_2d
+    from parity_util import oracle_1d_instance, oracle_2d, oracle_3d
 
     if isinstance(_POOL_W, tuple):
-        oracle_2d(_POOL_W[0], 1)
+        (oracle_3d if _POOL_W[0].__class__.__name__ == "Grid3D" else oracle_2d)(_POOL_W[0], 1)
         return _POOL_W[1]
     oracle_1d_instance(_POOL_W, b, 1)
     return int(_POOL_W.lengths[b])
@@ -335,7 +353,7 @@ def run_ours(args):
     # generator at 1024^2), the others the network trained on diverse 2D states
     wname = "warmstart_2d_config3.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
     wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", wname)
-    if args.warmstart == "learned" or not args.no_compare:
+    if D < 3 and (args.warmstart == "learned" or not args.no_compare):
         if os.path.exists(wpath):
             weights = np.load(wpath)
         else:  # no trained network shipped: train one on pairs recorded by the plain solver
@@ -349,7 +367,7 @@ def run_ours(args):
 
     def make(precision, start):
         kw = dict(stream=stream.cuda_stream, precision=prec[precision])
-        s_ = Solver.riemann1d(w, **kw) if D == 1 else Solver.grid2d(w, **kw)
+        s_ = Solver.riemann1d(w, **kw) if D == 1 else (Solver.grid2d(w, **kw) if D == 2 else Solver.grid3d(w, **kw))
         if start == "learned" and weights is not None:
             L.lelbm_set_mlp(s_.h, weights)
         if start == "stored":
@@ -479,7 +497,7 @@ def run_ours(args):
                                    if dram else None),
                 "peak_source": main_side["peak_source"],
                 "kernel": (f"batch_persistent_kernel<{prec_id}>" if persistent else
-                           f"cell_update_kernel<{D},{prec_id}>"),
+                           ("cell3d_kernel" if D == 3 else f"cell_update_kernel<{D},{prec_id}>")),
                 "kernel_ms": kern_ms, "steps_per_launch": steps_per_launch, **other_side,
                 "hbm": {"achieved_gbs": alg_bytes / sec / 1e9, "peak_gbs": hbm_peak,
                         "frac": alg_bytes / sec / 1e9 / hbm_peak,

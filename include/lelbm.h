@@ -21,9 +21,13 @@
  * the order of Eq. (IIB5):
  *   1D: M0, Mx, Mxx, MDx, G0, Gx                              (n_mom = 6)
  *   2D: M0, Mx, My, Mxx, Mxy, Myy, MDx, MDy, G0, Gx, Gy       (n_mom = 11)
+ *   3D: M0, Mx, My, Mz, Mxx, Mxy, Mxz, Myy, Myz, Mzz, MDx, MDy, MDz, G0, Gx,
+ *       Gy, Gz                                                  (n_mom = 17)
  * where MD_g = sum_i |c_i|^2 c_ig f_i.  Cells run over the PADDED grid:
  *   2D: index = iy * NX + ix with NX = nx + 2 pad (nx if x is periodic),
  *       NY = ny + 2 pad (ny if y is periodic);
+ *   3D: index = (iz * NY + iy) * NX + ix, NZ = nz + 2 pad (nz if z is
+ *       periodic);
  *   1D: the instances of a batch are concatenated, each as
  *       [pad | interior of lengths[b] cells | pad] (no pads when periodic).
  * Pad cells are overwritten by the boundary fill at the start of every step;
@@ -95,7 +99,7 @@ extern "C" {
 typedef struct lelbm* lelbm_t;
 
 typedef struct {
-    int dims;            /* 1 or 2                                                     */
+    int dims;            /* 1, 2 or 3                                                  */
     int nx, ny;          /* interior cells (ny = 1 in 1D)                              */
     int n_batch;         /* 1D: number of independent instances (<= 1: a single one)   */
     const int* lengths;  /* 1D batch, host [n_batch]: interior length of each instance */
@@ -123,8 +127,19 @@ typedef struct {
                             walls (Sec. III.B): a population whose path crosses a
                             solid face is specularly reflected, exactly traced in
                             1/64-cell units; a cloud-in-cell share that would fall
-                            on a solid cell is mirrored back across the wall.    */
+                            on a solid cell is mirrored back across the wall.  An
+                            outflow pad whose nearest interior cell is solid is
+                            solid too (the wall continues through the pads).    */
     void* stream;        /* cudaStream_t to run on; NULL: a stream owned by the handle  */
+    /* three dimensions (dims = 3; ignored below).  FP64 path with the Eq. (IID13)
+       start, fluid boundaries only (no solid cells, warm-start store or network,
+       batches).  One warp updates one cell; its velocity set is laid out as at
+       most 1024 runs of points along x (R_ac up to about 16, RT up to about 16
+       at the paper's n = 4).  A cell whose set does not fit is not streamed and
+       is counted as a Maxwellian fallback (lelbm_synchronize: E_EPR). */
+    int nz;              /* interior cells along z                                      */
+    int bc_z[2];         /* LELBM_BC_* for z-, z+                                       */
+    double inlet_uz;     /* z velocity of the inflow state (inlet[] holds rho, ux, uy, RT) */
 } lelbm_params;
 
 /* Per-handle counters accumulated by every step since the last reset. */
@@ -297,6 +312,16 @@ int lelbm_mlp_infer(int dims, const float* params, const float* X_dev, long long
 /* Use the network params (host, n_params floats) as warm start; NULL: the plain
  * Maxwellian start. */
 int lelbm_set_mlp(lelbm_t h, const float* params);
+
+/* Gate of the learned start: a cell whose normalised post-collision constraints
+ * (thermal units, Eq. IIB16-IIB18) all lie within `departure` of their
+ * equilibrium values (1, 0, delta_ab, 0 for fluons; 1, 0 for the phonons' free
+ * ones) starts from Eq. (IID13) instead of the network: near equilibrium
+ * Eq. (IID13) is closer to the solution than the network's fit.  A warp whose 32
+ * cells are all gated out skips the network.  0 (the default) uses the network
+ * for every cell.  Applies to the learned start of the cell-update path (not the
+ * persistent 1D batch).  Errors: E_INVAL (departure < 0 or not finite), E_CUDA. */
+int lelbm_set_mlp_gate(lelbm_t h, double departure);
 
 /* Stored warm start (Sec. II.D: the multipliers of each cell kept as the
  * precondition of its next step).  stored = 1 allocates a per-cell FP32 store of

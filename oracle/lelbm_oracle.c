@@ -689,6 +689,25 @@ static int land_axis(int i, int n, int pad, int periodic)
     return i;
 }
 
+/* Solid flag of padded cell (i, j) inside the array.  Interior cells carry the
+ * caller's flags.  reading (Sec. III.A with Sec. III.B): a pad cell of an outflow side
+ * whose nearest interior cell is solid is solid too -- the wall continues through the
+ * pads instead of a pad copying the empty state of a solid cell; inflow pads are
+ * never solid. */
+static int solid_flag(const orc_grid* g, int NX, int i, int j)
+{
+    int px = g->periodic[0] ? 0 : g->pad;
+    int py = (g->D == 1 || g->periodic[1]) ? 0 : g->pad;
+    int ny = g->D == 1 ? 1 : g->ny;
+    int inx = i >= px && i < px + g->nx, iny = j >= py && j < py + ny;
+    if (inx && iny) return g->solid[(long)j * NX + i] != 0;
+    if ((i < px && g->bc[0] == 1) || (i >= px + g->nx && g->bc[1] == 1)) return 0;
+    if (g->D >= 2 && ((j < py && g->bc[2] == 1) || (j >= py + ny && g->bc[3] == 1))) return 0;
+    int si = i < px ? px : (i >= px + g->nx ? px + g->nx - 1 : i);
+    int sj = j < py ? py : (j >= py + ny ? py + ny - 1 : j);
+    return g->solid[(long)sj * NX + si] != 0;
+}
+
 /* Sec. III.B: is padded cell (i, j) a solid cell?  Cells outside the array are
  * not (their populations are discarded later). */
 static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
@@ -697,7 +716,7 @@ static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
     if (g->periodic[0]) i = ((i % NX) + NX) % NX;
     if (g->D == 2 && g->periodic[1]) j = ((j % NY) + NY) % NY;
     if (i < 0 || i >= NX || j < 0 || j >= NY) return 0;
-    return g->solid[(long)j * NX + i] != 0;
+    return solid_flag(g, NX, i, j);
 }
 
 /* Sec. III.B, first step of the extended bounce-back: the path x -> x + c is
@@ -807,7 +826,7 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
     for (int iy = 0; iy < NY; iy++)
         for (int ix = 0; ix < NX; ix++) {
             long cell = ((long)iz * NY + iy) * NX + ix;
-            if (solid && solid[cell]) continue;
+            if (solid && solid_flag(g, NX, ix, iy)) continue;
             double M[ORC_MAXM];
             for (int m = 0; m < nm; m++) M[m] = W[m * ncell + cell];
             orc_collision co;

@@ -20,10 +20,11 @@ using namespace lbm;
 struct lelbm {
     lelbm_params p;
     int D = 1, nmom = 6;
-    int NX = 0, NY = 1;
+    int NX = 0, NY = 1, NZ = 1;
     long long ncell = 0;
     Model model{};
     Geometry geo{};
+    Geometry3 geo3{};
     // host copies of the layout
     std::vector<long long> inst_lo_h;
     std::vector<int> inst_n_h;
@@ -98,6 +99,7 @@ extern "C" void lelbm_default_params(lelbm_params* p) {
     p->dims = 1;
     p->nx = 1;
     p->ny = 1;
+    p->nz = 1;
     p->bc[0] = p->bc[1] = p->bc[2] = p->bc[3] = LELBM_BC_PERIODIC;
     p->inlet[0] = 1.0;
     p->inlet[3] = 1.0;
@@ -118,12 +120,18 @@ extern "C" void lelbm_default_params(lelbm_params* p) {
 
 static int validate(const lelbm_params* p) {
     if (!p) return fail(nullptr, LELBM_E_INVAL, "params is NULL");
-    if (p->dims != 1 && p->dims != 2) return fail(nullptr, LELBM_E_INVAL, "dims must be 1 or 2");
+    if (p->dims < 1 || p->dims > 3) return fail(nullptr, LELBM_E_INVAL, "dims must be 1, 2 or 3");
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LELBM_E_INVAL, "nx, ny must be >= 1");
     if (p->dims == 1 && p->ny != 1) return fail(nullptr, LELBM_E_INVAL, "ny must be 1 in 1D");
-    if (p->dims == 2 && p->n_batch > 1) return fail(nullptr, LELBM_E_INVAL, "batches are 1D only");
+    if (p->dims >= 2 && p->n_batch > 1) return fail(nullptr, LELBM_E_INVAL, "batches are 1D only");
+    if (p->dims == 3) {
+        if (p->nz < 1) return fail(nullptr, LELBM_E_INVAL, "nz must be >= 1 in 3D");
+        if (p->precision != LELBM_FP64) return fail(nullptr, LELBM_E_INVAL, "3D runs the FP64 path only");
+        if (p->solid) return fail(nullptr, LELBM_E_INVAL, "3D has no solid cells");
+        if (!std::isfinite(p->inlet_uz)) return fail(nullptr, LELBM_E_INVAL, "inlet_uz must be finite");
+    }
     for (int a = 0; a < p->dims; a++) {
-        const int l = p->bc[2 * a], r = p->bc[2 * a + 1];
+        const int l = a < 2 ? p->bc[2 * a] : p->bc_z[0], r = a < 2 ? p->bc[2 * a + 1] : p->bc_z[1];
         if (l < 0 || l > 2 || r < 0 || r > 2) return fail(nullptr, LELBM_E_INVAL, "bad bc kind");
         if ((l == LELBM_BC_PERIODIC) != (r == LELBM_BC_PERIODIC))
             return fail(nullptr, LELBM_E_INVAL, "periodic must be set on both sides of axis %d", a);
@@ -148,9 +156,12 @@ static int validate(const lelbm_params* p) {
             if (p->pads[b] < 1) return fail(nullptr, LELBM_E_INVAL, "pads[%d] < 1", b);
     if (p->dims == 2 && p->bc[0] == LELBM_BC_PERIODIC && p->bc[2] == LELBM_BC_PERIODIC && p->pad != 0)
         return fail(nullptr, LELBM_E_INVAL, "pad must be 0 on a fully periodic grid");
+    if (p->dims == 3 && p->bc[0] == LELBM_BC_PERIODIC && p->bc[2] == LELBM_BC_PERIODIC &&
+        p->bc_z[0] == LELBM_BC_PERIODIC && p->pad != 0)
+        return fail(nullptr, LELBM_E_INVAL, "pad must be 0 on a fully periodic grid");
     const double* in = p->inlet;
     bool any_in = false;
-    for (int s = 0; s < 2 * p->dims; s++) any_in = any_in || p->bc[s] == LELBM_BC_INFLOW;
+    for (int s = 0; s < 2 * p->dims; s++) any_in = any_in || (s < 4 ? p->bc[s] : p->bc_z[s - 4]) == LELBM_BC_INFLOW;
     if (any_in && !(in[0] > 0.0 && in[3] > 0.0)) return fail(nullptr, LELBM_E_INVAL, "inflow state needs rho, RT > 0");
     return LELBM_OK;
 }
@@ -263,7 +274,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     h->p.solid = nullptr;
     const int D = p->dims;
     h->D = D;
-    h->nmom = D == 1 ? 6 : 11;
+    h->nmom = D == 1 ? 6 : (D == 2 ? 11 : 17);
     cudaGetDevice(&h->device);
     if (p->stream) {
         h->stream = (cudaStream_t)p->stream;
@@ -352,6 +363,64 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
             delete h;
             return fail(nullptr, rc, "%s", e.c_str());
         }
+    } else if (D == 3) {
+        Geometry3& g3 = h->geo3;
+        g3.periodic[0] = p->bc[0] == LELBM_BC_PERIODIC;
+        g3.periodic[1] = p->bc[2] == LELBM_BC_PERIODIC;
+        g3.periodic[2] = p->bc_z[0] == LELBM_BC_PERIODIC;
+        const int px = g3.periodic[0] ? 0 : p->pad, py = g3.periodic[1] ? 0 : p->pad;
+        const int pz = g3.periodic[2] ? 0 : p->pad;
+        const int NX = p->nx + 2 * px, NY = p->ny + 2 * py, NZ = p->nz + 2 * pz;
+        h->NX = NX;
+        h->NY = NY;
+        h->NZ = NZ;
+        h->ncell = (long long)NX * NY * NZ;
+        g3.NX = NX;
+        g3.NY = NY;
+        g3.NZ = NZ;
+        g3.ncell = h->ncell;
+        g3.nx = p->nx;
+        g3.ny = p->ny;
+        g3.nz = p->nz;
+        g3.px = px;
+        g3.py = py;
+        g3.pz = pz;
+        g.nx = p->nx;
+        g.ny = p->ny;
+        g.n_inst = 1;
+        type.resize(h->ncell);
+        const int bcs[6] = {p->bc[0], p->bc[1], p->bc[2], p->bc[3], p->bc_z[0], p->bc_z[1]};
+        for (int iz = 0; iz < NZ; iz++)
+            for (int iy = 0; iy < NY; iy++)
+                for (int ix = 0; ix < NX; ix++) {
+                    const long long cell = ((long long)iz * NY + iy) * NX + ix;
+                    const bool inx = ix >= px && ix < px + p->nx;
+                    const bool iny = iy >= py && iy < py + p->ny;
+                    const bool inz = iz >= pz && iz < pz + p->nz;
+                    if (inx && iny && inz) {
+                        type[cell] = CELL_FLUID;
+                        continue;
+                    }
+                    // Sec. III.A: an inflow side wins at edges and corners
+                    bool inflow = false;
+                    if (ix < px && bcs[0] == LELBM_BC_INFLOW) inflow = true;
+                    if (ix >= px + p->nx && bcs[1] == LELBM_BC_INFLOW) inflow = true;
+                    if (iy < py && bcs[2] == LELBM_BC_INFLOW) inflow = true;
+                    if (iy >= py + p->ny && bcs[3] == LELBM_BC_INFLOW) inflow = true;
+                    if (iz < pz && bcs[4] == LELBM_BC_INFLOW) inflow = true;
+                    if (iz >= pz + p->nz && bcs[5] == LELBM_BC_INFLOW) inflow = true;
+                    type[cell] = inflow ? CELL_PAD_IN : CELL_PAD_OUT;
+                    pad_cell.push_back(cell);
+                    if (inflow) {
+                        pad_src.push_back(-1);
+                    } else {
+                        const int sx = std::min(std::max(ix, px), px + p->nx - 1);
+                        const int sy = std::min(std::max(iy, py), py + p->ny - 1);
+                        const int sz = std::min(std::max(iz, pz), pz + p->nz - 1);
+                        pad_src.push_back(((long long)sz * NY + sy) * NX + sx);
+                    }
+                }
+        g.pad = (g3.periodic[0] && g3.periodic[1] && g3.periodic[2]) ? 0 : p->pad;
     } else {
         const int px = g.periodic[0] ? 0 : p->pad;
         const int py = g.periodic[1] ? 0 : p->pad;
@@ -378,14 +447,23 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
                 if (ix >= px + p->nx && p->bc[1] == LELBM_BC_INFLOW) inflow = true;
                 if (iy < py && p->bc[2] == LELBM_BC_INFLOW) inflow = true;
                 if (iy >= py + p->ny && p->bc[3] == LELBM_BC_INFLOW) inflow = true;
-                type[cell] = inflow ? CELL_PAD_IN : CELL_PAD_OUT;
-                pad_cell.push_back(cell);
                 if (inflow) {
+                    type[cell] = CELL_PAD_IN;
+                    pad_cell.push_back(cell);
                     pad_src.push_back(-1);
                 } else {
                     const int sx = std::min(std::max(ix, px), px + p->nx - 1);
                     const int sy = std::min(std::max(iy, py), py + p->ny - 1);
-                    pad_src.push_back((long long)sy * NX + sx);
+                    const long long src = (long long)sy * NX + sx;
+                    if (p->solid && p->solid[src]) {
+                        // the wall continues through an outflow pad whose nearest interior
+                        // cell is solid (instead of the pad copying an empty state)
+                        type[cell] = CELL_SOLID;
+                        continue;
+                    }
+                    type[cell] = CELL_PAD_OUT;
+                    pad_cell.push_back(cell);
+                    pad_src.push_back(src);
                 }
             }
         // interior offset of every non-periodic axis (periodic axes have no pads)
@@ -425,7 +503,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         delete h;
         return fail(nullptr, rc, "%s", e.empty() ? "device set-up failed" : e.c_str());
     }
-    h->blocks = cell_update_blocks(D, p->precision, h->device);
+    h->blocks = D == 3 ? cell3d_blocks(h->device) : cell_update_blocks(D, p->precision, h->device);
     *out = h;
     return LELBM_OK;
 }
@@ -536,8 +614,13 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
     for (int s = 0; s < n; s++) {
         double* Min = h->M[h->cur];
         double* Mout = h->M[1 - h->cur];
-        launch_fill_pads(h->D, h->model, h->p.inlet, Min, h->ncell, h->d_pad_cell, h->d_pad_src, h->npad,
-                         h->stream);
+        if (h->D == 3) {
+            const double in5[5] = {h->p.inlet[0], h->p.inlet[1], h->p.inlet[2], h->p.inlet_uz, h->p.inlet[3]};
+            launch_fill_pads3(h->model, in5, Min, h->ncell, h->d_pad_cell, h->d_pad_src, h->npad, h->stream);
+        } else {
+            launch_fill_pads(h->D, h->model, h->p.inlet, Min, h->ncell, h->d_pad_cell, h->d_pad_src, h->npad,
+                             h->stream);
+        }
         CUDA_TRY(h, cudaMemsetAsync(Mout, 0, bytes, h->stream));
         CUDA_TRY(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
         std::pair<cudaEvent_t, cudaEvent_t> ev{};
@@ -555,8 +638,11 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
             mc.mlp_w = nullptr;
             mc.mlp_nrm = nullptr;
         }
-        launch_cell_update(mc, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks, h->p.precision,
-                           h->stream);
+        if (h->D == 3)
+            launch_cell3d(mc, h->geo3, Min, Mout, h->d_stats, h->d_work, h->blocks, h->stream);
+        else
+            launch_cell_update(mc, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks, h->p.precision,
+                               h->stream);
         if (h->timing) {
             CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
             h->ev_used.push_back(ev);
@@ -819,6 +905,7 @@ extern "C" int lelbm_autotune(lelbm_t h, int trial_steps, lelbm_tuning* best) {
 extern "C" int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev) {
     if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
     if (!x_dev || !y_dev) return fail(h, LELBM_E_INVAL, "NULL record buffer");
+    if (h->D == 3) return fail(h, LELBM_E_INVAL, "training pairs are recorded in 1D and 2D");
     h->model.rec_x = x_dev;
     h->model.rec_y = y_dev;
     const int rc = lelbm_step(h, 1);
@@ -829,6 +916,7 @@ extern "C" int lelbm_step_record(lelbm_t h, float* x_dev, float* y_dev) {
 
 extern "C" int lelbm_set_warmstart(lelbm_t h, int stored) {
     if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (h->D == 3 && stored) return fail(h, LELBM_E_INVAL, "3D has no warm-start store");
     if (stored) {
         if (!h->d_lam) {
             const size_t bytes = sizeof(float) * (size_t)(h->D == 1 ? 7 : 16) * (size_t)h->ncell;
@@ -843,6 +931,16 @@ extern "C" int lelbm_set_warmstart(lelbm_t h, int stored) {
         h->d_lam = nullptr;
         h->model.lam_store = nullptr;
     }
+    if (h->graph) cudaGraphExecDestroy(h->graph);  // the captured launch holds the old model
+    h->graph = nullptr;
+    return LELBM_OK;
+}
+
+extern "C" int lelbm_set_mlp_gate(lelbm_t h, double departure) {
+    if (!h) return fail(nullptr, LELBM_E_INVAL, "handle is NULL");
+    if (!(departure >= 0.0) || !std::isfinite(departure)) return fail(h, LELBM_E_INVAL, "departure must be >= 0");
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->model.mlp_gate = (float)departure;
     if (h->graph) cudaGraphExecDestroy(h->graph);  // the captured launch holds the old model
     h->graph = nullptr;
     return LELBM_OK;

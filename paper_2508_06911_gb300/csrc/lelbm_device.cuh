@@ -27,7 +27,7 @@ struct Dim<3> {
 
 // Position of the pair (a <= b) among the D(D+1)/2 second-order entries, row by row.
 __device__ __forceinline__ constexpr int pair3(int a, int b) {
-    return a > b ? pair3(b, a) : a * 3 - a * (a - 1) / 2 + (b - a);
+    return a > b ? b * 3 - b * (b - 1) / 2 + (a - b) : a * 3 - a * (a - 1) / 2 + (b - a);
 }
 // Stored-moment positions, Eq. (IIB5): M0, M_a, M_ab (a <= b, row by row), MD_g, G0, G_g.
 template <int D>

@@ -47,6 +47,8 @@ struct Model {
                                    // [NF + NG][ncell], or null
     const float* mlp_start;        // learned warm start of this step: per-cell corrections from
                                    // mlp_start_kernel, SoA [NF + NG][ncell] (NaN: none), or null
+    float mlp_gate;                // learned start only where the normalised constraints depart
+                                   // from equilibrium by at least this much (0: everywhere)
     // FP32 copies for the FP32 path (set by set_fp32_params)
     float K32, nu_s32, nu_b32, Pr32, n_conf32, r_min32, refine_div32;
     double rad2_32[5];  // squared refinement radii, FP32 arithmetic: (refine_rad / 2^L)^2
@@ -83,6 +85,16 @@ struct Geometry {
     const int* inst_n;           // 1D: interior length of each instance
     const uint8_t* wall_dist;    // 2D with solids: Chebyshev distance (cells) from each
                                  // cell to the nearest solid cell, capped at 255; else null
+};
+
+// Padded 3D grid: cell = (iz * NY + iy) * NX + ix; p* = pad layers of each axis (0 on a
+// periodic axis).
+struct Geometry3 {
+    int NX, NY, NZ;
+    long long ncell;
+    int nx, ny, nz;
+    int px, py, pz;
+    int periodic[3];
 };
 
 // Device-side counters (all 64-bit, updated with atomics).
@@ -128,6 +140,13 @@ void launch_mlp_infer(int D, const __nv_bfloat16* W, const float* nrm, const flo
                       cudaStream_t s);
 void launch_mlp_start(const Model& m, const Geometry& g, const uint8_t* type, const double* Min, float* out,
                       int device, cudaStream_t s);
+
+// 3D (lelbm_3d.cu): inlet = (rho, ux, uy, uz, RT).
+void launch_fill_pads3(const Model& m, const double inlet[5], double* M, long long ncell, const long long* pad_cell,
+                       const long long* pad_src, long long npad, cudaStream_t s);
+void launch_cell3d(const Model& m, const Geometry3& g, const double* Min, double* Mout, DevStats* st,
+                   unsigned long long* work, int blocks, cudaStream_t s);
+int cell3d_blocks(int device);
 
 // One object file per kernel variant (lelbm_cell.cu, lelbm_batch.cu).
 template <int D, int PREC>

@@ -172,8 +172,10 @@ void launch_eq_state(int D, double K, const uint8_t* type, const double* rho, co
     const int blocks = grid_for(ncell, 256);
     if (D == 1)
         eq_state_kernel<1><<<blocks, 256, 0, s>>>(K, type, rho, u, RT, M, ncell);
-    else
+    else if (D == 2)
         eq_state_kernel<2><<<blocks, 256, 0, s>>>(K, type, rho, u, RT, M, ncell);
+    else
+        eq_state_kernel<3><<<blocks, 256, 0, s>>>(K, type, rho, u, RT, M, ncell);
 }
 
 void launch_macros(int D, double K, const uint8_t* type, const double* M, double* rho, double* u, double* RT,
@@ -181,8 +183,10 @@ void launch_macros(int D, double K, const uint8_t* type, const double* M, double
     const int blocks = grid_for(ncell, 256);
     if (D == 1)
         macros_kernel<1><<<blocks, 256, 0, s>>>(K, type, M, rho, u, RT, ncell);
-    else
+    else if (D == 2)
         macros_kernel<2><<<blocks, 256, 0, s>>>(K, type, M, rho, u, RT, ncell);
+    else
+        macros_kernel<3><<<blocks, 256, 0, s>>>(K, type, M, rho, u, RT, ncell);
 }
 
 // ---------------------------------------------------------------------------
@@ -192,8 +196,28 @@ void launch_macros(int D, double K, const uint8_t* type, const double* M, double
 // memory, FP32 accumulation, SiLU in FP32) runs on the tensor cores for the warp's 32
 // cells at once.
 // out[k][cell] (SoA, NOUT rows) receives the predicted correction of Eq. (IID13); NaN
-// where the cell gets no learned start (solid, non-physical).
+// where the cell gets no learned start (solid, non-physical, or -- with a gate -- close
+// enough to equilibrium that Eq. (IID13) is the better start).  A warp whose 32 cells all
+// take Eq. (IID13) skips the network.
 // ---------------------------------------------------------------------------
+// Largest departure of the normalised post-collision constraints (thermal units) from
+// those of the equilibrium (Eq. IIB16-IIB18 with omega = 1): 1, 0, delta_ab, 0 for the
+// fluons and 1, 0, delta_ab for the phonons.
+template <int D>
+__device__ __forceinline__ float constraint_departure(const CellState<D>& c, bool has_g) {
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < Dim<D>::NF; k++) {
+        const bool diag = D == 1 ? k == 2 : (k == 3 || k == 5);  // M_aa / (rho RT)
+        d = fmaxf(d, fabsf(c.cf32[k] - ((k == 0 || diag) ? 1.f : 0.f)));
+    }
+    if (has_g) {
+#pragma unroll
+        for (int k = 0; k < 1 + D; k++) d = fmaxf(d, fabsf(c.cg32[k] - (k == 0 ? 1.f : 0.f)));
+    }
+    return d;
+}
+
 template <int D>
 __global__ void __launch_bounds__(128) mlp_start_kernel(const __grid_constant__ Model m,
                                                         const __grid_constant__ Geometry g,
@@ -219,11 +243,12 @@ __global__ void __launch_bounds__(128) mlp_start_kernel(const __grid_constant__ 
             ok = c.ok;
             if (ok) st.init32(c, m);
         }
+        if (ok && m.mlp_gate > 0.f) ok = constraint_departure<D>(c, m.K > 0.0) >= m.mlp_gate;
         float xin[MlpDims<D>::NIN], dl[MlpDims<D>::NOUT];
 #pragma unroll
         for (int k = 0; k < MlpDims<D>::NIN; k++) xin[k] = 0.f;
         if (ok) mlp_features<D, true>(c, st, xin);
-        warp_mlp<D, true>(s_mlp, xin, ok, dl);
+        if (__any_sync(0xffffffffu, ok)) warp_mlp<D, true>(s_mlp, xin, ok, dl);  // warp-uniform
         if (cell < g.ncell) {
 #pragma unroll
             for (int k = 0; k < MlpDims<D>::NOUT; k++) out[(long long)k * g.ncell + cell] = ok ? dl[k] : __int_as_float(0x7fc00000);

@@ -48,6 +48,9 @@ class lelbm_params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("solid", ctypes.POINTER(ctypes.c_ubyte)),
         ("stream", ctypes.c_void_p),
+        ("nz", ctypes.c_int),
+        ("bc_z", ctypes.c_int * 2),
+        ("inlet_uz", ctypes.c_double),
     ]
 
 
@@ -89,6 +92,7 @@ EXPORTS = [
     "lelbm_step_noalloc", "lelbm_set_steps", "lelbm_run_batch", "lelbm_autotune", "lelbm_set_tuning",
     "lelbm_mlp_size", "lelbm_mlp_init", "lelbm_mlp_loss_grad", "lelbm_mlp_train", "lelbm_step_record",
     "lelbm_set_mlp", "lelbm_set_warmstart", "lelbm_fma_peak", "lelbm_mlp_infer", "lelbm_df_exp2", "lelbm_df_dot",
+    "lelbm_set_mlp_gate",
 ]
 LELBM_NOALLOC_MAX_INSTANCES = 16384
 
@@ -136,6 +140,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.lelbm_reset_stats.argtypes = [_H]
         L.lelbm_set_timing.argtypes = [_H, ctypes.c_int]
         L.lelbm_fma_peak.argtypes = [ctypes.c_int, _DP]
+        L.lelbm_set_mlp_gate.argtypes = [_H, ctypes.c_double]
         L.lelbm_df_exp2.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong, _DP]
         L.lelbm_df_dot.argtypes = [ctypes.POINTER(ctypes.c_float), _DP, ctypes.c_longlong, ctypes.c_longlong, _DP]
         L.lelbm_mlp_infer.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p,
@@ -284,6 +289,11 @@ def lelbm_fma_peak(fp64: bool) -> float:
     v = ctypes.c_double(0.0)
     _check(load().lelbm_fma_peak(int(fp64), ctypes.byref(v)), None)
     return v.value
+
+
+def lelbm_set_mlp_gate(h, departure: float) -> None:
+    """Learned start only for cells whose constraints depart from equilibrium by >= departure."""
+    _check(load().lelbm_set_mlp_gate(h, float(departure)), h)
 
 
 def lelbm_df_exp2(w: np.ndarray) -> np.ndarray:

@@ -4,7 +4,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import lelbm as L
-from .workloads import Grid2D, Riemann1D
+from .workloads import Grid2D, Grid3D, Riemann1D
 
 
 class Solver:
@@ -12,12 +12,21 @@ class Solver:
 
     def __init__(self, dims: int, nx: int, ny: int = 1, *, K: float, nu: float, Pr: float = 0.71,
                  nu_bulk: float = -1.0, bc=(2, 2, 2, 2), pad: int = 0, lengths=None, pads=None, solid=None,
-                 inlet=(1.0, 0.0, 0.0, 1.0), limiter: int = 1, stream: int | None = None, **numerics):
+                 inlet=(1.0, 0.0, 0.0, 1.0), limiter: int = 1, stream: int | None = None, nz: int = 1,
+                 **numerics):
+        """bc: per side (x-, x+, y-, y+[, z-, z+]); inlet: (rho, ux, uy, RT) or, in 3D,
+        (rho, ux, uy, uz, RT)."""
         p = L.lelbm_default_params()
-        p.dims, p.nx, p.ny = dims, nx, ny
+        p.dims, p.nx, p.ny, p.nz = dims, nx, ny, nz
         for i in range(4):
             p.bc[i] = bc[i]
-            p.inlet[i] = inlet[i]
+        if len(bc) == 6:
+            p.bc_z[0], p.bc_z[1] = bc[4], bc[5]
+        if len(inlet) == 5:
+            p.inlet[0], p.inlet[1], p.inlet[2], p.inlet_uz, p.inlet[3] = inlet
+        else:
+            for i in range(4):
+                p.inlet[i] = inlet[i]
         p.pad = pad
         p.K, p.nu_shear, p.nu_bulk, p.prandtl, p.limiter = K, nu, nu_bulk, Pr, limiter
         for k, v in numerics.items():
@@ -41,6 +50,15 @@ class Solver:
         rho, u, RT, solid = w.padded()
         s = cls(2, w.nx, w.ny, K=w.K, nu=w.nu, Pr=w.Pr, bc=w.bc, pad=w.pad if w.bc[0] != 2 or w.bc[2] != 2 else 0,
                 solid=solid if w.solid is not None else None, inlet=w.inlet, stream=stream, **numerics)
+        s.set_state(rho, u, RT)
+        return s
+
+    @classmethod
+    def grid3d(cls, w: Grid3D, stream=None, **numerics) -> "Solver":
+        rho, u, RT = w.padded()
+        periodic = all(b == 2 for b in w.bc)
+        s = cls(3, w.nx, w.ny, nz=w.nz, K=w.K, nu=w.nu, Pr=w.Pr, bc=w.bc, pad=0 if periodic else w.pad,
+                inlet=w.inlet, stream=stream, **numerics)
         s.set_state(rho, u, RT)
         return s
 

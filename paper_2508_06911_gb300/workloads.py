@@ -283,6 +283,77 @@ def hot_box(dims: int, n: int, RT: float, u: float = 10.0) -> Grid2D | Riemann1D
                   name=f"hotbox2d_{n}_RT{RT}")
 
 
+@dataclass
+class Grid3D:
+    """A 3D problem: interior fields (nz, ny, nx) in lattice units and boundary kinds."""
+    nx: int
+    ny: int
+    nz: int
+    rho: np.ndarray
+    u: np.ndarray  # (3, nz, ny, nx)
+    RT: np.ndarray
+    bc: tuple      # x-, x+, y-, y+, z-, z+ : 0 outflow, 1 inflow, 2 periodic
+    pad: int
+    K: float
+    nu: float
+    Pr: float
+    steps: int
+    inlet: tuple = (1.0, 0.0, 0.0, 0.0, 1.0)
+    name: str = ""
+
+    def padded(self):
+        """Padded (rho, u[3], RT) in the layout of the C ABI: cell = (iz NY + iy) NX + ix."""
+        px = 0 if self.bc[0] == 2 else self.pad
+        py = 0 if self.bc[2] == 2 else self.pad
+        pz = 0 if self.bc[4] == 2 else self.pad
+        NZ, NY, NX = self.nz + 2 * pz, self.ny + 2 * py, self.nx + 2 * px
+        rho = np.zeros((NZ, NY, NX))
+        u = np.zeros((3, NZ, NY, NX))
+        RT = np.zeros((NZ, NY, NX))
+        sl = (slice(pz, pz + self.nz), slice(py, py + self.ny), slice(px, px + self.nx))
+        rho[sl] = self.rho
+        u[(slice(None),) + sl] = self.u
+        RT[sl] = self.RT
+        return rho.reshape(-1), u.reshape(3, -1), RT.reshape(-1)
+
+
+def hot_box_3d(n: int, RT: float, u: float = 10.0) -> Grid3D:
+    """Sec. IV.E in three dimensions: periodic n^3 box, rho = 1, u = (10, 10, 10), temperature RT."""
+    return Grid3D(nx=n, ny=n, nz=n, rho=np.ones((n, n, n)), u=np.full((3, n, n, n), u), RT=np.full((n, n, n), RT),
+                  bc=(2,) * 6, pad=0, K=internal_dof(GAMMA, 3), nu=1e-3, Pr=0.71, steps=1,
+                  name=f"hotbox3d_{n}_RT{RT}")
+
+
+def riemann_3d(n: int = 128, seed_index: int = 6, steps: int = 200, nu: float = 1e-3, max_ratio: float = 8.0,
+               RT_floor: float = 0.25, periodic: bool = False) -> Grid3D:
+    """Seeded eight-octant Riemann problem, the 3D analogue of riemann_2d: per octant
+    rho ~ U[0.1, 1.5], velocity uniform in the ball of radius 1.5, p ~ U[0.03, 1.5]; draws with
+    RT_max / RT_min above max_ratio are redrawn (3D velocity sets grow as (4 sqrt RT)^3);
+    acoustic scaling puts the coldest octant at lattice RT = RT_floor; outflow on every side
+    (periodic: wrap-around instead, no pads)."""
+    g = rng(seed_index)
+    while True:
+        rho_q = g.uniform(0.1, 1.5, 8)
+        d = g.standard_normal((8, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        vel = d * (1.5 * g.random(8) ** (1.0 / 3.0))[:, None]
+        p_q = g.uniform(0.03, 1.5, 8)
+        T = p_q / rho_q
+        if T.max() / T.min() <= max_ratio:
+            break
+    s = math.sqrt(RT_floor / T.min())
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    q = (X >= 0.5).astype(int) + 2 * (Y >= 0.5).astype(int) + 4 * (Z >= 0.5).astype(int)
+    vel = vel * s
+    T = T * s * s
+    umax = float(np.linalg.norm(vel, axis=1).max())
+    pad = 0 if periodic else pad_for(umax * 1.3, float(T.max()) * 2.0)
+    return Grid3D(nx=n, ny=n, nz=n, rho=rho_q[q], u=np.stack([vel[q, 0], vel[q, 1], vel[q, 2]]), RT=T[q],
+                  bc=(2 if periodic else 0,) * 6, pad=pad, K=internal_dof(GAMMA, 3), nu=nu, Pr=0.71, steps=steps,
+                  name=f"riemann3d_{n}")
+
+
 def random_smooth_2d(nx: int, ny: int, seed_index: int, RT_lo: float, RT_hi: float, umag: float,
                      periodic: bool = True, pad: int = 0) -> Grid2D:
     """Random smooth fields for parity tests (a few Fourier modes)."""
@@ -329,3 +400,25 @@ def cylinder_2d(nx: int = 2048, ny: int = 1024, diameter: int = 128, mach: float
     return Grid2D(nx=nx, ny=ny, rho=rho_f, u=u, RT=RT_f, bc=(1, 0, 0, 0), pad=pad, K=internal_dof(GAMMA, 2),
                   nu=0.0, Pr=0.71, steps=steps, inlet=(rho, u_lat, 0.0, RT_lattice), solid=solid,
                   name=f"cylinder2d_{nx}x{ny}_D{diameter}_Ma{mach:g}")
+
+
+def oblique_2d(mach: float, theta_deg: float, nx: int = 512, ny: int = 320, RT: float = 0.5, rho: float = 1.0,
+               nu: float = 1e-3, lead: float = 0.1, flow_throughs: float = 2.5) -> Grid2D:
+    """Oblique shock (Sec. V.F, Fig. VIF1) in the frame of the deflecting slip wall: a flat
+    wall along the bottom of the domain from x = lead * nx on (solid interior row 0), and the
+    supersonic stream (rho, RT, Mach number mach) arriving at the angle theta towards it, so
+    the wall turns the flow by theta.  Inflow of the stream at x-, y- and y+ (the pads
+    below the wall's leading part act as the non-reflective lower boundary), outflow at x+;
+    impulsive start; run for flow_throughs passages of the domain length."""
+    c_s = math.sqrt(GAMMA * RT)
+    V = mach * c_s
+    th = math.radians(theta_deg)
+    ux, uy = V * math.cos(th), -V * math.sin(th)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[0, int(round(lead * nx)):] = 1
+    pad = pad_for(V * 1.3, RT * 1.5)
+    steps = int(math.ceil(flow_throughs * nx / ux))
+    return Grid2D(nx=nx, ny=ny, rho=np.full((ny, nx), rho), u=np.stack([np.full((ny, nx), ux), np.full((ny, nx), uy)]),
+                  RT=np.full((ny, nx), RT), bc=(1, 0, 1, 1), pad=pad, K=internal_dof(GAMMA, 2), nu=nu, Pr=0.71,
+                  steps=steps, inlet=(rho, ux, uy, RT), solid=solid,
+                  name=f"oblique2d_Ma{mach:g}_theta{theta_deg:g}_{nx}x{ny}")

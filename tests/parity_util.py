@@ -31,6 +31,16 @@ def oracle_2d(w: Grid2D, nsteps: int, stats=None, **kw):
     return O.run(g, p, M, nsteps, stats)
 
 
+def oracle_3d(w, nsteps: int, stats=None, **kw):
+    """Oracle padded state [nmom, NZ*NY*NX] of a Grid3D after nsteps."""
+    periodic = tuple(w.bc[2 * a] == 2 for a in range(3))
+    g = O.grid(3, w.nx, w.ny, nz=w.nz, periodic=periodic, pad=0 if all(periodic) else w.pad,
+               bc=tuple(1 if b == 1 else 0 for b in w.bc), inlet=w.inlet)
+    p = oracle_params(3, w.K, w.nu, w.Pr, **kw)
+    M = O.state_from_primitives(g, p, w.rho, w.u, w.RT)
+    return O.run(g, p, M, nsteps, stats)
+
+
 def interior_mask_2d(w: Grid2D):
     px = 0 if w.bc[0] == 2 else w.pad
     py = 0 if w.bc[2] == 2 else w.pad

@@ -285,3 +285,32 @@ def test_symmetric_flow_around_block_stays_symmetric():
     sign = np.array([1, -1, 1, 1, -1, 1, -1, 1, 1, -1, 1.0])[:, None, None]
     scale = np.abs(A).max(axis=(1, 2), keepdims=True)
     assert (np.abs(A - sign * B) / scale).max() < 1e-12
+
+
+def test_wall_through_outflow_pads_keeps_parallel_stream_uniform():
+    """A flat slip wall along the bottom that runs out through the outflow side: the outflow
+    pads whose nearest interior cell is solid are solid too, so a uniform stream parallel to
+    the wall, fed by inflow pads of the same state, stays uniform (the flat-wall invariant of
+    Sec. III.B).  A pad copying the empty state of a wall cell instead breaks it at once."""
+    nx, ny, pad = 24, 10, 5
+    K = 3.0
+    rho0, ux, RT0 = 1.0, 0.8, 0.6
+    NX, NY = nx + 2 * pad, ny + 2 * pad
+    solid = np.zeros((NY, NX), dtype=np.uint8)
+    solid[pad, pad:pad + nx] = 1  # interior row 0 along the whole length
+    g = O.grid(2, nx, ny, pad=pad, bc=(1, 0, 1, 1), inlet=(rho0, ux, 0.0, RT0), solid=solid.reshape(-1))
+    p = O.params(2, K, nu_s=1e-3)
+    rho = np.full((ny, nx), rho0)
+    u = np.stack([np.full((ny, nx), ux), np.zeros((ny, nx))])
+    T = np.full((ny, nx), RT0)
+    rho[0] = 0.0  # the wall row: never read
+    M0 = O.state_from_primitives(g, p, np.where(rho > 0, rho, rho0), u, T)
+    st = O.Stats()
+    M = O.run(g, p, M0, 3, st)
+    fluid = np.zeros((NY, NX), dtype=bool)
+    fluid[pad + 1:pad + ny, pad:pad + nx] = True
+    ref = M0[:, fluid.reshape(-1)]
+    got = M[:, fluid.reshape(-1)]
+    assert np.all(np.isfinite(M))
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+    assert st.fallback_mx == 0 and st.wall_hits > 0
