@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default persistent launch shape")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "maxwell", "stored"],
                     help="EPR Newton start of the timed path: the trained MLP or Eq. (IID13)")
+    ap.add_argument("--mlp-gate", type=float, default=1e-3,
+                    help="timed path: learned start only for cells whose constraints depart from equilibrium "
+                         "by at least this much (0: every cell); the FP64 comparison runs use the network everywhere")
     ap.add_argument("--per-step", action="store_true", help="1D batch: one launch per step instead of the "
                     "persistent batch kernel")
     ap.add_argument("--no-e2e", action="store_true")
@@ -370,6 +373,8 @@ def run_ours(args):
         s_ = Solver.riemann1d(w, **kw) if D == 1 else (Solver.grid2d(w, **kw) if D == 2 else Solver.grid3d(w, **kw))
         if start == "learned" and weights is not None:
             L.lelbm_set_mlp(s_.h, weights)
+            if precision == args.precision and precision != "fp64":
+                L.lelbm_set_mlp_gate(s_.h, args.mlp_gate)
         if start == "stored":
             s_.set_warmstart(True)
         return s_
@@ -541,6 +546,7 @@ def run_ours(args):
                 "config": desc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
                 "speedup_vs_fp64": (value / compare["value"]) if (compare and args.precision != "fp64") else None,
                 "warmstart": args.warmstart if (args.warmstart != "learned" or weights is not None) else "maxwell",
+                "mlp_gate": args.mlp_gate if (args.warmstart == "learned" and weights is not None) else None,
                 "warm_starts": warm_starts, "fp32_path": fp32_path, "points_fp32": st.points_32,
                 "points_df_corr": st.points_df_corr, "points_df_stream": st.points_df,
                 "fma_peaks_tflops": {"fp32": fp32_peak / 1e12, "fp64": fp64_peak / 1e12},

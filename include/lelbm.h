@@ -140,6 +140,13 @@ typedef struct {
     int nz;              /* interior cells along z                                      */
     int bc_z[2];         /* LELBM_BC_* for z-, z+                                       */
     double inlet_uz;     /* z velocity of the inflow state (inlet[] holds rho, ux, uy, RT) */
+    int deterministic;   /* 1: moment streaming as a gather in a fixed order instead of
+                            FP64 atomic scatters, so repeated runs give the same bits
+                            whatever else the GPU runs (2D, LELBM_FP64, no solid cells;
+                            E_INVAL otherwise).  The cell kernel keeps each cell's
+                            multipliers ((N_f + N_g) doubles per cell, 128 B in 2D) for
+                            a gather kernel in which every target cell sums what the
+                            cells within reach send it (Eq. IIE3).                    */
 } lelbm_params;
 
 /* Per-handle counters accumulated by every step since the last reset. */

@@ -18,6 +18,7 @@ UNITS = [
     ("lelbm_mlp.cu", "lelbm_mlp.o", []),
     ("lelbm_check.cu", "lelbm_check.o", []),
     ("lelbm_3d.cu", "lelbm_3d.o", []),
+    ("lelbm_gather.cu", "lelbm_gather.o", []),
     ("lelbm_cell.cu", "lelbm_cell_1d_fp64.o", ["-DLBM_D=1", "-DLBM_PREC=0"]),
     ("lelbm_cell.cu", "lelbm_cell_1d_mixed.o", ["-DLBM_D=1", "-DLBM_PREC=1"]),
     ("lelbm_cell.cu", "lelbm_cell_1d_fp32.o", ["-DLBM_D=1", "-DLBM_PREC=2"]),

@@ -52,6 +52,8 @@ struct lelbm {
     float* d_mlp_nrm = nullptr;        // and normalisation
     float* d_lam = nullptr;            // stored warm start (lelbm_set_warmstart)
     float* d_mlp_start = nullptr;      // learned start of the current step (cell-update path)
+    double* d_det_lam = nullptr;       // deterministic streaming: per-cell multipliers
+    int* d_det_halo = nullptr;         // and the reach of the step's velocity sets
     cudaGraphExec_t graph = nullptr;  // captured lelbm_run_batch launch
     int graph_n = -1, graph_cur = -1;
     bool graph_budgets = false;
@@ -124,6 +126,8 @@ static int validate(const lelbm_params* p) {
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LELBM_E_INVAL, "nx, ny must be >= 1");
     if (p->dims == 1 && p->ny != 1) return fail(nullptr, LELBM_E_INVAL, "ny must be 1 in 1D");
     if (p->dims >= 2 && p->n_batch > 1) return fail(nullptr, LELBM_E_INVAL, "batches are 1D only");
+    if (p->deterministic && (p->dims != 2 || p->precision != LELBM_FP64 || p->solid))
+        return fail(nullptr, LELBM_E_INVAL, "deterministic streaming needs a 2D FP64 grid without solid cells");
     if (p->dims == 3) {
         if (p->nz < 1) return fail(nullptr, LELBM_E_INVAL, "nz must be >= 1 in 3D");
         if (p->precision != LELBM_FP64) return fail(nullptr, LELBM_E_INVAL, "3D runs the FP64 path only");
@@ -196,6 +200,8 @@ static void free_all(lelbm* h) {
     cudaFree(h->d_mlp_nrm);
     cudaFree(h->d_lam);
     cudaFree(h->d_mlp_start);
+    cudaFree(h->d_det_lam);
+    cudaFree(h->d_det_halo);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -496,6 +502,11 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     if (!rc && cudaMalloc((void**)&h->d_work, sizeof(unsigned long long)) != cudaSuccess) rc = LELBM_E_NOMEM;
     if (!rc && (cudaMemset(h->M[0], 0, bytes) != cudaSuccess || cudaMemset(h->M[1], 0, bytes) != cudaSuccess))
         rc = LELBM_E_CUDA;
+    if (!rc && p->deterministic) {
+        if (cudaMalloc((void**)&h->d_det_lam, sizeof(double) * 16 * (size_t)h->ncell) != cudaSuccess ||
+            cudaMalloc((void**)&h->d_det_halo, sizeof(int)) != cudaSuccess)
+            rc = LELBM_E_NOMEM;
+    }
     if (!rc) rc = reset_stats_dev(h);
     if (rc) {
         std::string e = h->err;
@@ -638,11 +649,17 @@ extern "C" int lelbm_step(lelbm_t h, int n) {
             mc.mlp_w = nullptr;
             mc.mlp_nrm = nullptr;
         }
+        if (h->d_det_lam) {
+            mc.det_lam = h->d_det_lam;
+            mc.det_halo = h->d_det_halo;
+            CUDA_TRY(h, cudaMemsetAsync(h->d_det_halo, 0, sizeof(int), h->stream));
+        }
         if (h->D == 3)
             launch_cell3d(mc, h->geo3, Min, Mout, h->d_stats, h->d_work, h->blocks, h->stream);
         else
             launch_cell_update(mc, h->geo, h->d_type, Min, Mout, h->d_stats, h->d_work, h->blocks, h->p.precision,
                                h->stream);
+        if (h->d_det_lam) launch_gather2d(mc, h->geo, Min, Mout, h->d_stats, h->stream);
         if (h->timing) {
             CUDA_TRY(h, cudaEventRecord(ev.second, h->stream));
             h->ev_used.push_back(ev);

@@ -60,24 +60,32 @@ struct CellState {
     bool ok;
 };
 
+// Eq. (IIB6), with the operation order of a plain loop and one rounding each: rho, u, RT
+// and whether they describe a gas (rho > 0, RT > 0, finite).  usq receives |u|^2.
+template <int D>
+__device__ __forceinline__ bool cell_macros(const double* M, double K, double& rho, double* u, double& RT,
+                                            double& usq) {
+    rho = M[0];
+    usq = 0.0;
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        u[a] = __ddiv_rn(M[1 + a], rho);
+        usq = __dadd_rn(usq, __dmul_rn(u[a], u[a]));
+        tr = __dadd_rn(tr, M[iM2<D>(a, a)]);
+    }
+    RT = __ddiv_rn(__dsub_rn(__ddiv_rn(__dadd_rn(tr, M[iG0<D>()]), rho), usq), __dadd_rn((double)D, K));
+    return rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
+}
+
 template <int D>
 __device__ __forceinline__ void collide(const double* M, const Model& m, CellState<D>& c) {
     constexpr int NF = Dim<D>::NF, NG = Dim<D>::NG;
     const double K = m.K;
-    // Eq. (IIB6), with the operation order of a plain loop and one rounding each.
-    const double rho = M[0];
-    double usq = 0.0, tr = 0.0;
-#pragma unroll
-    for (int a = 0; a < D; a++) {
-        c.u[a] = __ddiv_rn(M[1 + a], rho);
-        usq = __dadd_rn(usq, __dmul_rn(c.u[a], c.u[a]));
-        tr = __dadd_rn(tr, M[iM2<D>(a, a)]);
-    }
-    const double RT = __ddiv_rn(__dsub_rn(__ddiv_rn(__dadd_rn(tr, M[iG0<D>()]), rho), usq),
-                                __dadd_rn((double)D, K));
+    double rho, RT, usq;
+    c.ok = cell_macros<D>(M, K, rho, c.u, RT, usq);
     c.rho = rho;
     c.RT = RT;
-    c.ok = rho > 0.0 && RT > 0.0 && isfinite(rho) && isfinite(RT);
     if (!c.ok) return;
     c.sig = sqrt(RT);
     c.inv_sig = 1.0 / c.sig;

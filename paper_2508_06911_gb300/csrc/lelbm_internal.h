@@ -49,6 +49,11 @@ struct Model {
                                    // mlp_start_kernel, SoA [NF + NG][ncell] (NaN: none), or null
     float mlp_gate;                // learned start only where the normalised constraints depart
                                    // from equilibrium by at least this much (0: everywhere)
+    double* det_lam;               // deterministic streaming (FP64 2D): the cell kernel writes
+                                   // each cell's final multipliers here, SoA [NF + NG][ncell],
+                                   // instead of scattering; null: scatter with atomics
+    int* det_halo;                 // with det_lam: max over cells of the reach of the velocity
+                                   // set (cells), for the gather's window
     // FP32 copies for the FP32 path (set by set_fp32_params)
     float K32, nu_s32, nu_b32, Pr32, n_conf32, r_min32, refine_div32;
     double rad2_32[5];  // squared refinement radii, FP32 arithmetic: (refine_rad / 2^L)^2
@@ -147,6 +152,11 @@ void launch_fill_pads3(const Model& m, const double inlet[5], double* M, long lo
 void launch_cell3d(const Model& m, const Geometry3& g, const double* Min, double* Mout, DevStats* st,
                    unsigned long long* work, int blocks, cudaStream_t s);
 int cell3d_blocks(int device);
+// Deterministic moment streaming (lelbm_gather.cu): every target cell of a padded 2D grid
+// sums, in a fixed order, what the cells within reach send it, from the multipliers the
+// FP64 cell kernel left in m.det_lam.
+void launch_gather2d(const Model& m, const Geometry& g, const double* Min, double* Mout, DevStats* st,
+                     cudaStream_t s);
 
 // One object file per kernel variant (lelbm_cell.cu, lelbm_batch.cu).
 template <int D, int PREC>

@@ -195,8 +195,8 @@ void launch_macros(int D, double K, const uint8_t* type, const double* M, double
 // in FP32 alone gives the features, and the network (2 x 64 SiLU, BF16 weights staged in shared
 // memory, FP32 accumulation, SiLU in FP32) runs on the tensor cores for the warp's 32
 // cells at once.
-// out[k][cell] (SoA, NOUT rows) receives the predicted correction of Eq. (IID13); NaN
-// where the cell gets no learned start (solid, non-physical, or -- with a gate -- close
+// out[k][cell] (SoA, NOUT rows) receives the predicted correction of Eq. (IID13); a NaN
+// in the first row (the others left unwritten) where the cell gets no learned start (solid, non-physical, or -- with a gate -- close
 // enough to equilibrium that Eq. (IID13) is the better start).  A warp whose 32 cells all
 // take Eq. (IID13) skips the network.
 // ---------------------------------------------------------------------------
@@ -250,8 +250,12 @@ __global__ void __launch_bounds__(128) mlp_start_kernel(const __grid_constant__ 
         if (ok) mlp_features<D, true>(c, st, xin);
         if (__any_sync(0xffffffffu, ok)) warp_mlp<D, true>(s_mlp, xin, ok, dl);  // warp-uniform
         if (cell < g.ncell) {
+            if (ok) {
 #pragma unroll
-            for (int k = 0; k < MlpDims<D>::NOUT; k++) out[(long long)k * g.ncell + cell] = ok ? dl[k] : __int_as_float(0x7fc00000);
+                for (int k = 0; k < MlpDims<D>::NOUT; k++) out[(long long)k * g.ncell + cell] = dl[k];
+            } else {
+                out[cell] = __int_as_float(0x7fc00000);  // NaN in the first row: no learned start
+            }
         }
     }
 }

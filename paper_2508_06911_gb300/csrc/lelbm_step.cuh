@@ -789,6 +789,27 @@ __device__ __forceinline__ void fp64_tail(const Model& m, const Geometry& g, con
             atomicMin(&stats->first_fail, (unsigned long long)cell);
         }
     }
+    if (m.det_lam) {  // deterministic streaming: the gather kernel deposits from these
+#pragma unroll
+        for (int j = 0; j < NF; j++) m.det_lam[(long long)j * g.ncell + cell] = lf[j];
+#pragma unroll
+        for (int j = 0; j < NG; j++) m.det_lam[(long long)(NF + j) * g.ncell + cell] = has_g ? lg[j] : 0.0;
+        double umax = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; a++) umax = fmax(umax, fabs(c.u[a]));
+        atomicMax(m.det_halo, (int)ceil(umax + (double)st.R + 0.5) + 1);
+        unsigned long long q = 0;  // the velocity set's size and reach, for the counters
+        auto count = [&](const double* cp, double) {
+            q++;
+            double d2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; a++) d2 += cp[a] * cp[a];
+            ls.disp_max2 = fmax(ls.disp_max2, d2);
+        };
+        st.for_each(count);
+        if (q > ls.q_max) ls.q_max = q;
+        return;
+    }
     scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls);
 }
 
@@ -1008,10 +1029,13 @@ __device__ __forceinline__ void finish_cell(const Model& m, const Geometry& g, c
     const bool has_g = m.K > 0.0;
     float dls[MlpDims<D>::NOUT];
     if (!dl && m.mlp_start) {  // the learned start of this step, from mlp_start_kernel
+        dls[0] = m.mlp_start[cell];
+        if (isfinite(dls[0])) {  // a NaN first row: the kernel left the cell to Eq. (IID13)
 #pragma unroll
-        for (int k = 0; k < MlpDims<D>::NOUT; k++) dls[k] = m.mlp_start[(long long)k * g.ncell + cell];
-        dl = dls;
-        tc.mlp_cells++;
+            for (int k = 1; k < MlpDims<D>::NOUT; k++) dls[k] = m.mlp_start[(long long)k * g.ncell + cell];
+            dl = dls;
+            tc.mlp_cells++;
+        }
     }
     double lf[NF], lg[NG];
     float lf32[NF], lg32[NG];  // the FP32 path's multipliers
@@ -1221,9 +1245,13 @@ __device__ __forceinline__ void mixed_block(const Model& m, const Geometry& g, c
             }
         } else {
             mlp = m.mlp_start != nullptr && ok;
+            if (mlp) {  // a NaN first row: the network's kernel left the cell to Eq. (IID13)
+                dl[0] = m.mlp_start[cell];
+                mlp = isfinite(dl[0]);
+            }
             if (mlp) {
 #pragma unroll
-                for (int k = 0; k < MlpDims<D>::NOUT; k++) dl[k] = m.mlp_start[(long long)k * g.ncell + cell];
+                for (int k = 1; k < MlpDims<D>::NOUT; k++) dl[k] = m.mlp_start[(long long)k * g.ncell + cell];
                 tc.mlp_cells++;
             }
         }

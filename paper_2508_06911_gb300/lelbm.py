@@ -51,6 +51,7 @@ class lelbm_params(ctypes.Structure):
         ("nz", ctypes.c_int),
         ("bc_z", ctypes.c_int * 2),
         ("inlet_uz", ctypes.c_double),
+        ("deterministic", ctypes.c_int),
     ]
 
 
