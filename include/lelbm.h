@@ -121,15 +121,21 @@ typedef struct {
     double tol;          /* EPR residual tolerance in thermal units; paper: 1e-12      */
     int max_newton;      /* Newton update cap per solve, 1..60                         */
     int precision;       /* LELBM_FP64, LELBM_MIXED or LELBM_FP32                      */
-    const uint8_t* solid;/* host, one byte per padded cell, 1 = solid; NULL: none.
-                            2D interior cells only (flags on pads and in 1D are
-                            ignored).  Solid cells are stationary adiabatic slip
-                            walls (Sec. III.B): a population whose path crosses a
-                            solid face is specularly reflected, exactly traced in
-                            1/64-cell units; a cloud-in-cell share that would fall
-                            on a solid cell is mirrored back across the wall.  An
-                            outflow pad whose nearest interior cell is solid is
-                            solid too (the wall continues through the pads).    */
+    const uint8_t* solid;/* host, one byte per padded cell: 0 fluid, 1 slip wall,
+                            2 no-slip wall; NULL: none.  2D interior cells only
+                            (flags on pads and in 1D are ignored).  Walls are
+                            stationary and adiabatic (Sec. III.B).  A population
+                            whose path crosses a solid face is specularly
+                            reflected, exactly traced in 1/64-cell units.  Slip
+                            walls: a cloud-in-cell share that would fall on a wall
+                            cell is mirrored back across the wall.  No-slip walls
+                            (FP64 path only): a population whose path touches one
+                            is absorbed, with any share that would fall on one;
+                            the cell then launches its own populations with -c_i
+                            (the image populations of Eq. IIIB13 for u_w = 0) and
+                            those whose paths touch the wall enter, scaled to the
+                            absorbed mass (Eq. IIIB14-IIIB15).  An outflow pad
+                            whose nearest interior cell is a wall is that wall. */
     void* stream;        /* cudaStream_t to run on; NULL: a stream owned by the handle  */
     /* three dimensions (dims = 3; ignored below).  FP64 path with the Eq. (IID13)
        start, fluid boundaries only (no solid cells, warm-start store or network,

@@ -700,16 +700,20 @@ static int solid_flag(const orc_grid* g, int NX, int i, int j)
     int py = (g->D == 1 || g->periodic[1]) ? 0 : g->pad;
     int ny = g->D == 1 ? 1 : g->ny;
     int inx = i >= px && i < px + g->nx, iny = j >= py && j < py + ny;
-    if (inx && iny) return g->solid[(long)j * NX + i] != 0;
+    if (inx && iny) return g->solid[(long)j * NX + i];
     if ((i < px && g->bc[0] == 1) || (i >= px + g->nx && g->bc[1] == 1)) return 0;
     if (g->D >= 2 && ((j < py && g->bc[2] == 1) || (j >= py + ny && g->bc[3] == 1))) return 0;
     int si = i < px ? px : (i >= px + g->nx ? px + g->nx - 1 : i);
     int sj = j < py ? py : (j >= py + ny ? py + ny - 1 : j);
-    return g->solid[(long)sj * NX + si] != 0;
+    return g->solid[(long)sj * NX + si];
 }
 
-/* Sec. III.B: is padded cell (i, j) a solid cell?  Cells outside the array are
- * not (their populations are discarded later). */
+/* The bit a wall kind sets in a path's contact record: 1 slip wall, 2 no-slip wall. */
+static int kind_bit(int kind) { return kind == 0 ? 0 : (kind == 2 ? 2 : 1); }
+
+/* Sec. III.B: the wall kind of padded cell (i, j): 0 fluid, 1 slip wall, 2 no-slip
+ * wall (stationary).  Cells outside the array are fluid (their populations are
+ * discarded later). */
 static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
 {
     if (!g->solid) return 0;
@@ -730,8 +734,9 @@ static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
  * cell corner whose diagonal cell is solid reflects only the component normal
  * to a flat wall (one of the two side cells solid, the other fluid) and both
  * components otherwise; with the diagonal cell fluid it passes the corner.
- * Returns 1 if the population touched a wall; *fi, *fj receive the final cell,
- * off[] the final offset from its centre, cs[] the reflected velocity c*. */
+ * Returns the walls the path touched (bit 1: a slip wall, bit 2: a no-slip wall; 0:
+ * none); *fi, *fj receive the final cell, off[] the final offset from its centre,
+ * cs[] the reflected velocity c*. */
 int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const double* c, int* fi, int* fj,
                       double* off, double* cs)
 {
@@ -759,25 +764,29 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
                 i += sx;
                 j += sy;
             } else {
+                int sd = solid_at(g, NX, NY, i + sx, j + sy);
                 int sa = solid_at(g, NX, NY, i + sx, j), sb = solid_at(g, NX, NY, i, j + sy);
-                touched = 1;
                 if (sa && !sb) {
+                    touched |= kind_bit(sa);
                     sx = -sx;
                     j += sy;
                 } else if (sb && !sa) {
+                    touched |= kind_bit(sb);
                     sy = -sy;
                     i += sx;
                 } else {
+                    touched |= kind_bit(sd) | kind_bit(sa) | kind_bit(sb);
                     sx = -sx;
                     sy = -sy;
                 }
             }
         } else {
             int ti = i + (stx ? sx : 0), tj = j + (sty ? sy : 0);
-            if (solid_at(g, NX, NY, ti, tj)) {
+            int st = solid_at(g, NX, NY, ti, tj);
+            if (st) {
                 if (stx) sx = -sx;
                 if (sty) sy = -sy;
-                touched = 1;
+                touched |= kind_bit(st);
             } else {
                 i = ti;
                 j = tj;
@@ -793,6 +802,127 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
     cs[0] = sx * fabs(c[0]);
     cs[1] = D == 2 ? sy * fabs(c[1]) : 0.0;
     return touched;
+}
+
+enum { STREAM_REAL = 0, STREAM_IMAGE_SUM = 1, STREAM_IMAGE_PUT = 2 };
+
+/* Lands one population of padded cell (ix, iy, iz) with velocity c, mass fraction mf
+ * and phonon energy fraction mg (Eq. IIE3).  Without walls it goes to x + c; with
+ * walls its path is traced (Sec. III.B).  The landing point is shared between the
+ * cells it overlaps by cloud-in-cell weights.
+ *   STREAM_REAL: a path that touched a no-slip wall is absorbed (acc += mf, mg; Eq.
+ *     IIIB8), as is a share that would fall on a no-slip cell; a share that would fall
+ *     on a slip cell is mirrored back (the slip-wall reading); the rest is deposited.
+ *   STREAM_IMAGE_SUM / _PUT (c is the reversed velocity -c_i of an image population,
+ *     Eq. IIIB13): only a path that touched a no-slip wall enters; shares that would
+ *     fall on a wall cell are dropped.  _SUM adds the mass of what enters to acc (Eq.
+ *     IIIB14), _PUT deposits it scaled by sf (f) and sg (g) (Eq. IIIB15). */
+static void stream_one(const orc_grid* g, int NX, int NY, int NZ, int ix, int iy, int iz, const double* c,
+                       double mf, double mg, int mode, double sf, double sg, double* Mout, double* acc,
+                       orc_stats* st)
+{
+    int D = g->D, nm = orc_nmom(D);
+    long ncell = (long)NX * NY * NZ;
+    int px = g->periodic[0] ? 0 : g->pad;
+    int py = (D == 1 || g->periodic[1]) ? 0 : g->pad;
+    int pz = (D < 3 || g->periodic[2]) ? 0 : g->pad;
+    int ny = D == 1 ? 1 : g->ny;
+    int nz = D < 3 ? 1 : g->nz;
+    const unsigned char* solid = D <= 2 ? g->solid : NULL;
+    /* landing point: x + c, or the end of the reflected path (Sec. III.B) */
+    double cl[ORC_MAXD] = {c[0], D >= 2 ? c[1] : 0.0, D == 3 ? c[2] : 0.0}, pos[ORC_MAXD];
+    int fi = ix, fj = iy;
+    if (solid) {
+        double off[2];
+        int touched = orc_trace_path(g, NX, NY, ix, iy, c, &fi, &fj, off, cl);
+        if (mode == STREAM_REAL) {
+            if (st && touched) st->wall_hits++;
+            if (touched & 2) {
+                acc[0] += mf;
+                acc[1] += mg;
+                return;
+            }
+        } else if (!(touched & 2)) {
+            return;
+        }
+        pos[0] = fi + off[0];
+        pos[1] = fj + off[1];
+        pos[2] = 0.0;
+    } else {
+        pos[0] = ix + c[0];
+        pos[1] = iy + (D >= 2 ? c[1] : 0.0);
+        pos[2] = iz + (D == 3 ? c[2] : 0.0);
+    }
+    /* cloud-in-cell split of the landing position */
+    int i0[ORC_MAXD] = {0, 0, 0};
+    double w1[ORC_MAXD] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < D; a++) {
+        double fl = floor(pos[a]);
+        i0[a] = (int)fl;
+        w1[a] = pos[a] - fl;
+    }
+    int ncx = w1[0] > 0.0 ? 2 : 1;
+    int ncy = (D >= 2 && w1[1] > 0.0) ? 2 : 1;
+    int ncz = (D == 3 && w1[2] > 0.0) ? 2 : 1;
+    for (int sz = 0; sz < ncz; sz++)
+        for (int sy = 0; sy < ncy; sy++)
+            for (int sx = 0; sx < ncx; sx++) {
+                double w = (sx ? w1[0] : 1.0 - w1[0]);
+                if (D >= 2) w *= (sy ? w1[1] : 1.0 - w1[1]);
+                if (D == 3) w *= (sz ? w1[2] : 1.0 - w1[2]);
+                int cx_ = i0[0] + sx, cy_ = D >= 2 ? i0[1] + sy : 0, cz_ = D == 3 ? i0[2] + sz : 0;
+                double cw[ORC_MAXD] = {cl[0], cl[1], cl[2]};
+                int kind = solid ? solid_at(g, NX, NY, cx_, cy_) : 0;
+                if (kind && mode != STREAM_REAL) continue;
+                if (kind == 2) {
+                    acc[0] += w * mf;
+                    acc[1] += w * mg;
+                    continue;
+                }
+                /* reading: a share that would fall on a slip-wall cell is the mirror
+                 * image of one arriving from the image lattice, so it is mirrored
+                 * back across the wall with the normal velocity component reversed
+                 * (exact for flat walls, Sec. III.B).  A diagonal share behind a
+                 * flat wall (one side cell fluid) goes to that side cell; behind a
+                 * corner of solid cells it goes to the final cell, both reversed. */
+                if (kind) {
+                    int ox = cx_ != fi, oy = cy_ != fj;
+                    if (ox && oy) {
+                        int sa = solid_at(g, NX, NY, cx_, fj), sb = solid_at(g, NX, NY, fi, cy_);
+                        if (!sa && sb) {
+                            ox = 0; /* keep x: mirror across the y wall */
+                        } else if (sa && !sb) {
+                            oy = 0; /* keep y: mirror across the x wall */
+                        }
+                    }
+                    if (ox) {
+                        cw[0] = -cw[0];
+                        cx_ = fi;
+                    }
+                    if (oy) {
+                        cw[1] = -cw[1];
+                        cy_ = fj;
+                    }
+                }
+                /* px = 0 on a periodic axis, py and pz likewise */
+                int tx = land_axis(cx_, g->nx, px, g->periodic[0]);
+                int ty = 0, tz = 0;
+                if (D >= 2) ty = land_axis(cy_, ny, py, g->periodic[1]);
+                if (D == 3) tz = land_axis(cz_, nz, pz, g->periodic[2]);
+                if (mode == STREAM_IMAGE_SUM) {
+                    acc[0] += w * mf;
+                    acc[1] += w * mg;
+                    continue;
+                }
+                if (tx < 0 || ty < 0 || tz < 0) continue;
+                double dM[ORC_MAXM];
+                if (mode == STREAM_IMAGE_PUT)
+                    raw_contrib(D, cw, sf * mf, sg * mg, dM);
+                else
+                    raw_contrib(D, cw, mf, mg, dM);
+                long tgt = ((long)tz * NY + ty) * NX + tx;
+                for (int m = 0; m < nm; m++) Mout[m * ncell + tgt] += w * dM[m];
+            }
 }
 
 /* One time step over a padded grid: fill the pads, then for every non-solid
@@ -846,83 +976,41 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
             }
             double mscale = co.rho;                  /* rho dV f'   (IIE3a) */
             double gscale = co.rho * p->K * co.RT;   /* rho K RT dV g'      */
+            double absorbed[2] = {0.0, 0.0};         /* Eq. (IIIB8): Delta m of f and g */
             for (int k = 0; k < q; k++) {
                 const double* c = pts[k].c;
                 if (st) {
                     double cm = sqrt(dist2(D, c, (double[ORC_MAXD]){0.0, 0.0, 0.0}));
                     if (cm > st->disp_max) st->disp_max = cm;
                 }
-                /* landing point: x + c, or the end of the reflected path (Sec. III.B) */
-                double cl[ORC_MAXD] = {c[0], D >= 2 ? c[1] : 0.0, D == 3 ? c[2] : 0.0}, pos[ORC_MAXD];
-                int fi = ix, fj = iy;
-                if (solid) {
-                    double off[2];
-                    int touched = orc_trace_path(g, NX, NY, ix, iy, c, &fi, &fj, off, cl);
-                    if (st && touched) st->wall_hits++;
-                    pos[0] = fi + off[0];
-                    pos[1] = fj + off[1];
-                    pos[2] = 0.0;
-                } else {
-                    pos[0] = ix + c[0];
-                    pos[1] = iy + (D >= 2 ? c[1] : 0.0);
-                    pos[2] = iz + (D == 3 ? c[2] : 0.0);
-                }
                 double mf = mscale * popf[k], mg = p->K > 0.0 ? gscale * popg[k] : 0.0;
-                /* cloud-in-cell split of the landing position */
-                int i0[ORC_MAXD] = {0, 0, 0};
-                double w1[ORC_MAXD] = {0.0, 0.0, 0.0};
-                for (int a = 0; a < D; a++) {
-                    double fl = floor(pos[a]);
-                    i0[a] = (int)fl;
-                    w1[a] = pos[a] - fl;
-                }
-                int ncx = w1[0] > 0.0 ? 2 : 1;
-                int ncy = (D >= 2 && w1[1] > 0.0) ? 2 : 1;
-                int ncz = (D == 3 && w1[2] > 0.0) ? 2 : 1;
-                for (int sz = 0; sz < ncz; sz++)
-                for (int sy = 0; sy < ncy; sy++)
-                    for (int sx = 0; sx < ncx; sx++) {
-                        double w = (sx ? w1[0] : 1.0 - w1[0]);
-                        if (D >= 2) w *= (sy ? w1[1] : 1.0 - w1[1]);
-                        if (D == 3) w *= (sz ? w1[2] : 1.0 - w1[2]);
-                        int cx_ = i0[0] + sx, cy_ = D >= 2 ? i0[1] + sy : 0, cz_ = D == 3 ? i0[2] + sz : 0;
-                        double cw[ORC_MAXD] = {cl[0], cl[1], cl[2]};
-                        /* reading: a share that would fall on a solid cell is the mirror
-                         * image of one arriving from the image lattice, so it is mirrored
-                         * back across the wall with the normal velocity component reversed
-                         * (exact for flat walls, Sec. III.B).  A diagonal share behind a
-                         * flat wall (one side cell fluid) goes to that side cell; behind a
-                         * corner of solid cells it goes to the final cell, both reversed. */
-                        if (solid && solid_at(g, NX, NY, cx_, cy_)) {
-                            int ox = cx_ != fi, oy = cy_ != fj;
-                            if (ox && oy) {
-                                int sa = solid_at(g, NX, NY, cx_, fj), sb = solid_at(g, NX, NY, fi, cy_);
-                                if (!sa && sb) {
-                                    ox = 0; /* keep x: mirror across the y wall */
-                                } else if (sa && !sb) {
-                                    oy = 0; /* keep y: mirror across the x wall */
-                                }
-                            }
-                            if (ox) {
-                                cw[0] = -cw[0];
-                                cx_ = fi;
-                            }
-                            if (oy) {
-                                cw[1] = -cw[1];
-                                cy_ = fj;
-                            }
-                        }
-                        double dM[ORC_MAXM];
-                        raw_contrib(D, cw, mf, mg, dM);
-                        /* px = 0 on a periodic axis, py and pz likewise */
-                        int tx = land_axis(cx_, g->nx, px, g->periodic[0]);
-                        int ty = 0, tz = 0;
-                        if (D >= 2) ty = land_axis(cy_, ny, py, g->periodic[1]);
-                        if (D == 3) tz = land_axis(cz_, nz, pz, g->periodic[2]);
-                        if (tx < 0 || ty < 0 || tz < 0) continue;
-                        long tgt = ((long)tz * NY + ty) * NX + tx;
-                        for (int m = 0; m < nm; m++) Mout[m * ncell + tgt] += w * dM[m];
+                stream_one(g, NX, NY, NZ, ix, iy, iz, c, mf, mg, STREAM_REAL, 1.0, 1.0, Mout, absorbed, st);
+            }
+            if (absorbed[0] > 0.0 || absorbed[1] > 0.0) {
+                /* Eq. (IIIB13)-(IIIB15) for a stationary no-slip wall: the image
+                 * populations are the cell's own (u_n = u, Eq. IIIB11) launched with
+                 * -c_i; those whose path touches the no-slip wall enter the domain,
+                 * scaled so that their mass equals what the wall absorbed. */
+                double kept[2] = {0.0, 0.0};
+                for (int pass = 0; pass < 2; pass++) {
+                    double sf = kept[0] > 0.0 ? absorbed[0] / kept[0] : 0.0;
+                    double sg = kept[1] > 0.0 ? absorbed[1] / kept[1] : 0.0;
+                    for (int k = 0; k < q; k++) {
+                        double cm[ORC_MAXD] = {-pts[k].c[0], -pts[k].c[1], -pts[k].c[2]};
+                        double mf = mscale * popf[k], mg = p->K > 0.0 ? gscale * popg[k] : 0.0;
+                        stream_one(g, NX, NY, NZ, ix, iy, iz, cm, mf, mg, pass == 0 ? STREAM_IMAGE_SUM : STREAM_IMAGE_PUT,
+                                   sf, sg, Mout, kept, st);
                     }
+                }
+                /* reading: no image reaches the domain (a cell boxed in by walls): the
+                 * absorbed mass and internal energy stay in the cell, at rest */
+                int sxi = land_axis(ix, g->nx, px, g->periodic[0]);
+                int syi = D >= 2 ? land_axis(iy, ny, py, g->periodic[1]) : 0;
+                if (sxi >= 0 && syi >= 0) {
+                    long self = ((long)iz * NY + iy) * NX + ix;
+                    if (kept[0] <= 0.0) Mout[self] += absorbed[0];
+                    if (kept[1] <= 0.0) Mout[(long)iG0(D) * ncell + self] += absorbed[1];
+                }
             }
         }
     free(pts);

@@ -33,6 +33,7 @@ struct lelbm {
     int cur = 0;
     uint8_t* d_type = nullptr;
     uint8_t* d_wall_dist = nullptr;  // 2D with solids: Chebyshev distance to a solid cell
+    uint8_t* d_noslip = nullptr;     // 2D with no-slip walls: their cells
     int* d_inst = nullptr;
     long long* d_inst_lo = nullptr;
     int* d_inst_n = nullptr;
@@ -126,6 +127,12 @@ static int validate(const lelbm_params* p) {
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LELBM_E_INVAL, "nx, ny must be >= 1");
     if (p->dims == 1 && p->ny != 1) return fail(nullptr, LELBM_E_INVAL, "ny must be 1 in 1D");
     if (p->dims >= 2 && p->n_batch > 1) return fail(nullptr, LELBM_E_INVAL, "batches are 1D only");
+    if (p->dims == 2 && p->solid && p->precision != LELBM_FP64) {
+        const int qx = p->bc[0] == LELBM_BC_PERIODIC ? 0 : p->pad, qy = p->bc[2] == LELBM_BC_PERIODIC ? 0 : p->pad;
+        const long long nc = (long long)(p->nx + 2 * qx) * (p->ny + 2 * qy);
+        for (long long i = 0; i < nc; i++)
+            if (p->solid[i] == 2) return fail(nullptr, LELBM_E_INVAL, "no-slip walls need the FP64 path");
+    }
     if (p->deterministic && (p->dims != 2 || p->precision != LELBM_FP64 || p->solid))
         return fail(nullptr, LELBM_E_INVAL, "deterministic streaming needs a 2D FP64 grid without solid cells");
     if (p->dims == 3) {
@@ -183,6 +190,7 @@ static void free_all(lelbm* h) {
     cudaFree(h->M[1]);
     cudaFree(h->d_type);
     cudaFree(h->d_wall_dist);
+    cudaFree(h->d_noslip);
     cudaFree(h->d_inst);
     cudaFree(h->d_inst_lo);
     cudaFree(h->d_inst_n);
@@ -313,6 +321,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     g.periodic[0] = p->bc[0] == LELBM_BC_PERIODIC;
     g.periodic[1] = D == 2 ? p->bc[2] == LELBM_BC_PERIODIC : 1;
     std::vector<uint8_t> type;
+    std::vector<uint8_t> noslip;  // 2D: 1 on no-slip wall cells (solid byte 2)
     std::vector<long long> pad_cell, pad_src;
     if (D == 1) {
         const int nb = p->n_batch > 1 ? p->n_batch : 1;
@@ -439,6 +448,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
         g.ny = p->ny;
         g.n_inst = 1;
         type.resize(h->ncell);
+        noslip.assign(h->ncell, 0);
         for (int iy = 0; iy < NY; iy++)
             for (int ix = 0; ix < NX; ix++) {
                 const long long cell = (long long)iy * NX + ix;
@@ -446,6 +456,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
                 const bool iny = iy >= py && iy < py + p->ny;
                 if (inx && iny) {
                     type[cell] = (p->solid && p->solid[cell]) ? CELL_SOLID : CELL_FLUID;
+                    noslip[cell] = (p->solid && p->solid[cell] == 2) ? 1 : 0;
                     continue;
                 }
                 bool inflow = false;
@@ -465,6 +476,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
                         // the wall continues through an outflow pad whose nearest interior
                         // cell is solid (instead of the pad copying an empty state)
                         type[cell] = CELL_SOLID;
+                        noslip[cell] = p->solid[src] == 2 ? 1 : 0;
                         continue;
                     }
                     type[cell] = CELL_PAD_OUT;
@@ -495,6 +507,10 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     if (!rc && D == 2 && std::find(type.begin(), type.end(), (uint8_t)CELL_SOLID) != type.end()) {
         rc = upload(h, &h->d_wall_dist, wall_distance(type, h->NX, h->NY, g.periodic[0], g.periodic[1]));
         g.wall_dist = h->d_wall_dist;
+        if (!rc && std::find(noslip.begin(), noslip.end(), (uint8_t)1) != noslip.end()) {
+            rc = upload(h, &h->d_noslip, noslip);
+            g.noslip = h->d_noslip;
+        }
     }
     if (!rc) rc = upload(h, &h->d_pad_cell, pad_cell);
     if (!rc) rc = upload(h, &h->d_pad_src, pad_src);

@@ -90,6 +90,8 @@ struct Geometry {
     const int* inst_n;           // 1D: interior length of each instance
     const uint8_t* wall_dist;    // 2D with solids: Chebyshev distance (cells) from each
                                  // cell to the nearest solid cell, capped at 255; else null
+    const uint8_t* noslip;       // 2D with no-slip walls: 1 on every solid cell that is a
+                                 // stationary no-slip wall (0: slip wall); null if none
 };
 
 // Padded 3D grid: cell = (iz * NY + iy) * NX + ix; p* = pad layers of each axis (0 on a

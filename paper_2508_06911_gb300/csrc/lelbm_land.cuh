@@ -74,6 +74,23 @@ __device__ __forceinline__ bool solid_at(const Geometry& g, const uint8_t* type,
     return type[(long long)j * g.NX + i] == CELL_SOLID;
 }
 
+// Contact bit of padded cell (i, j) for a path that reflects off it: 1 for a slip wall, 2
+// for a no-slip wall, 0 for a cell that is not solid.
+__device__ __forceinline__ int wall_bit(const Geometry& g, const uint8_t* type, int i, int j) {
+    if (g.periodic[0]) {
+        i %= g.NX;
+        if (i < 0) i += g.NX;
+    }
+    if (g.periodic[1]) {
+        j %= g.NY;
+        if (j < 0) j += g.NY;
+    }
+    if (i < 0 || i >= g.NX || j < 0 || j >= g.NY) return 0;
+    const long long k = (long long)j * g.NX + i;
+    if (type[k] != CELL_SOLID) return 0;
+    return (g.noslip && g.noslip[k]) ? 2 : 1;
+}
+
 // End of the path x -> x + c past solid cells: the path is walked face by face and at
 // a face of a solid cell the velocity component normal to it is reversed (specular
 // reflection), until the displacement |c| is used up.  Positions are exact integers in
@@ -86,7 +103,7 @@ struct WallLanding {
     int i, j;        // final (fluid) cell, unwrapped padded coordinates
     double off[2];   // landing point relative to its centre, each in (-1/2, 1/2]
     double cs[2];    // reflected velocity c*
-    bool touched;    // reflected at least once
+    int touched;     // walls the path reflected off: bit 1 slip, bit 2 no-slip (0: none)
 };
 
 __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8_t* type, int ix, int iy,
@@ -96,7 +113,7 @@ __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8
     int sx = (qx > 0) - (qx < 0), sy = (qy > 0) - (qy < 0);
     const long long ax = qx < 0 ? -qx : qx, ay = qy < 0 ? -qy : qy;
     int i = ix, j = iy;
-    bool touched = false;
+    int touched = 0;
     long long kx = 0, ky = 0;
     while (true) {
         const long long Xn = S / 2 + S * kx, Yn = S / 2 + S * ky;
@@ -109,29 +126,33 @@ __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8
             sty = r <= l;
         }
         if (stx && sty) {
-            if (!solid_at(g, type, i + sx, j + sy)) {
+            const int bd = wall_bit(g, type, i + sx, j + sy);
+            if (!bd) {
                 i += sx;
                 j += sy;
             } else {
-                const bool sa = solid_at(g, type, i + sx, j), sb = solid_at(g, type, i, j + sy);
-                touched = true;
-                if (sa && !sb) {
+                const int ba = wall_bit(g, type, i + sx, j), bb = wall_bit(g, type, i, j + sy);
+                if (ba && !bb) {
+                    touched |= ba;
                     sx = -sx;
                     j += sy;
-                } else if (sb && !sa) {
+                } else if (bb && !ba) {
+                    touched |= bb;
                     sy = -sy;
                     i += sx;
                 } else {
+                    touched |= bd | ba | bb;
                     sx = -sx;
                     sy = -sy;
                 }
             }
         } else {
             const int ti = i + (stx ? sx : 0), tj = j + (sty ? sy : 0);
-            if (solid_at(g, type, ti, tj)) {
+            const int bt = wall_bit(g, type, ti, tj);
+            if (bt) {
                 if (stx) sx = -sx;
                 if (sty) sy = -sy;
-                touched = true;
+                touched |= bt;
             } else {
                 i = ti;
                 j = tj;
@@ -162,15 +183,39 @@ __device__ __forceinline__ void add_moments_2d(double* Mout, long long ncell, lo
     for (int mm = 0; mm < 11; mm++) atomicAdd(Mout + mm * ncell + tgt, dM[mm]);
 }
 
+// How stream_traced treats a population (Sec. III.B, Eq. IIIB8-IIIB15):
+//   kStreamReal: a population of the cell.  Its path reflects specularly at slip walls; a
+//     path that touches a no-slip wall is absorbed (acc += mf, mg: the Delta m of Eq.
+//     IIIB8), as is a cloud-in-cell share that would fall on a no-slip cell; a share that
+//     would fall on a slip cell is mirrored back across the wall.
+//   kStreamImageSum / kStreamImagePut: an image population of a no-slip wall (cp is the
+//     reversed velocity -c_i, Eq. IIIB13).  Only a path that touches a no-slip wall enters
+//     the domain, and shares that would fall on a solid cell are dropped; _Sum adds the
+//     mass that enters to acc (Eq. IIIB14), _Put deposits it scaled by sf and sg (Eq.
+//     IIIB15).
+enum : int { kStreamReal = 0, kStreamImageSum = 1, kStreamImagePut = 2 };
+
 // Streams one population of cell (ix, iy) with velocity cp past the solid cells (2D):
 // its path is traced, the landing point is shared between cells by cloud-in-cell
-// weights, and a share that would fall on a solid cell is mirrored back across the wall
-// with the normal component of its velocity reversed (into the side cell behind a flat
-// wall, into the final cell behind a corner of solid cells).  Returns whether the path
-// was reflected.  Kept out of line: only cells near a solid cell take this path.
-static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8_t* type, double* Mout, int ix, int iy,
-                                           const double* cp, double mf, double mg) {
+// weights, and a share that would fall on a slip-wall cell is mirrored back across the
+// wall with the normal component of its velocity reversed (into the side cell behind a
+// flat wall, into the final cell behind a corner of solid cells).  acc == null: every wall
+// is treated as a slip wall (the paths without no-slip walls).  Returns the walls the path
+// touched (bit 1 slip, bit 2 no-slip).  Kept out of line: only cells near a solid cell take
+// this path.
+static __device__ __noinline__ int stream_traced(const Geometry& g, const uint8_t* type, double* Mout, int ix, int iy,
+                                                 const double* cp, double mf, double mg, int mode = kStreamReal,
+                                                 double* acc = nullptr, double sf = 1.0, double sg = 1.0) {
     const WallLanding L = trace_path(g, type, ix, iy, cp);
+    const bool noslip = acc != nullptr;
+    if (noslip) {
+        if (mode == kStreamReal && (L.touched & 2)) {
+            acc[0] += mf;
+            acc[1] += mg;
+            return L.touched;
+        }
+        if (mode != kStreamReal && !(L.touched & 2)) return L.touched;
+    }
     const double pos[2] = {(double)L.i + L.off[0], (double)L.j + L.off[1]};
     int base[2];
     double w1[2];
@@ -186,7 +231,16 @@ static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8
             const double w = (sx ? w1[0] : 1.0 - w1[0]) * (sy ? w1[1] : 1.0 - w1[1]);
             int tx = base[0] + sx, ty = base[1] + sy;
             double cw[2] = {L.cs[0], L.cs[1]};
-            if (solid_at(g, type, tx, ty)) {
+            const int kind = wall_bit(g, type, tx, ty);
+            if (kind && noslip) {
+                if (mode != kStreamReal) continue;
+                if (kind == 2) {
+                    acc[0] += w * mf;
+                    acc[1] += w * mg;
+                    continue;
+                }
+            }
+            if (kind) {
                 bool ox = tx != L.i, oy = ty != L.j;
                 if (ox && oy) {
                     const bool sa = solid_at(g, type, tx, L.j), sb = solid_at(g, type, L.i, ty);
@@ -202,8 +256,14 @@ static __device__ __noinline__ bool stream_traced(const Geometry& g, const uint8
                     ty = L.j;
                 }
             }
+            if (mode == kStreamImageSum) {
+                acc[0] += w * mf;
+                acc[1] += w * mg;
+                continue;
+            }
             const long long tgt = land<2>(g, 0, 0, 0, ix, iy, tx - ix, ty - iy);
-            if (tgt >= 0 && type[tgt] == CELL_FLUID) add_moments_2d(Mout, g.ncell, tgt, cw, w * mf, w * mg);
+            const double kf = mode == kStreamImagePut ? sf : 1.0, kg = mode == kStreamImagePut ? sg : 1.0;
+            if (tgt >= 0 && type[tgt] == CELL_FLUID) add_moments_2d(Mout, g.ncell, tgt, cw, w * kf * mf, w * kg * mg);
         }
     return L.touched;
 }

@@ -447,6 +447,48 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
 // and <= 2 (phonons) of the deposited populations and returns whether their
 // residual against conF / conG is within the tolerance (the FP64 judge of the
 // mixed path).  sign = -1 removes a previous deposit of the same populations.
+// Image populations of a stationary no-slip wall (Sec. III.B, Eq. IIIB13-IIIB15) for a cell
+// whose streaming gave the wall the mass absorbed[0] (f) and energy absorbed[1] (g).  With
+// u_w = 0 the image moments are the cell's own (u_n = u, Eq. IIIB11), so the images are the
+// cell's populations launched with -c_i; those whose path touches the no-slip wall enter the
+// domain, scaled so that they carry exactly what the wall absorbed: one pass sums what
+// enters, a second deposits it.  If nothing enters (a cell boxed in by walls) the absorbed
+// mass and internal energy stay in the cell, at rest.
+static __device__ __noinline__ void noslip_images(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
+                                                  long long cell, int ix, int iy, const CellState<2>& c,
+                                                  const Stencil<2>& st, const double* lf, const double* lg, double mfs,
+                                                  double mgs, const double* absorbed) {
+    const bool has_g = m.K > 0.0;
+    double kept[2] = {0.0, 0.0}, unused[2] = {0.0, 0.0};
+    for (int pass = 0; pass < 2; pass++) {
+        const double sf = kept[0] > 0.0 ? absorbed[0] / kept[0] : 0.0;
+        const double sg = kept[1] > 0.0 ? absorbed[1] / kept[1] : 0.0;
+        auto image = [&](const double* cp, double dC) {
+            const double t[2] = {(cp[0] - c.u[0]) * c.inv_sig, (cp[1] - c.u[1]) * c.inv_sig};
+            double T[10];
+            Basis<2, true>::eval(t, T);
+            double ef = 1.0;
+#pragma unroll
+            for (int j = 0; j < 10; j++) ef += lf[j] * T[j];
+            double gp = 0.0;
+            if (has_g) {
+                double eg = 1.0;
+#pragma unroll
+                for (int j = 0; j < 6; j++) eg += lg[j] * T[j];
+                gp = dC * exp(-eg);
+            }
+            const double cm[2] = {-cp[0], -cp[1]};
+            stream_traced(g, type, Mout, ix, iy, cm, mfs * (dC * exp(-ef)), mgs * gp,
+                          pass == 0 ? kStreamImageSum : kStreamImagePut, pass == 0 ? kept : unused, sf, sg);
+        };
+        st.for_each(image);
+    }
+    if (type[cell] == CELL_FLUID) {
+        if (kept[0] <= 0.0 && absorbed[0] != 0.0) atomicAdd(Mout + cell, absorbed[0]);
+        if (kept[1] <= 0.0 && absorbed[1] != 0.0) atomicAdd(Mout + (long long)iG0<2>() * g.ncell + cell, absorbed[1]);
+    }
+}
+
 template <int D, bool CHECK>
 __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                              long long cell, const CellState<D>& c, const Stencil<D>& st,
@@ -506,8 +548,12 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
 #pragma unroll
         for (int mm = 0; mm < NM; mm++) atomicAdd(Mout + mm * g.ncell + tgt, dM[mm]);
     };
+    double absorbed[2] = {0.0, 0.0};  // Eq. (IIIB8): what no-slip walls took, f and g
     auto deposit_traced = [&](const double* cp, double mf, double mg) {
-        if constexpr (D == 2) walls += stream_traced(g, type, Mout, ix, iy, cp, mf, mg) ? (sign > 0.0 ? 1 : -1) : 0;
+        if constexpr (D == 2)
+            walls += stream_traced(g, type, Mout, ix, iy, cp, mf, mg, kStreamReal, g.noslip ? absorbed : nullptr)
+                         ? (sign > 0.0 ? 1 : -1)
+                         : 0;
     };
     auto row = [&](int cy, int xa, int xb) {
         double y = 0.0;
@@ -599,6 +645,10 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
             }
     };
     st.for_each_row(row, leaf);
+    if constexpr (D == 2) {
+        if (absorbed[0] != 0.0 || absorbed[1] != 0.0)
+            noslip_images(m, g, type, Mout, cell, ix, iy, c, st, lf, lg, mfs, mgs, absorbed);
+    }
     if (q > ls.q_max) ls.q_max = q;
     ls.points += q;
     ls.walls += walls;

@@ -113,3 +113,78 @@ def test_wall_through_outflow_pads(prec):
     assert_close(M[:, mask], ref[:, mask], tol, f"wall through outflow pads ({prec})")
     assert st.wall_hits == st_o.wall_hits > 0
     assert st.fallback_mx == 0 and st_o.fallback_mx == 0
+
+
+def noslip_field(nx, ny, seed_index, RT_lo, RT_hi, umag):
+    """Slip and no-slip walls together: a no-slip frame, slip blocks and single cells."""
+    w = obstacle_field(nx, ny, seed_index, RT_lo, RT_hi, umag, 0.02)
+    w.solid = w.solid.copy()
+    frame = np.zeros_like(w.solid)
+    frame[0, :] = frame[-1, :] = frame[:, 0] = 1
+    w.solid[frame == 1] = 2  # the frame is no-slip, the rest stays slip
+    return w
+
+
+@pytest.mark.parametrize("RT_lo,RT_hi", [(0.6, 2.0), (0.1, 0.35)])
+def test_noslip_walls_match_oracle(RT_lo, RT_hi):
+    """Stationary no-slip walls (Sec. III.B, Eq. IIIB8-IIIB15 with u_w = 0) beside slip
+    blocks: one and three steps against the oracle, and mass conserved in the closed box."""
+    w = noslip_field(30, 22, 11, RT_lo, RT_hi, 0.4)
+    mask = interior_mask_2d(w)
+    for n in (1, 3):
+        M, ref, st, st_o = run_both(w, n)
+        assert_close(M[:, mask], ref[:, mask], STEP_TOL * n, f"no-slip walls, {n} steps")
+        assert st.wall_hits == st_o.wall_hits > 0
+        assert st.fallback_mx == 0
+    s = Solver.grid2d(w)
+    m0 = s.get_moments()[0, mask].sum()
+    s.step(20)
+    m1 = s.get_moments()[0, mask].sum()
+    s.close()
+    assert abs(m1 / m0 - 1) < 1e-12
+
+
+def test_noslip_channel_shear_mode_on_gpu():
+    """The lowest shear mode between two no-slip walls, H = 32: the GPU's decay matches the
+    oracle's step by step and the viscous rate nu (pi / H)^2 within 10 %."""
+    H, nx, nu, RT, amp = 32, 4, 0.05, 0.5, 1e-3
+    ny = H + 2
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0] = solid[-1] = 2
+    yc = np.arange(ny) + 0.5
+    mode = np.sin(np.pi * (yc - 1.0) / H)
+    mode[0] = mode[-1] = 0.0
+    u = np.zeros((2, ny, nx))
+    u[0] = amp * mode[:, None]
+    w = W.Grid2D(nx=nx, ny=ny, rho=np.ones((ny, nx)), u=u, RT=np.full((ny, nx), RT), bc=(2, 2, 2, 2), pad=0,
+                 K=3.0, nu=nu, Pr=1.0, steps=400, solid=solid)
+    s = Solver.grid2d(w, limiter=0)
+    fl = (solid == 0).reshape(-1)
+    a = []
+    for _ in range(400):
+        s.step(1)
+        M = s.get_moments()
+        ux = np.zeros(ny * nx)
+        ux[fl] = M[1, fl] / M[0, fl]
+        a.append((ux.reshape(ny, nx).mean(1) * mode).sum() / (mode * mode).sum())
+    s.close()
+    t = np.arange(1, 401)
+    rate = -np.polyfit(t[66:], np.log(np.array(a)[66:]), 1)[0]
+    ratio = rate / (nu * (np.pi / H) ** 2)
+    print(f"no-slip channel H = {H}: decay rate / nu (pi/H)^2 = {ratio:.4f}")
+    assert abs(ratio - 1) < 0.10
+    ref = oracle_2d(w, 3, limiter=0)
+    s = Solver.grid2d(w, limiter=0)
+    s.step(3)
+    got = s.get_moments()
+    s.close()
+    # the transverse moments vanish by symmetry (rounding noise on both sides), so the
+    # bound is relative to the largest moment of the state
+    err = np.abs(got[:, fl] - ref[:, fl]).max() / np.abs(ref[:, fl]).max()
+    assert err <= 3 * STEP_TOL, f"no-slip channel, 3 steps: {err:.2e}"
+
+
+def test_noslip_walls_need_the_fp64_path():
+    w = noslip_field(16, 12, 12, 0.5, 1.0, 0.2)
+    with pytest.raises(L.LelbmError):
+        Solver.grid2d(w, precision=L.LELBM_MIXED)

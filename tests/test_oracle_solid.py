@@ -314,3 +314,88 @@ def test_wall_through_outflow_pads_keeps_parallel_stream_uniform():
     assert np.all(np.isfinite(M))
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
     assert st.fallback_mx == 0 and st.wall_hits > 0
+
+
+# --- stationary no-slip walls (Sec. III.B, Eq. IIIB8-IIIB15 with u_w = 0) -----------------
+
+def noslip_box(n, seed, RT_lo, RT_hi, umag, kind=2):
+    """A periodic n x n grid inside a one-cell frame of wall cells of the given kind."""
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((n, n), np.uint8)
+    solid[0, :] = solid[-1, :] = solid[:, 0] = solid[:, -1] = kind
+    g = O.grid(2, n, n, periodic=(True, True), solid=solid.reshape(-1))
+    Y, X = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, 4)
+    rho = 1.0 + 0.2 * np.cos(2 * np.pi * X / n + ph[0]) * np.cos(2 * np.pi * Y / n + ph[1])
+    RT = RT_lo + (RT_hi - RT_lo) * (0.5 + 0.5 * np.sin(2 * np.pi * (X + Y) / n + ph[2]))
+    u = umag * np.stack([np.sin(2 * np.pi * Y / n + ph[3]), np.cos(2 * np.pi * X / n + ph[0])])
+    return g, solid, rho, u, RT
+
+
+@pytest.mark.parametrize("RT_lo,RT_hi", [(0.5, 1.5), (0.2, 0.4)])
+def test_noslip_closed_box_conserves_mass(RT_lo, RT_hi):
+    """The wall returns, as image populations, exactly the mass it took (Eq. IIIB15): the
+    total of rho over the fluid cells is conserved to rounding.  (Energy is not a step
+    invariant here: images carry the cell's own energy per unit mass, not the absorbed one.)"""
+    g, solid, rho, u, RT = noslip_box(18, 5, RT_lo, RT_hi, 0.4)
+    p = O.params(2, 3.0, nu_s=5e-3)
+    fluid = (solid == 0).reshape(-1)
+    M = O.state_from_primitives(g, p, rho, u, RT)
+    M[:, ~fluid] = 0.0
+    st = O.Stats()
+    for _ in range(3):
+        M1 = O.step(g, p, M, st)
+        assert abs(M1[0, fluid].sum() / M[0, fluid].sum() - 1) < 1e-13
+        assert np.all(M1[:, ~fluid] == 0.0)
+        M = M1
+    assert st.wall_hits > 0 and st.fallback_mx == 0
+
+
+def test_noslip_gas_at_rest_stays_at_rest():
+    g, solid, rho, u, RT = noslip_box(14, 6, 0.6, 0.6, 0.0)
+    rho[:] = 1.0
+    p = O.params(2, 3.0, nu_s=5e-3)
+    M = O.state_from_primitives(g, p, rho, u, RT)
+    fluid = (solid == 0).reshape(-1)
+    M[:, ~fluid] = 0.0
+    M1 = O.run(g, p, M, 3)
+    np.testing.assert_allclose(M1[:, fluid], M[:, fluid], rtol=1e-12, atol=1e-13)
+
+
+def channel_decay_rate(H, steps, nu=0.05, RT=0.5, amp=1e-3, nx=4, kind=2):
+    """Decay rate of the lowest shear mode u_x = a sin(pi (y - 1) / H) between two walls
+    (interior rows 0 and H + 1), periodic along x."""
+    ny = H + 2
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0] = solid[-1] = kind
+    g = O.grid(2, nx, ny, periodic=(True, True), solid=solid.reshape(-1))
+    p = O.params(2, 3.0, nu_s=nu, Pr=1.0, limiter=0)
+    yc = np.arange(ny) + 0.5
+    mode = np.sin(np.pi * (yc - 1.0) / H)
+    mode[0] = mode[-1] = 0.0
+    u = np.zeros((2, ny, nx))
+    u[0] = amp * mode[:, None]
+    M = O.state_from_primitives(g, p, np.ones((ny, nx)), u, np.full((ny, nx), RT))
+    fl = (solid == 0).reshape(-1)
+    M[:, ~fl] = 0.0
+    a = []
+    for _ in range(steps):
+        M = O.step(g, p, M)
+        ux = np.zeros(ny * nx)
+        ux[fl] = M[1, fl] / M[0, fl]
+        ux = ux.reshape(ny, nx).mean(1)
+        a.append((ux * mode).sum() / (mode * mode).sum())
+    t = np.arange(1, steps + 1)
+    sl = slice(steps // 6, steps)
+    return -np.polyfit(t[sl], np.log(np.array(a)[sl]), 1)[0]
+
+
+def test_noslip_channel_shear_mode_decays_at_viscous_rate():
+    """Between two stationary no-slip walls the lowest shear mode decays at nu (pi / H)^2
+    (a wall-bounded Sec. IV.A): within 10 % at H = 32, and the deviation (the position of
+    the no-slip plane, a fraction of a cell from the wall face) shrinks with H."""
+    nu = 0.05
+    r32 = channel_decay_rate(32, 400, nu) / (nu * (np.pi / 32) ** 2)
+    r16 = channel_decay_rate(16, 200, nu) / (nu * (np.pi / 16) ** 2)
+    assert abs(r32 - 1) < 0.10
+    assert abs(r16 - 1) > 1.6 * abs(r32 - 1)
