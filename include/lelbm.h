@@ -122,7 +122,7 @@ typedef struct {
     int max_newton;      /* Newton update cap per solve, 1..60                         */
     int precision;       /* LELBM_FP64, LELBM_MIXED or LELBM_FP32                      */
     const uint8_t* solid;/* host, one byte per padded cell: 0 fluid, 1 slip wall,
-                            2 no-slip wall; NULL: none.  2D interior cells only
+                            2 no-slip wall, 3 moving no-slip wall; NULL: none.  2D interior cells only
                             (flags on pads and in 1D are ignored).  Walls are
                             stationary and adiabatic (Sec. III.B).  A population
                             whose path crosses a solid face is specularly
@@ -134,8 +134,12 @@ typedef struct {
                             the cell then launches its own populations with -c_i
                             (the image populations of Eq. IIIB13 for u_w = 0) and
                             those whose paths touch the wall enter, scaled to the
-                            absorbed mass (Eq. IIIB14-IIIB15).  An outflow pad
-                            whose nearest interior cell is a wall is that wall. */
+                            absorbed mass (Eq. IIIB14-IIIB15).  3: a no-slip wall
+                            moving at wall_u (tangentially; the cell stays solid):
+                            its images are the EPR populations of the cell's
+                            post-collision central constraints at the bulk
+                            velocity u - 2 u_w (Eq. IIIB10-IIIB11).  An outflow pad
+                            whose nearest interior cell is a wall is that wall.  */
     void* stream;        /* cudaStream_t to run on; NULL: a stream owned by the handle  */
     /* three dimensions (dims = 3; ignored below).  FP64 path with the Eq. (IID13)
        start, fluid boundaries only (no solid cells, warm-start store or network,
@@ -153,6 +157,8 @@ typedef struct {
                             multipliers ((N_f + N_g) doubles per cell, 128 B in 2D) for
                             a gather kernel in which every target cell sums what the
                             cells within reach send it (Eq. IIE3).                    */
+    double wall_u[2];    /* velocity u_w of the moving no-slip walls (solid byte 3),
+                            Eq. (IIIB2)-(IIIB4)                                        */
 } lelbm_params;
 
 /* Per-handle counters accumulated by every step since the last reset. */

@@ -94,6 +94,7 @@ class Grid(ctypes.Structure):
         ("bc", ctypes.c_int * 6),
         ("inlet", ctypes.c_double * 5),
         ("solid", ctypes.POINTER(ctypes.c_ubyte)),
+        ("wall_u", ctypes.c_double * 2),
     ]
 
 
@@ -316,10 +317,11 @@ def cell_populations(p: Params, M):
 
 
 def grid(D, nx, ny=1, periodic=(False, False), pad=0, bc=(0, 0, 0, 0), inlet=(1.0, 0.0, 0.0, 1.0),
-         solid=None, nz=1):
+         solid=None, nz=1, wall_u=(0.0, 0.0)):
     """Grid description; ``solid`` is a uint8 array over the padded grid (kept alive on the Grid).
     bc: per side (x-, x+, y-, y+[, z-, z+]); inlet: (rho, ux, uy, RT) or (rho, ux, uy, uz, RT);
-    periodic: per axis (2 or 3 entries)."""
+    periodic: per axis (2 or 3 entries); solid: wall kinds (0 fluid, 1 slip, 2 no-slip at rest,
+    3 no-slip moving at wall_u)."""
     g = Grid()
     g.D, g.nx, g.ny, g.nz = D, nx, (ny if D >= 2 else 1), (nz if D == 3 else 1)
     per = tuple(periodic) + (False,) * (3 - len(periodic))
@@ -338,6 +340,7 @@ def grid(D, nx, ny=1, periodic=(False, False), pad=0, bc=(0, 0, 0, 0), inlet=(1.
         g.solid = s.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
     else:
         g.solid = ctypes.POINTER(ctypes.c_ubyte)()
+    g.wall_u[0], g.wall_u[1] = float(wall_u[0]), float(wall_u[1])
     return g
 
 

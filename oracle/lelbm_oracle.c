@@ -87,7 +87,10 @@ typedef struct {
     int pad;                 /* pad layers on every non-periodic side       */
     int bc[6];               /* x-, x+, y-, y+, z-, z+: 0 outflow, 1 inflow */
     double inlet[5];         /* rho, ux, uy, uz, RT of the inflow state     */
-    const unsigned char* solid; /* padded-grid solid flags or NULL (1D, 2D) */
+    const unsigned char* solid; /* padded-grid wall kinds or NULL (1D, 2D): 0 fluid,
+                                   1 slip wall, 2 no-slip wall at rest, 3 no-slip wall
+                                   moving at wall_u                            */
+    double wall_u[2];        /* velocity u_w of the kind-3 walls (Eq. IIIB2-IIIB4) */
 } orc_grid;
 
 /* N_M = 1 + D + D(D+1)/2 + D (fluons) plus 1 + D (phonons), Eq. (IIB5) */
@@ -708,8 +711,11 @@ static int solid_flag(const orc_grid* g, int NX, int i, int j)
     return g->solid[(long)sj * NX + si];
 }
 
-/* The bit a wall kind sets in a path's contact record: 1 slip wall, 2 no-slip wall. */
-static int kind_bit(int kind) { return kind == 0 ? 0 : (kind == 2 ? 2 : 1); }
+/* The bit a wall kind sets in a path's contact record: 1 slip wall, 2 no-slip wall at
+ * rest, 4 moving no-slip wall. */
+static int kind_bit(int kind) { return kind == 0 ? 0 : (kind == 2 ? 2 : (kind == 3 ? 4 : 1)); }
+/* The no-slip boundary n (Eq. IIIB8) a contact belongs to: 1 at rest, 2 moving, 0 none. */
+static int noslip_of(int kind) { return kind == 2 ? 1 : (kind == 3 ? 2 : 0); }
 
 /* Sec. III.B: the wall kind of padded cell (i, j): 0 fluid, 1 slip wall, 2 no-slip
  * wall (stationary).  Cells outside the array are fluid (their populations are
@@ -734,9 +740,10 @@ static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
  * cell corner whose diagonal cell is solid reflects only the component normal
  * to a flat wall (one of the two side cells solid, the other fluid) and both
  * components otherwise; with the diagonal cell fluid it passes the corner.
- * Returns the walls the path touched (bit 1: a slip wall, bit 2: a no-slip wall; 0:
- * none); *fi, *fj receive the final cell, off[] the final offset from its centre,
- * cs[] the reflected velocity c*. */
+ * Returns the walls the path touched (bit 1: a slip wall, bit 2: a no-slip wall at rest,
+ * bit 4: a moving no-slip wall; 0: none) and, in bits 4-5, the last no-slip boundary it
+ * touched (1 at rest, 2 moving); *fi, *fj receive the final cell, off[] the final offset
+ * from its centre, cs[] the reflected velocity c*. */
 int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const double* c, int* fi, int* fj,
                       double* off, double* cs)
 {
@@ -745,7 +752,7 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
     long qx = lround(S * c[0]), qy = D == 2 ? lround(S * c[1]) : 0;
     int sx = qx > 0 ? 1 : (qx < 0 ? -1 : 0), sy = qy > 0 ? 1 : (qy < 0 ? -1 : 0);
     long ax = labs(qx), ay = labs(qy);
-    int i = ix, j = iy, touched = 0;
+    int i = ix, j = iy, touched = 0, last_ns = 0;
     long kx = 0, ky = 0;
     for (;;) {
         long Xn = S / 2 + S * kx, Yn = S / 2 + S * ky;
@@ -768,14 +775,19 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
                 int sa = solid_at(g, NX, NY, i + sx, j), sb = solid_at(g, NX, NY, i, j + sy);
                 if (sa && !sb) {
                     touched |= kind_bit(sa);
+                    if (noslip_of(sa)) last_ns = noslip_of(sa);
                     sx = -sx;
                     j += sy;
                 } else if (sb && !sa) {
                     touched |= kind_bit(sb);
+                    if (noslip_of(sb)) last_ns = noslip_of(sb);
                     sy = -sy;
                     i += sx;
                 } else {
                     touched |= kind_bit(sd) | kind_bit(sa) | kind_bit(sb);
+                    /* a corner: the diagonal cell, else a side cell, names the boundary */
+                    int k = noslip_of(sd) ? sd : (noslip_of(sa) ? sa : sb);
+                    if (noslip_of(k)) last_ns = noslip_of(k);
                     sx = -sx;
                     sy = -sy;
                 }
@@ -787,6 +799,7 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
                 if (stx) sx = -sx;
                 if (sty) sy = -sy;
                 touched |= kind_bit(st);
+                if (noslip_of(st)) last_ns = noslip_of(st);
             } else {
                 i = ti;
                 j = tj;
@@ -801,7 +814,7 @@ int orc_trace_path(const orc_grid* g, int NX, int NY, int ix, int iy, const doub
     off[1] = sy * (double)(ay - S * ky) / S;
     cs[0] = sx * fabs(c[0]);
     cs[1] = D == 2 ? sy * fabs(c[1]) : 0.0;
-    return touched;
+    return touched | (last_ns << 4);
 }
 
 enum { STREAM_REAL = 0, STREAM_IMAGE_SUM = 1, STREAM_IMAGE_PUT = 2 };
@@ -810,15 +823,18 @@ enum { STREAM_REAL = 0, STREAM_IMAGE_SUM = 1, STREAM_IMAGE_PUT = 2 };
  * and phonon energy fraction mg (Eq. IIE3).  Without walls it goes to x + c; with
  * walls its path is traced (Sec. III.B).  The landing point is shared between the
  * cells it overlaps by cloud-in-cell weights.
- *   STREAM_REAL: a path that touched a no-slip wall is absorbed (acc += mf, mg; Eq.
- *     IIIB8), as is a share that would fall on a no-slip cell; a share that would fall
- *     on a slip cell is mirrored back (the slip-wall reading); the rest is deposited.
- *   STREAM_IMAGE_SUM / _PUT (c is the reversed velocity -c_i of an image population,
- *     Eq. IIIB13): only a path that touched a no-slip wall enters; shares that would
- *     fall on a wall cell are dropped.  _SUM adds the mass of what enters to acc (Eq.
- *     IIIB14), _PUT deposits it scaled by sf (f) and sg (g) (Eq. IIIB15). */
+ *   STREAM_REAL: a path that touched a no-slip wall is absorbed by the last no-slip
+ *     boundary n it touched (acc[2(n-1)] += mf, acc[2(n-1)+1] += mg; Eq. IIIB8), as is a
+ *     share that would fall on a no-slip cell (by that cell's boundary); a share that
+ *     would fall on a slip cell is mirrored back (the slip-wall reading); the rest is
+ *     deposited.
+ *   STREAM_IMAGE_SUM / _PUT (c is the reversed velocity -c_i of an image population of
+ *     boundary sel, Eq. IIIB13): only a path whose last no-slip contact is boundary sel
+ *     enters; shares that would fall on a wall cell are dropped.  _SUM adds the mass of
+ *     what enters to acc[0..1] (Eq. IIIB14), _PUT deposits it scaled by sf (f) and sg
+ *     (g) (Eq. IIIB15). */
 static void stream_one(const orc_grid* g, int NX, int NY, int NZ, int ix, int iy, int iz, const double* c,
-                       double mf, double mg, int mode, double sf, double sg, double* Mout, double* acc,
+                       double mf, double mg, int mode, int sel, double sf, double sg, double* Mout, double* acc,
                        orc_stats* st)
 {
     int D = g->D, nm = orc_nmom(D);
@@ -835,14 +851,15 @@ static void stream_one(const orc_grid* g, int NX, int NY, int NZ, int ix, int iy
     if (solid) {
         double off[2];
         int touched = orc_trace_path(g, NX, NY, ix, iy, c, &fi, &fj, off, cl);
+        int ns = touched >> 4; /* the last no-slip boundary the path touched */
         if (mode == STREAM_REAL) {
-            if (st && touched) st->wall_hits++;
-            if (touched & 2) {
-                acc[0] += mf;
-                acc[1] += mg;
+            if (st && (touched & 15)) st->wall_hits++;
+            if (ns) {
+                acc[2 * (ns - 1)] += mf;
+                acc[2 * (ns - 1) + 1] += mg;
                 return;
             }
-        } else if (!(touched & 2)) {
+        } else if (ns != sel) {
             return;
         }
         pos[0] = fi + off[0];
@@ -874,9 +891,9 @@ static void stream_one(const orc_grid* g, int NX, int NY, int NZ, int ix, int iy
                 double cw[ORC_MAXD] = {cl[0], cl[1], cl[2]};
                 int kind = solid ? solid_at(g, NX, NY, cx_, cy_) : 0;
                 if (kind && mode != STREAM_REAL) continue;
-                if (kind == 2) {
-                    acc[0] += w * mf;
-                    acc[1] += w * mg;
+                if (noslip_of(kind)) {
+                    acc[2 * (noslip_of(kind) - 1)] += w * mf;
+                    acc[2 * (noslip_of(kind) - 1) + 1] += w * mg;
                     continue;
                 }
                 /* reading: a share that would fall on a slip-wall cell is the mirror
@@ -952,6 +969,9 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
     orc_point* pts = (orc_point*)malloc(sizeof(orc_point) * cap);
     double* popf = (double*)malloc(sizeof(double) * cap);
     double* popg = (double*)malloc(sizeof(double) * cap);
+    int icap = 0; /* image velocity sets of moving walls */
+    orc_point* imp = NULL;
+    double *imf = NULL, *img = NULL;
     for (int iz = 0; iz < NZ; iz++)
     for (int iy = 0; iy < NY; iy++)
         for (int ix = 0; ix < NX; ix++) {
@@ -976,7 +996,8 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
             }
             double mscale = co.rho;                  /* rho dV f'   (IIE3a) */
             double gscale = co.rho * p->K * co.RT;   /* rho K RT dV g'      */
-            double absorbed[2] = {0.0, 0.0};         /* Eq. (IIIB8): Delta m of f and g */
+            double absorbed[4] = {0.0, 0.0, 0.0, 0.0}; /* Eq. (IIIB8): Delta m (f, g) of the
+                                                         no-slip boundaries at rest, moving */
             for (int k = 0; k < q; k++) {
                 const double* c = pts[k].c;
                 if (st) {
@@ -984,22 +1005,51 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
                     if (cm > st->disp_max) st->disp_max = cm;
                 }
                 double mf = mscale * popf[k], mg = p->K > 0.0 ? gscale * popg[k] : 0.0;
-                stream_one(g, NX, NY, NZ, ix, iy, iz, c, mf, mg, STREAM_REAL, 1.0, 1.0, Mout, absorbed, st);
+                stream_one(g, NX, NY, NZ, ix, iy, iz, c, mf, mg, STREAM_REAL, 0, 1.0, 1.0, Mout, absorbed, st);
             }
-            if (absorbed[0] > 0.0 || absorbed[1] > 0.0) {
-                /* Eq. (IIIB13)-(IIIB15) for a stationary no-slip wall: the image
-                 * populations are the cell's own (u_n = u, Eq. IIIB11) launched with
-                 * -c_i; those whose path touches the no-slip wall enter the domain,
-                 * scaled so that their mass equals what the wall absorbed. */
+            for (int n = 1; n <= 2; n++) {
+                double* dm = absorbed + 2 * (n - 1);
+                if (!(dm[0] > 0.0 || dm[1] > 0.0)) continue;
+                /* Eq. (IIIB10)-(IIIB15): the image populations of boundary n are the EPR
+                 * populations of the cell's post-collision central moments at the bulk
+                 * velocity u_n = u - 2 u_w (Eq. IIIB11; both components: no slip),
+                 * launched with -c_i; those whose last no-slip contact is boundary n enter
+                 * the domain, scaled so that their mass equals what boundary n absorbed.
+                 * At rest (u_w = 0) they are the cell's own populations. */
+                int qi = q;
+                orc_point* ipts = pts;
+                double *ipf = popf, *ipg = popg;
+                if (n == 2) {
+                    orc_collision cn = co;
+                    for (int a = 0; a < D; a++) cn.u[a] = co.u[a] - 2.0 * g->wall_u[a];
+                    if (icap < cap) {
+                        icap = cap;
+                        imp = (orc_point*)realloc(imp, sizeof(orc_point) * icap);
+                        imf = (double*)realloc(imf, sizeof(double) * icap);
+                        img = (double*)realloc(img, sizeof(double) * icap);
+                    }
+                    qi = orc_las(D, cn.u, co.RT, p, imp, icap);
+                    if (qi < 0) {
+                        icap = -qi;
+                        imp = (orc_point*)realloc(imp, sizeof(orc_point) * icap);
+                        imf = (double*)realloc(imf, sizeof(double) * icap);
+                        img = (double*)realloc(img, sizeof(double) * icap);
+                        qi = orc_las(D, cn.u, co.RT, p, imp, icap);
+                    }
+                    solve_cell(p, qi, imp, &cn, imf, img, NULL);
+                    ipts = imp;
+                    ipf = imf;
+                    ipg = img;
+                }
                 double kept[2] = {0.0, 0.0};
                 for (int pass = 0; pass < 2; pass++) {
-                    double sf = kept[0] > 0.0 ? absorbed[0] / kept[0] : 0.0;
-                    double sg = kept[1] > 0.0 ? absorbed[1] / kept[1] : 0.0;
-                    for (int k = 0; k < q; k++) {
-                        double cm[ORC_MAXD] = {-pts[k].c[0], -pts[k].c[1], -pts[k].c[2]};
-                        double mf = mscale * popf[k], mg = p->K > 0.0 ? gscale * popg[k] : 0.0;
-                        stream_one(g, NX, NY, NZ, ix, iy, iz, cm, mf, mg, pass == 0 ? STREAM_IMAGE_SUM : STREAM_IMAGE_PUT,
-                                   sf, sg, Mout, kept, st);
+                    double sf = kept[0] > 0.0 ? dm[0] / kept[0] : 0.0;
+                    double sg = kept[1] > 0.0 ? dm[1] / kept[1] : 0.0;
+                    for (int k = 0; k < qi; k++) {
+                        double cm[ORC_MAXD] = {-ipts[k].c[0], -ipts[k].c[1], -ipts[k].c[2]};
+                        double mf = mscale * ipf[k], mg = p->K > 0.0 ? gscale * ipg[k] : 0.0;
+                        stream_one(g, NX, NY, NZ, ix, iy, iz, cm, mf, mg,
+                                   pass == 0 ? STREAM_IMAGE_SUM : STREAM_IMAGE_PUT, n, sf, sg, Mout, kept, st);
                     }
                 }
                 /* reading: no image reaches the domain (a cell boxed in by walls): the
@@ -1008,14 +1058,17 @@ int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* 
                 int syi = D >= 2 ? land_axis(iy, ny, py, g->periodic[1]) : 0;
                 if (sxi >= 0 && syi >= 0) {
                     long self = ((long)iz * NY + iy) * NX + ix;
-                    if (kept[0] <= 0.0) Mout[self] += absorbed[0];
-                    if (kept[1] <= 0.0) Mout[(long)iG0(D) * ncell + self] += absorbed[1];
+                    if (kept[0] <= 0.0) Mout[self] += dm[0];
+                    if (kept[1] <= 0.0) Mout[(long)iG0(D) * ncell + self] += dm[1];
                 }
             }
         }
     free(pts);
     free(popf);
     free(popg);
+    free(imp);
+    free(imf);
+    free(img);
     free(W);
     return 0;
 }

@@ -131,8 +131,10 @@ static int validate(const lelbm_params* p) {
         const int qx = p->bc[0] == LELBM_BC_PERIODIC ? 0 : p->pad, qy = p->bc[2] == LELBM_BC_PERIODIC ? 0 : p->pad;
         const long long nc = (long long)(p->nx + 2 * qx) * (p->ny + 2 * qy);
         for (long long i = 0; i < nc; i++)
-            if (p->solid[i] == 2) return fail(nullptr, LELBM_E_INVAL, "no-slip walls need the FP64 path");
+            if (p->solid[i] >= 2) return fail(nullptr, LELBM_E_INVAL, "no-slip walls need the FP64 path");
     }
+    if (!std::isfinite(p->wall_u[0]) || !std::isfinite(p->wall_u[1]))
+        return fail(nullptr, LELBM_E_INVAL, "wall_u must be finite");
     if (p->deterministic && (p->dims != 2 || p->precision != LELBM_FP64 || p->solid))
         return fail(nullptr, LELBM_E_INVAL, "deterministic streaming needs a 2D FP64 grid without solid cells");
     if (p->dims == 3) {
@@ -456,7 +458,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
                 const bool iny = iy >= py && iy < py + p->ny;
                 if (inx && iny) {
                     type[cell] = (p->solid && p->solid[cell]) ? CELL_SOLID : CELL_FLUID;
-                    noslip[cell] = (p->solid && p->solid[cell] == 2) ? 1 : 0;
+                    noslip[cell] = (p->solid && (p->solid[cell] == 2 || p->solid[cell] == 3)) ? p->solid[cell] - 1 : 0;
                     continue;
                 }
                 bool inflow = false;
@@ -476,7 +478,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
                         // the wall continues through an outflow pad whose nearest interior
                         // cell is solid (instead of the pad copying an empty state)
                         type[cell] = CELL_SOLID;
-                        noslip[cell] = p->solid[src] == 2 ? 1 : 0;
+                        noslip[cell] = (p->solid[src] == 2 || p->solid[src] == 3) ? p->solid[src] - 1 : 0;
                         continue;
                     }
                     type[cell] = CELL_PAD_OUT;
@@ -490,6 +492,8 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     g.NX = h->NX;
     g.NY = h->NY;
     g.ncell = h->ncell;
+    g.wall_u[0] = p->wall_u[0];
+    g.wall_u[1] = p->wall_u[1];
     g.inst_of_cell = h->d_inst;
     g.inst_lo = h->d_inst_lo;
     g.inst_n = h->d_inst_n;
@@ -507,7 +511,7 @@ extern "C" int lelbm_create(lelbm_t* out, const lelbm_params* p) {
     if (!rc && D == 2 && std::find(type.begin(), type.end(), (uint8_t)CELL_SOLID) != type.end()) {
         rc = upload(h, &h->d_wall_dist, wall_distance(type, h->NX, h->NY, g.periodic[0], g.periodic[1]));
         g.wall_dist = h->d_wall_dist;
-        if (!rc && std::find(noslip.begin(), noslip.end(), (uint8_t)1) != noslip.end()) {
+        if (!rc && std::any_of(noslip.begin(), noslip.end(), [](uint8_t v) { return v != 0; })) {
             rc = upload(h, &h->d_noslip, noslip);
             g.noslip = h->d_noslip;
         }

@@ -90,8 +90,9 @@ struct Geometry {
     const int* inst_n;           // 1D: interior length of each instance
     const uint8_t* wall_dist;    // 2D with solids: Chebyshev distance (cells) from each
                                  // cell to the nearest solid cell, capped at 255; else null
-    const uint8_t* noslip;       // 2D with no-slip walls: 1 on every solid cell that is a
-                                 // stationary no-slip wall (0: slip wall); null if none
+    const uint8_t* noslip;       // 2D with no-slip walls: per solid cell 1 for a no-slip wall
+                                 // at rest, 2 for one moving at wall_u (0: slip wall); null if none
+    double wall_u[2];            // velocity u_w of the moving no-slip walls (Eq. IIIB2-IIIB4)
 };
 
 // Padded 3D grid: cell = (iz * NY + iy) * NX + ix; p* = pad layers of each axis (0 on a

@@ -75,7 +75,7 @@ __device__ __forceinline__ bool solid_at(const Geometry& g, const uint8_t* type,
 }
 
 // Contact bit of padded cell (i, j) for a path that reflects off it: 1 for a slip wall, 2
-// for a no-slip wall, 0 for a cell that is not solid.
+// for a no-slip wall at rest, 4 for a moving no-slip wall, 0 for a cell that is not solid.
 __device__ __forceinline__ int wall_bit(const Geometry& g, const uint8_t* type, int i, int j) {
     if (g.periodic[0]) {
         i %= g.NX;
@@ -88,8 +88,10 @@ __device__ __forceinline__ int wall_bit(const Geometry& g, const uint8_t* type, 
     if (i < 0 || i >= g.NX || j < 0 || j >= g.NY) return 0;
     const long long k = (long long)j * g.NX + i;
     if (type[k] != CELL_SOLID) return 0;
-    return (g.noslip && g.noslip[k]) ? 2 : 1;
+    return g.noslip ? (g.noslip[k] == 1 ? 2 : (g.noslip[k] == 2 ? 4 : 1)) : 1;
 }
+// The no-slip boundary of a contact bit: 1 at rest, 2 moving, 0 none.
+__device__ __forceinline__ int noslip_of_bit(int b) { return b == 2 ? 1 : (b == 4 ? 2 : 0); }
 
 // End of the path x -> x + c past solid cells: the path is walked face by face and at
 // a face of a solid cell the velocity component normal to it is reversed (specular
@@ -103,7 +105,9 @@ struct WallLanding {
     int i, j;        // final (fluid) cell, unwrapped padded coordinates
     double off[2];   // landing point relative to its centre, each in (-1/2, 1/2]
     double cs[2];    // reflected velocity c*
-    int touched;     // walls the path reflected off: bit 1 slip, bit 2 no-slip (0: none)
+    int touched;     // walls the path reflected off: bit 1 slip, bit 2 no-slip at rest, bit 4
+                     // moving no-slip (0: none)
+    int last_ns;     // the last no-slip boundary it touched: 1 at rest, 2 moving, 0 none
 };
 
 __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8_t* type, int ix, int iy,
@@ -113,7 +117,7 @@ __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8
     int sx = (qx > 0) - (qx < 0), sy = (qy > 0) - (qy < 0);
     const long long ax = qx < 0 ? -qx : qx, ay = qy < 0 ? -qy : qy;
     int i = ix, j = iy;
-    int touched = 0;
+    int touched = 0, last_ns = 0;
     long long kx = 0, ky = 0;
     while (true) {
         const long long Xn = S / 2 + S * kx, Yn = S / 2 + S * ky;
@@ -134,14 +138,19 @@ __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8
                 const int ba = wall_bit(g, type, i + sx, j), bb = wall_bit(g, type, i, j + sy);
                 if (ba && !bb) {
                     touched |= ba;
+                    if (noslip_of_bit(ba)) last_ns = noslip_of_bit(ba);
                     sx = -sx;
                     j += sy;
                 } else if (bb && !ba) {
                     touched |= bb;
+                    if (noslip_of_bit(bb)) last_ns = noslip_of_bit(bb);
                     sy = -sy;
                     i += sx;
                 } else {
                     touched |= bd | ba | bb;
+                    // a corner: the diagonal cell, else a side cell, names the boundary
+                    const int k = noslip_of_bit(bd) ? bd : (noslip_of_bit(ba) ? ba : bb);
+                    if (noslip_of_bit(k)) last_ns = noslip_of_bit(k);
                     sx = -sx;
                     sy = -sy;
                 }
@@ -153,6 +162,7 @@ __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8
                 if (stx) sx = -sx;
                 if (sty) sy = -sy;
                 touched |= bt;
+                if (noslip_of_bit(bt)) last_ns = noslip_of_bit(bt);
             } else {
                 i = ti;
                 j = tj;
@@ -169,6 +179,7 @@ __device__ __forceinline__ WallLanding trace_path(const Geometry& g, const uint8
     L.cs[0] = (double)sx * fabs(c[0]);
     L.cs[1] = (double)sy * fabs(c[1]);
     L.touched = touched;
+    L.last_ns = last_ns;
     return L;
 }
 
@@ -185,14 +196,15 @@ __device__ __forceinline__ void add_moments_2d(double* Mout, long long ncell, lo
 
 // How stream_traced treats a population (Sec. III.B, Eq. IIIB8-IIIB15):
 //   kStreamReal: a population of the cell.  Its path reflects specularly at slip walls; a
-//     path that touches a no-slip wall is absorbed (acc += mf, mg: the Delta m of Eq.
-//     IIIB8), as is a cloud-in-cell share that would fall on a no-slip cell; a share that
-//     would fall on a slip cell is mirrored back across the wall.
-//   kStreamImageSum / kStreamImagePut: an image population of a no-slip wall (cp is the
-//     reversed velocity -c_i, Eq. IIIB13).  Only a path that touches a no-slip wall enters
-//     the domain, and shares that would fall on a solid cell are dropped; _Sum adds the
-//     mass that enters to acc (Eq. IIIB14), _Put deposits it scaled by sf and sg (Eq.
-//     IIIB15).
+//     path that touches a no-slip wall is absorbed by the last no-slip boundary n it
+//     touched (acc[2(n-1)] += mf, acc[2(n-1)+1] += mg: the Delta m of Eq. IIIB8; n = 1 at
+//     rest, 2 moving), as is a cloud-in-cell share that would fall on a no-slip cell; a
+//     share that would fall on a slip cell is mirrored back across the wall.
+//   kStreamImageSum / kStreamImagePut: an image population of no-slip boundary sel (cp is
+//     the reversed velocity -c_i, Eq. IIIB13).  Only a path whose last no-slip contact is
+//     sel enters the domain, and shares that would fall on a solid cell are dropped; _Sum
+//     adds the mass that enters to acc[0..1] (Eq. IIIB14), _Put deposits it scaled by sf
+//     and sg (Eq. IIIB15).
 enum : int { kStreamReal = 0, kStreamImageSum = 1, kStreamImagePut = 2 };
 
 // Streams one population of cell (ix, iy) with velocity cp past the solid cells (2D):
@@ -205,16 +217,17 @@ enum : int { kStreamReal = 0, kStreamImageSum = 1, kStreamImagePut = 2 };
 // this path.
 static __device__ __noinline__ int stream_traced(const Geometry& g, const uint8_t* type, double* Mout, int ix, int iy,
                                                  const double* cp, double mf, double mg, int mode = kStreamReal,
-                                                 double* acc = nullptr, double sf = 1.0, double sg = 1.0) {
+                                                 double* acc = nullptr, double sf = 1.0, double sg = 1.0,
+                                                 int sel = 0) {
     const WallLanding L = trace_path(g, type, ix, iy, cp);
     const bool noslip = acc != nullptr;
     if (noslip) {
-        if (mode == kStreamReal && (L.touched & 2)) {
-            acc[0] += mf;
-            acc[1] += mg;
+        if (mode == kStreamReal && L.last_ns) {
+            acc[2 * (L.last_ns - 1)] += mf;
+            acc[2 * (L.last_ns - 1) + 1] += mg;
             return L.touched;
         }
-        if (mode != kStreamReal && !(L.touched & 2)) return L.touched;
+        if (mode != kStreamReal && L.last_ns != sel) return L.touched;
     }
     const double pos[2] = {(double)L.i + L.off[0], (double)L.j + L.off[1]};
     int base[2];
@@ -234,9 +247,10 @@ static __device__ __noinline__ int stream_traced(const Geometry& g, const uint8_
             const int kind = wall_bit(g, type, tx, ty);
             if (kind && noslip) {
                 if (mode != kStreamReal) continue;
-                if (kind == 2) {
-                    acc[0] += w * mf;
-                    acc[1] += w * mg;
+                const int n = noslip_of_bit(kind);
+                if (n) {
+                    acc[2 * (n - 1)] += w * mf;
+                    acc[2 * (n - 1) + 1] += w * mg;
                     continue;
                 }
             }

@@ -447,45 +447,93 @@ __device__ __forceinline__ void scatter_cell32(const Model& m, const Geometry& g
 // and <= 2 (phonons) of the deposited populations and returns whether their
 // residual against conF / conG is within the tolerance (the FP64 judge of the
 // mixed path).  sign = -1 removes a previous deposit of the same populations.
-// Image populations of a stationary no-slip wall (Sec. III.B, Eq. IIIB13-IIIB15) for a cell
-// whose streaming gave the wall the mass absorbed[0] (f) and energy absorbed[1] (g).  With
-// u_w = 0 the image moments are the cell's own (u_n = u, Eq. IIIB11), so the images are the
-// cell's populations launched with -c_i; those whose path touches the no-slip wall enter the
-// domain, scaled so that they carry exactly what the wall absorbed: one pass sums what
+// Image populations of the no-slip walls (Sec. III.B, Eq. IIIB10-IIIB15) for a cell whose
+// streaming gave no-slip boundary n (1 at rest, 2 moving at u_w) the mass absorbed[2(n-1)]
+// (f) and the phonon energy absorbed[2(n-1)+1] (g).  The images of boundary n are the EPR
+// populations of the cell's post-collision central constraints (conF, conG) at the bulk
+// velocity u_n = u - 2 u_w (Eq. IIIB11, both components), launched with -c_i; at rest they
+// are the cell's own populations.  Those whose last no-slip contact is boundary n enter the
+// domain, scaled so that they carry exactly what the boundary absorbed: one pass sums what
 // enters, a second deposits it.  If nothing enters (a cell boxed in by walls) the absorbed
 // mass and internal energy stay in the cell, at rest.
 static __device__ __noinline__ void noslip_images(const Model& m, const Geometry& g, const uint8_t* type, double* Mout,
                                                   long long cell, int ix, int iy, const CellState<2>& c,
-                                                  const Stencil<2>& st, const double* lf, const double* lg, double mfs,
-                                                  double mgs, const double* absorbed) {
+                                                  const Stencil<2>& st, const double* lf, const double* lg,
+                                                  const double* conF, const double* conG, double mfs, double mgs,
+                                                  const double* absorbed) {
     const bool has_g = m.K > 0.0;
-    double kept[2] = {0.0, 0.0}, unused[2] = {0.0, 0.0};
-    for (int pass = 0; pass < 2; pass++) {
-        const double sf = kept[0] > 0.0 ? absorbed[0] / kept[0] : 0.0;
-        const double sg = kept[1] > 0.0 ? absorbed[1] / kept[1] : 0.0;
-        auto image = [&](const double* cp, double dC) {
-            const double t[2] = {(cp[0] - c.u[0]) * c.inv_sig, (cp[1] - c.u[1]) * c.inv_sig};
-            double T[10];
-            Basis<2, true>::eval(t, T);
-            double ef = 1.0;
+    for (int n = 1; n <= 2; n++) {
+        const double* dm = absorbed + 2 * (n - 1);
+        if ((dm[0] == 0.0 && dm[1] == 0.0) || (n == 2 && !conF)) continue;
+        CellState<2> ci = c;
+        Stencil<2> si = st;
+        double li_f[10], li_g[6];
 #pragma unroll
-            for (int j = 0; j < 10; j++) ef += lf[j] * T[j];
-            double gp = 0.0;
-            if (has_g) {
-                double eg = 1.0;
+        for (int j = 0; j < 10; j++) li_f[j] = lf[j];
 #pragma unroll
-                for (int j = 0; j < 6; j++) eg += lg[j] * T[j];
-                gp = dC * exp(-eg);
+        for (int j = 0; j < 6; j++) li_g[j] = lg[j];
+        if (n == 2) {  // the EPR at u_n, with the fallbacks of a failed solve
+            ci.u[0] = c.u[0] - 2.0 * g.wall_u[0];
+            ci.u[1] = c.u[1] - 2.0 * g.wall_u[1];
+            si.init(ci, m);
+            unsigned int pf = 0, pg = 0;
+            int sf, sg;
+            solve_fg<2>(ci, si, conF, conG, has_g, li_f, li_g, m, sf, sg, pf, pg);
+            if (sf < 0 || sg < 0) {
+                maxwell_start_fg<2, 10, 6>(ci.RT, li_f, li_g);
+                solve_fg<2>(ci, si, conF, conG, has_g, li_f, li_g, m, sf, sg, pf, pg);
             }
-            const double cm[2] = {-cp[0], -cp[1]};
-            stream_traced(g, type, Mout, ix, iy, cm, mfs * (dC * exp(-ef)), mgs * gp,
-                          pass == 0 ? kStreamImageSum : kStreamImagePut, pass == 0 ? kept : unused, sf, sg);
-        };
-        st.for_each(image);
-    }
-    if (type[cell] == CELL_FLUID) {
-        if (kept[0] <= 0.0 && absorbed[0] != 0.0) atomicAdd(Mout + cell, absorbed[0]);
-        if (kept[1] <= 0.0 && absorbed[1] != 0.0) atomicAdd(Mout + (long long)iG0<2>() * g.ncell + cell, absorbed[1]);
+            if (sf < 0 || sg < 0) {
+                double ef[10], eg[6];
+#pragma unroll
+                for (int j = 0; j < 10; j++) ef[j] = (j == 0 || j == 3 || j == 5) ? 1.0 : 0.0;
+#pragma unroll
+                for (int j = 0; j < 6; j++) eg[j] = (j == 0 || j == 3 || j == 5) ? 1.0 : 0.0;
+                maxwell_start_fg<2, 10, 6>(ci.RT, li_f, li_g);
+                solve_fg<2>(ci, si, ef, eg, has_g, li_f, li_g, m, sf, sg, pf, pg);
+                if (sf < 0 || sg < 0) {  // normalised Maxwellian weights, f and g alike
+#pragma unroll
+                    for (int j = 0; j < 10; j++) li_f[j] = (j == 3 || j == 5) ? 0.5 : 0.0;
+                    double S = 0.0;
+                    auto sum = [&](const double* cp, double dC) {
+                        const double tx = (cp[0] - ci.u[0]) * ci.inv_sig, ty = (cp[1] - ci.u[1]) * ci.inv_sig;
+                        S += dC * exp(-0.5 * (tx * tx + ty * ty));
+                    };
+                    si.for_each(sum);
+                    li_f[0] = log(S) - 1.0;
+#pragma unroll
+                    for (int j = 0; j < 6; j++) li_g[j] = li_f[j];
+                }
+            }
+        }
+        double kept[2] = {0.0, 0.0}, unused[2] = {0.0, 0.0};
+        for (int pass = 0; pass < 2; pass++) {
+            const double sf = kept[0] > 0.0 ? dm[0] / kept[0] : 0.0;
+            const double sg = kept[1] > 0.0 ? dm[1] / kept[1] : 0.0;
+            auto image = [&](const double* cp, double dC) {
+                const double t[2] = {(cp[0] - ci.u[0]) * ci.inv_sig, (cp[1] - ci.u[1]) * ci.inv_sig};
+                double T[10];
+                Basis<2, true>::eval(t, T);
+                double ef = 1.0;
+#pragma unroll
+                for (int j = 0; j < 10; j++) ef += li_f[j] * T[j];
+                double gp = 0.0;
+                if (has_g) {
+                    double eg = 1.0;
+#pragma unroll
+                    for (int j = 0; j < 6; j++) eg += li_g[j] * T[j];
+                    gp = dC * exp(-eg);
+                }
+                const double cm[2] = {-cp[0], -cp[1]};
+                stream_traced(g, type, Mout, ix, iy, cm, mfs * (dC * exp(-ef)), mgs * gp,
+                              pass == 0 ? kStreamImageSum : kStreamImagePut, pass == 0 ? kept : unused, sf, sg, n);
+            };
+            si.for_each(image);
+        }
+        if (type[cell] == CELL_FLUID) {
+            if (kept[0] <= 0.0 && dm[0] != 0.0) atomicAdd(Mout + cell, dm[0]);
+            if (kept[1] <= 0.0 && dm[1] != 0.0) atomicAdd(Mout + (long long)iG0<2>() * g.ncell + cell, dm[1]);
+        }
     }
 }
 
@@ -548,7 +596,8 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
 #pragma unroll
         for (int mm = 0; mm < NM; mm++) atomicAdd(Mout + mm * g.ncell + tgt, dM[mm]);
     };
-    double absorbed[2] = {0.0, 0.0};  // Eq. (IIIB8): what no-slip walls took, f and g
+    double absorbed[4] = {0.0, 0.0, 0.0, 0.0};  // Eq. (IIIB8): what the no-slip walls took (f, g;
+                                                // at rest, moving)
     auto deposit_traced = [&](const double* cp, double mf, double mg) {
         if constexpr (D == 2)
             walls += stream_traced(g, type, Mout, ix, iy, cp, mf, mg, kStreamReal, g.noslip ? absorbed : nullptr)
@@ -646,8 +695,8 @@ __device__ __forceinline__ bool scatter_cell(const Model& m, const Geometry& g, 
     };
     st.for_each_row(row, leaf);
     if constexpr (D == 2) {
-        if (absorbed[0] != 0.0 || absorbed[1] != 0.0)
-            noslip_images(m, g, type, Mout, cell, ix, iy, c, st, lf, lg, mfs, mgs, absorbed);
+        if (absorbed[0] != 0.0 || absorbed[1] != 0.0 || absorbed[2] != 0.0 || absorbed[3] != 0.0)
+            noslip_images(m, g, type, Mout, cell, ix, iy, c, st, lf, lg, conF, conG, mfs, mgs, absorbed);
     }
     if (q > ls.q_max) ls.q_max = q;
     ls.points += q;
@@ -860,7 +909,7 @@ __device__ __forceinline__ void fp64_tail(const Model& m, const Geometry& g, con
         if (q > ls.q_max) ls.q_max = q;
         return;
     }
-    scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls);
+    scatter_cell<D, false>(m, g, type, Mout, cell, c, st, lf, lg, ls, 1.0, conF, conG);
 }
 
 struct TailCounts {

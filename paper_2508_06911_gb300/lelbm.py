@@ -52,6 +52,7 @@ class lelbm_params(ctypes.Structure):
         ("bc_z", ctypes.c_int * 2),
         ("inlet_uz", ctypes.c_double),
         ("deterministic", ctypes.c_int),
+        ("wall_u", ctypes.c_double * 2),
     ]
 
 

@@ -399,3 +399,48 @@ def test_noslip_channel_shear_mode_decays_at_viscous_rate():
     r16 = channel_decay_rate(16, 200, nu) / (nu * (np.pi / 16) ** 2)
     assert abs(r32 - 1) < 0.10
     assert abs(r16 - 1) > 1.6 * abs(r32 - 1)
+
+
+# --- moving no-slip walls (kind 3, velocity u_w; Eq. IIIB2-IIIB4, IIIB10-IIIB11) ---------
+
+def channel_state(kbot, ktop, wall_u, u0, H=16, nx=4, RT=0.5, nu=0.1):
+    ny = H + 2
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0], solid[-1] = kbot, ktop
+    g = O.grid(2, nx, ny, periodic=(True, True), solid=solid.reshape(-1), wall_u=wall_u)
+    p = O.params(2, 3.0, nu_s=nu, Pr=0.71, limiter=0)
+    u = np.zeros((2, ny, nx))
+    u[0] = u0
+    M = O.state_from_primitives(g, p, np.ones((ny, nx)), u, np.full((ny, nx), RT))
+    fl = (solid == 0).reshape(-1)
+    M[:, ~fl] = 0.0
+    return g, p, M, fl, ny, nx
+
+
+def test_walls_moving_with_a_uniform_stream_leave_it_uniform():
+    """No-slip walls moving at the stream's own velocity impose nothing: the image
+    populations (bulk velocity -u + 2 u_w = u, Eq. IIIB4) replace exactly what the walls
+    absorbed, so the stream stays uniform; walls at rest slow it down."""
+    g, p, M0, fl, _, _ = channel_state(3, 3, (0.3, 0.0), 0.3)
+    M = O.run(g, p, M0, 4)
+    dev = np.abs(M[:, fl] - M0[:, fl]).max() / np.abs(M0[:, fl]).max()
+    assert dev < 1e-13
+    assert abs(M[0, fl].sum() / M0[0, fl].sum() - 1) < 1e-13
+    g2, p2, N0, _, _, _ = channel_state(2, 2, (0.0, 0.0), 0.3)
+    N = O.run(g2, p2, N0, 4)
+    assert N[1, fl].sum() < 0.99 * N0[1, fl].sum()
+
+
+def test_couette_flow_profile_is_linear_between_the_walls():
+    """Plane Couette flow: a wall at rest below (kind 2) and a wall moving at U above (kind 3).
+    The steady velocity profile is linear, 0 at the lower wall face (y = 1) and U at the upper
+    one (y = H + 1), each within a fifth of a cell; residuals below 0.1 % of U."""
+    U, H = 0.05, 16
+    g, p, M, fl, ny, nx = channel_state(2, 3, (U, 0.0), 0.0, H=H, nu=0.2)
+    M = O.run(g, p, M, 1500)
+    ux = (M[1, fl] / M[0, fl]).reshape(H, nx).mean(1)
+    y = np.arange(1, H + 1) + 0.5
+    a, b = np.polyfit(y, ux, 1)
+    assert abs(-b / a - 1.0) < 0.2
+    assert abs((U - b) / a - (H + 1.0)) < 0.2
+    assert np.abs(ux - (a * y + b)).max() < 1e-3 * U
