@@ -78,6 +78,12 @@ def parse():
     ap.add_argument("--mlp-gate", type=float, default=1e-3,
                     help="timed path: learned start only for cells whose constraints depart from equilibrium "
                          "by at least this much (0: every cell); the FP64 comparison runs use the network everywhere")
+    ap.add_argument("--full-run", action="store_true",
+                    help="run the workload's whole configured step count on the timed path and on the "
+                         "plain FP64 path from the same state; report both MLUPS and the final L1 density "
+                         "difference (one JSON line, metric: L1 after the full run)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="FP64 2D path: moment streaming as a fixed-order gather (no atomics)")
     ap.add_argument("--per-step", action="store_true", help="1D batch: one launch per step instead of the "
                     "persistent batch kernel")
     ap.add_argument("--no-e2e", action="store_true")
@@ -370,6 +376,8 @@ def run_ours(args):
 
     def make(precision, start):
         kw = dict(stream=stream.cuda_stream, precision=prec[precision])
+        if args.deterministic and precision == "fp64":
+            kw["deterministic"] = 1
         s_ = Solver.riemann1d(w, **kw) if D == 1 else (Solver.grid2d(w, **kw) if D == 2 else Solver.grid3d(w, **kw))
         if start == "learned" and weights is not None:
             L.lelbm_set_mlp(s_.h, weights)
@@ -502,13 +510,16 @@ def run_ours(args):
                                    if dram else None),
                 "peak_source": main_side["peak_source"],
                 "kernel": (f"batch_persistent_kernel<{prec_id}>" if persistent else
-                           ("cell3d_kernel" if D == 3 else f"cell_update_kernel<{D},{prec_id}>")),
+                           ("cell3d_kernel" if D == 3 else f"cell_update_kernel<{D},{prec_id}>")
+                           + (" + gather2d_kernel" if args.deterministic and args.precision == "fp64" else "")),
                 "kernel_ms": kern_ms, "steps_per_launch": steps_per_launch, **other_side,
                 "hbm": {"achieved_gbs": alg_bytes / sec / 1e9, "peak_gbs": hbm_peak,
                         "frac": alg_bytes / sec / 1e9 / hbm_peak,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}}
-    # per step: pad fill (padded grids), the warm-start network (learned start), the cell update
-    launches_per_step = 1 + (s.n_cells > interior) + (args.warmstart == "learned" and weights is not None)
+    # per step: pad fill (padded grids), the warm-start network (learned start), the cell update,
+    # the gather (deterministic streaming)
+    launches_per_step = (1 + (s.n_cells > interior) + (args.warmstart == "learned" and weights is not None)
+                         + (args.deterministic and args.precision == "fp64"))
     hist = list(st.newton_hist)
     solves = sum(hist)
     mean_updates = sum(i * h for i, h in enumerate(hist)) / max(solves, 1)
@@ -535,6 +546,8 @@ def run_ours(args):
         cpu = cpu_baseline(args)
 
     if rank == 0:
+        if args.deterministic and args.precision == "fp64":
+            desc["streaming"] = "deterministic gather"
         desc.update({"precision": args.precision, "l2": f"inputs larger than L2 (state {state_bytes / 1e6:.0f} MB x 2 buffers)"
                      if 2 * state_bytes > 129e6 else "state fits in L2",
                      "parallelism": f"{world} independent replica(s)" if world > 1 else "single GPU"})
@@ -563,10 +576,69 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_full(args):
+    """The workload's whole run (its configured step count) on the timed path and on the plain
+    FP64 path (Eq. IID13 start) from the same initial state: MLUPS of each and the relative L1
+    density difference between the two final states (the accuracy half of the metric)."""
+    import torch
+
+    from paper_2508_06911_gb300 import build as B, lelbm as L
+    from paper_2508_06911_gb300.solver import Solver
+
+    torch.cuda.set_device(0)
+    B.build()
+    w, desc = make_workload(args, 0)
+    D = desc["dims"]
+    if D != 2:
+        raise SystemExit("--full-run covers the 2D workloads")
+    nsteps = int(w.steps)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = {"fp32": L.LELBM_FP32, "mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
+    wname = "warmstart_2d_config3.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
+    wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", wname)
+    res = {}
+    rho = {}
+    for name, precision, start in (("timed", args.precision, args.warmstart), ("fp64", "fp64", "maxwell")):
+        kw = dict(stream=stream.cuda_stream, precision=prec[precision])
+        s = Solver.grid2d(w, **kw)
+        if start == "learned" and os.path.exists(wpath):
+            L.lelbm_set_mlp(s.h, np.load(wpath))
+            if precision != "fp64":
+                L.lelbm_set_mlp_gate(s.h, args.mlp_gate)
+        if start == "stored":
+            s.set_warmstart(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = 0
+        while done < nsteps:  # in chunks, so that a very long run is not one enqueue
+            k = min(500, nsteps - done)
+            s.step(k)
+            done += k
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = s.stats()
+        res[name] = {"precision": precision, "warmstart": start, "steps": nsteps, "seconds": ms / 1e3,
+                     "value": desc["interior_cells"] * nsteps / (ms / 1e3) / 1e6, "status": L.STATUS.get(s.synchronize()),
+                     "fallback_mx": st.fallback_mx, "judge_redo": st.judge_redo}
+        rho[name] = s.get_moments()[0]
+        s.close()
+    l1 = float(np.abs(rho["timed"] - rho["fp64"]).sum() / np.abs(rho["fp64"]).sum())
+    desc.update({"precision": args.precision, "steps": nsteps})
+    print(json.dumps({"metric": "relative L1 density difference from the plain FP64 path after the full run",
+                      "value": l1, "unit": "relative", "n_gpus": 1, "higher_is_better": False,
+                      "data": "synthetic (seeded)", "config": desc, "runs": res,
+                      "speedup_vs_fp64": res["timed"]["value"] / res["fp64"]["value"]}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.full_run:
+        run_full(args)
     else:
         run_ours(args)
 
