@@ -52,6 +52,9 @@ __device__ __forceinline__ int mon_index(int a, int b, int c, int P) {
     return idx + a;
 }
 
+// Position of y^b z^c (b + c <= 6) in a row's table of transverse monomials.
+__device__ __forceinline__ int yz_index(int b, int c) { return c * 7 - c * (c - 1) / 2 + b; }
+
 // One run of stencil points: c = (x + k h, y, z) for k = 0..n-1, h = 2^-level, all in
 // units of 1/64 cell; dC = 2^(-3 level) (Eq. IIC11).
 struct Item3 {
@@ -61,7 +64,7 @@ struct Item3 {
 struct Warp3 {
     Item3 items[kW3Items];
     double S[32][12];     // row sums of a chunk: fluon x^0..6, phonon x^0..4
-    double YZ[32][14];    // y^0..6 and z^0..6 of the chunk's rows (thermal units)
+    double YZ[32][28];    // y^b z^c (b + c <= 6) of the chunk's rows (thermal units), yz_index
     double MF[kMF3];      // population moments of the fluons
     double MG[kMG3];      // and of the phonons
     double A[kNF3 * kNF3];
@@ -270,23 +273,34 @@ __device__ void moment_pass3(Warp3* w, const CellState<3>& c, int n_items, bool 
             for (int a = 0; a < 7; a++) w->S[lane][a] = Sf[a];
 #pragma unroll
             for (int a = 0; a < 5; a++) w->S[lane][7 + a] = Sg[a];
-            double yp = 1.0, zp = 1.0;
+            // the row's transverse monomials, once per row (the lanes then need one product
+            // per monomial and row)
+            double yp[7];
+            yp[0] = 1.0;
 #pragma unroll
-            for (int k = 0; k < 7; k++) {
-                w->YZ[lane][k] = yp;
-                w->YZ[lane][7 + k] = zp;
-                yp *= gi.ty;
+            for (int k = 1; k < 7; k++) yp[k] = yp[k - 1] * gi.ty;
+            double zp = 1.0;
+#pragma unroll
+            for (int cz = 0; cz < 7; cz++) {
+#pragma unroll
+                for (int b = 0; b + cz < 7; b++) w->YZ[lane][yz_index(b, cz)] = yp[b] * zp;
                 zp *= gi.tz;
             }
         }
         __syncwarp();
         const int nr = n_items - base < 32 ? n_items - base : 32;
+        bool act[4];
+        int si[4], yi[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            act[k] = k < nown && ((msel[k] == 0 && doF) || (msel[k] == 1 && doG));
+            si[k] = k < nown ? (msel[k] ? 7 : 0) + ma[k] : 0;
+            yi[k] = k < nown ? yz_index(mb[k], mcz[k]) : 0;
+        }
         for (int r = 0; r < nr; r++) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (k < nown && ((msel[k] == 0 && doF) || (msel[k] == 1 && doG)))
-                    acc[k] += w->S[r][(msel[k] ? 7 : 0) + ma[k]] * (w->YZ[r][mb[k]] * w->YZ[r][7 + mcz[k]]);
-            }
+            for (int k = 0; k < 4; k++)
+                if (act[k]) acc[k] = fma(w->S[r][si[k]], w->YZ[r][yi[k]], acc[k]);
         }
         __syncwarp();
     }
