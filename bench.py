@@ -358,9 +358,9 @@ def run_ours(args):
     prec = {"fp32": L.LELBM_FP32, "mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
 
     weights = None
-    # the four-quadrant workload uses the network trained along the config-3 run (the same
+    # the four-quadrant workload uses the network trained along the 2000-step 1024^2 run (the same
     # generator at 1024^2), the others the network trained on diverse 2D states
-    wname = "warmstart_2d_config3.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
+    wname = "warmstart_2d_quadrants.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
     wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", wname)
     if D < 3 and (args.warmstart == "learned" or not args.no_compare):
         if os.path.exists(wpath):
@@ -471,7 +471,7 @@ def run_ours(args):
 
     # dominant kernel: the fused cell update, bound by its ALU pipe: FP64 on the FP64 path,
     # FP32 on the FP32 and mixed paths (the mixed path's double-float passes run on the FP32
-    # pipe).  Algorithmic work (SURVEY-style definition): per stencil point and Newton pass
+    # pipe).  Algorithmic work (the naive assembly): per stencil point and Newton pass
     # of a population 2(2N + N(N+1)/2) FLOP (exponent, residual, packed Jacobian), per
     # streamed point 2 n_mom FLOP; a double-float correction pass counts as a Newton pass,
     # a double-float streaming pass as streaming.  One timed launch covers args.steps steps
@@ -595,7 +595,7 @@ def run_full(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     prec = {"fp32": L.LELBM_FP32, "mixed": L.LELBM_MIXED, "fp64": L.LELBM_FP64}
-    wname = "warmstart_2d_config3.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
+    wname = "warmstart_2d_quadrants.npy" if args.workload == "riemann2d" else f"warmstart_{D}d.npy"
     wpath = os.path.join(ROOT, "paper_2508_06911_gb300", "weights", wname)
     res = {}
     rho = {}

@@ -6,7 +6,7 @@ initialised and trained by the library's own BF16/FP32 kernels (lelbm_mlp_init,
 lelbm_mlp_train).  PyTorch only provides device buffers here.
 
   python -m paper_2508_06911_gb300.warmstart --dims 1 --out warm1d.npy
-  python -m paper_2508_06911_gb300.warmstart --dims 2 --data config3 --out warm2d_config3.npy
+  python -m paper_2508_06911_gb300.warmstart --dims 2 --data quadrants --out warm2d_quadrants.npy
 """
 from __future__ import annotations
 
@@ -90,10 +90,10 @@ def record_pairs_2d(max_pairs: int):
     return X[keep].contiguous(), Y[keep].contiguous()
 
 
-def record_pairs_config3(max_pairs: int, times=(0, 3, 10, 30, 100, 300, 1000, 1999), n: int = 1024,
-                         extra_smooth: int = 2):
+def record_pairs_quadrants(max_pairs: int, times=(0, 3, 10, 30, 100, 300, 1000, 1999), n: int = 1024,
+                           extra_smooth: int = 2):
     """2D pairs along the 1024^2 four-quadrant run (the generator of the 4096^2 benchmark
-    workload, seed index 2), as the learned-start configuration prescribes: the state is
+    workload, seed index 2), the flow the learned start is meant for: the state is
     advanced by the mixed path and, at each time in `times`, copied into an FP64 handle that
     records one step (the mixed path's converged multipliers equal the FP64 path's to its
     1e-12 tolerance).  `extra_smooth` smooth random fields (seed indices 60-63: temperatures
@@ -142,8 +142,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=None, help="default: 4 (1D), 24 (2D)")
     ap.add_argument("--out", required=True)
-    ap.add_argument("--data", default="config3", choices=["config3", "diverse"],
-                    help="2D pairs: along the config-3 run (default) or from diverse fields")
+    ap.add_argument("--data", default="quadrants", choices=["quadrants", "diverse"],
+                    help="2D pairs: along the 1024^2 four-quadrant run (default) or from diverse fields")
     ap.add_argument("--lr-stages", type=int, default=3, choices=[1, 3],
                     help="2D: 1 = one stage at lr 2e-3; 3 = three stages at 2e-3, 5e-4, 1.25e-4")
     a = ap.parse_args()
@@ -153,8 +153,8 @@ def main():
     if a.dims == 1:  # pairs from the 4096-instance batch (seed index 11: not the benchmark's)
         s = Solver.riemann1d(W.riemann_1d_batch(n_batch=4096, seed_index=11))
         X, Y = record_pairs(s, steps=4, max_pairs=a.pairs)
-    elif a.data == "config3":
-        X, Y = record_pairs_config3(a.pairs)
+    elif a.data == "quadrants":
+        X, Y = record_pairs_quadrants(a.pairs)
     else:
         X, Y = record_pairs_2d(a.pairs)
     t1 = time.time()

@@ -43,7 +43,7 @@ def totals(D, M):
 
 
 def test_fp32_1d_step_and_full_run():
-    """Config 0 (400 cells, 80 steps to t = 0.2): per step and after the run."""
+    """The 400-cell 1D Riemann problem (80 steps to t = 0.2): per step and after the run."""
     w = W.riemann_1d(n=400, seed_index=0)
     p = int(w.pads[0])
     s = Solver.riemann1d(w, **FP32)
@@ -56,7 +56,7 @@ def test_fp32_1d_step_and_full_run():
     st = s.stats()
     ref = oracle_1d_instance(w, 0, nsteps)
     l1 = l1_rel(M[0, p:p + 400], ref[0, p:p + 400])
-    print(f"FP32 config 0: L1 density error {l1:.2e}, max rel {max_rel_err(M[:, p:p + 400], ref[:, p:p + 400]):.2e}")
+    print(f"FP32, 400-cell 1D Riemann problem: L1 density error {l1:.2e}, max rel {max_rel_err(M[:, p:p + 400], ref[:, p:p + 400]):.2e}")
     assert l1 < L1_TOL
     assert st.fallback_mx == 0 and st.points_32 > 0 and st.points_f == 0
     s.close()

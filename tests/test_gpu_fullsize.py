@@ -66,7 +66,7 @@ def oracle_target(w, p, tx, ty, reach):
 
 def test_four_quadrant_4096_bench_launch_sampled_against_oracle():
     w = W.riemann_2d(n=4096, seed_index=2)
-    weights = np.load(os.path.join(ROOT, "paper_2508_06911_gb300", "weights", "warmstart_2d_config3.npy"))
+    weights = np.load(os.path.join(ROOT, "paper_2508_06911_gb300", "weights", "warmstart_2d_quadrants.npy"))
     s = Solver.grid2d(w, precision=L.LELBM_MIXED)
     L.lelbm_set_mlp(s.h, weights)
     L.lelbm_set_mlp_gate(s.h, 1e-3)

@@ -57,7 +57,7 @@ def test_mixed_full_run_matches_fp64_riemann2d_1024():
     w = W.riemann_2d(n=1024, seed_index=2)
     nsteps = int(w.steps)
     assert nsteps == 2000
-    weights = np.load(os.path.join(ROOT, "paper_2508_06911_gb300", "weights", "warmstart_2d_config3.npy"))
+    weights = np.load(os.path.join(ROOT, "paper_2508_06911_gb300", "weights", "warmstart_2d_quadrants.npy"))
     m = interior_mask_2d(w)
     ref = Solver.grid2d(w)
     ref.step(nsteps)

@@ -39,7 +39,7 @@ def test_mixed_1d_step_and_run():
     M = s.get_moments()
     st = s.stats()
     ref = oracle_1d_instance(w, 0, int(w.steps[0]))
-    assert_close(M[:, p:p + 400], ref[:, p:p + 400], RUN_TOL, "mixed config 0 full run")
+    assert_close(M[:, p:p + 400], ref[:, p:p + 400], RUN_TOL, "mixed, 400-cell 1D Riemann problem, full run")
     l1 = np.abs(M[0, p:p + 400] - ref[0, p:p + 400]).sum() / np.abs(ref[0, p:p + 400]).sum()
     assert l1 < 1e-9, l1
     assert st.fallback_mx == 0 and st.points_32 > 0

@@ -199,7 +199,7 @@ def test_shipped_networks_save_newton_updates(dims, case):
 
 
 def test_learned_start_gains_time_on_the_fp64_path():
-    """What the 2D network trained along the config-3 run (weights/warmstart_2d_config3.npy)
+    """What the 2D network trained along the 1024^2 four-quadrant run (weights/warmstart_2d_quadrants.npy)
     gains in time, not only in Newton updates: on the FP64 path, where every Newton update
     is an FP64 pass over the velocity set, the learned start (the network's kernel included)
     makes the step faster than Eq. (IID13), with the same results.  The 1024^2 four-quadrant
@@ -208,7 +208,7 @@ def test_learned_start_gains_time_on_the_fp64_path():
     import os
 
     here = os.path.dirname(os.path.abspath(__file__))
-    params = np.load(os.path.join(here, "..", "paper_2508_06911_gb300", "weights", "warmstart_2d_config3.npy"))
+    params = np.load(os.path.join(here, "..", "paper_2508_06911_gb300", "weights", "warmstart_2d_quadrants.npy"))
     w = W.riemann_2d(n=1024, seed_index=2)
     res = {}
     for start in ("maxwell", "learned"):

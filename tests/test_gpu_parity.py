@@ -70,14 +70,14 @@ def test_1d_periodic_random_steps():
         s.close()
 
 
-def test_1d_full_run_config0():
+def test_1d_full_run_400_cells():
     """The 400-cell seeded Riemann problem to t = 0.2 (80 steps): <= 1e-9 after the run."""
     w = W.riemann_1d(n=400, seed_index=0)
     nsteps = int(w.steps[0])
     s, M, st = gpu_1d(w, nsteps)
     ref = oracle_1d_instance(w, 0, nsteps)
     p = int(w.pads[0])
-    assert_close(M[:, p:p + 400], ref[:, p:p + 400], RUN_TOL, "config 0 full run")
+    assert_close(M[:, p:p + 400], ref[:, p:p + 400], RUN_TOL, "400-cell 1D Riemann problem, full run")
     assert st.fallback_mx == 0
     s.close()
 
