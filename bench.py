@@ -46,12 +46,9 @@ N_M = {1: 6, 2: 11, 3: 17}
 # same kernel on the same workload and launch of one step (the summaries in profiles/).
 # Configurations without a capture report traffic null.
 DRAM_PER_STEP = {
-    ("batch1d", 4096, "fp32", "learned"): (1366.3e6, "profiles/batch_persistent_fp32_riemann1d_batch4096.md"),
-    ("batch1d", 4096, "fp64", "maxwell"): (1008.8e6, "profiles/batch_persistent_fp64_riemann1d_batch4096.md"),
-    ("riemann2d", 1024, "fp32", "learned"): (339.8e6, "profiles/cell_update_fp32_riemann2d_1024.md"),
-    ("riemann2d", 1024, "mixed", "learned"): (1115.8e6, "profiles/cell_update_mixed_riemann2d_1024.md"),
+    ("riemann2d", 1024, "mixed", "learned"): (999.0e6, "profiles/cell_update_mixed_riemann2d_1024.md"),
     # one-pass capture (dram bytes only) of the full 4096^2 workload
-    ("riemann2d", 4096, "mixed", "learned"): (18.34e9, "profiles/cell_update_mixed_riemann2d_1024.md (4096^2 capture)"),
+    ("riemann2d", 4096, "mixed", "learned"): (16.61e9, "profiles/cell_update_mixed_riemann2d_1024.md (4096^2 capture)"),
 }
 
 
