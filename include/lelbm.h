@@ -385,8 +385,9 @@ const char* lelbm_last_error(lelbm_t h);
  * fragment.  The caller passes the state buffers it already owns; the step itself
  * calls no cudaMalloc, cudaFree or other allocating routine.
  *
- * p:      the parameters of lelbm_create, with solid == NULL, precision FP64 and
- *         at most LELBM_NOALLOC_MAX_INSTANCES 1D instances; p->stream is the
+ * p:      the parameters of lelbm_create for a 1D or 2D grid, with solid == NULL,
+ *         precision FP64, deterministic == 0 and at most
+ *         LELBM_NOALLOC_MAX_INSTANCES 1D instances; p->stream is the
  *         stream to run on (NULL: the legacy default stream).
  * m_in:   device [n_mom][n_cells] moments at time t in the padded layout above;
  *         pad cells are not read (they are derived from the interior or the

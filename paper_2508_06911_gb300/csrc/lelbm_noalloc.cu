@@ -370,7 +370,7 @@ using namespace lbm;
 extern "C" int lelbm_step_noalloc(const lelbm_params* p, const double* m_in, double* m_out, lelbm_stats* stats) {
     if (!p || !m_in || !m_out) return LELBM_E_INVAL;
     if (p->dims != 1 && p->dims != 2) return LELBM_E_INVAL;
-    if (p->solid || p->precision != LELBM_FP64) return LELBM_E_INVAL;
+    if (p->solid || p->precision != LELBM_FP64 || p->deterministic) return LELBM_E_INVAL;
     if (p->nx < 1 || p->ny < 1 || (p->dims == 1 && p->ny != 1)) return LELBM_E_INVAL;
     if (!(p->K >= 0.0) || !(p->nu_shear >= 0.0) || !(p->prandtl > 0.0) || !(p->tol > 0.0)) return LELBM_E_INVAL;
     if (p->max_newton < 1 || p->max_newton > 60 || p->max_refine < 0 || p->max_refine > 4) return LELBM_E_INVAL;
