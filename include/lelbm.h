@@ -195,12 +195,17 @@ typedef struct {
 void lelbm_abi_sizes(long long* params_size, long long* stats_size);
 
 /* Fill p with the paper's defaults (n = 4, R_min = 2, refinement 3/3, tol 1e-12,
- * limiter on, omega_b = 1, Pr = 1, K = 0) for a periodic 1D grid of 1 cell. */
+ * limiter on, omega_b = 1, Pr = 1, K = 0) for a 1D grid of 1 cell, every axis periodic
+ * (x, y and z, so that setting dims and the sizes alone gives a fully periodic grid). */
 void lelbm_default_params(lelbm_params* p);
 
 /* Validate p, allocate the device state (two moment buffers, cell types, the
  * instance table, counters) and return a handle in *out.  The state starts at
- * zero; set it with lelbm_set_state or lelbm_set_moments.
+ * zero; set it with lelbm_set_state or lelbm_set_moments.  The host arrays
+ * p->lengths, p->pads and p->solid are read during the call only; the handle keeps
+ * no pointer to them or to p.  The parameters are validated before any CUDA call,
+ * so an invalid set gives E_INVAL (with the reason in lelbm_last_error(NULL)) also
+ * on a machine without a GPU.
  * Errors: E_INVAL (bad parameter), E_NOMEM, E_CUDA (no device). */
 int lelbm_create(lelbm_t* out, const lelbm_params* p);
 

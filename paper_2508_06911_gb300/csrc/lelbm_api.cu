@@ -104,6 +104,7 @@ extern "C" void lelbm_default_params(lelbm_params* p) {
     p->ny = 1;
     p->nz = 1;
     p->bc[0] = p->bc[1] = p->bc[2] = p->bc[3] = LELBM_BC_PERIODIC;
+    p->bc_z[0] = p->bc_z[1] = LELBM_BC_PERIODIC;
     p->inlet[0] = 1.0;
     p->inlet[3] = 1.0;
     p->K = 0.0;

@@ -198,23 +198,28 @@ def lelbm_abi_sizes():
 
 
 def lelbm_create(p: lelbm_params, lengths=None, solid=None, pads=None) -> int:
-    """Create a handle; ``lengths``/``pads`` (1D batch) and ``solid`` (padded uint8 mask) are host arrays."""
+    """Create a handle; ``lengths``/``pads`` (1D batch) and ``solid`` (padded uint8 mask) are host arrays.
+
+    They go into a copy of ``p`` (the library copies what it needs during the call), so the
+    caller's parameters never point at them afterwards.
+    """
+    q = lelbm_params.from_buffer_copy(p)
     keep = []
     if lengths is not None:
         arr = np.ascontiguousarray(lengths, dtype=np.int32)
         keep.append(arr)
-        p.lengths = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        p.n_batch = len(arr)
+        q.lengths = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        q.n_batch = len(arr)
     if pads is not None:
         pa = np.ascontiguousarray(pads, dtype=np.int32)
         keep.append(pa)
-        p.pads = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        q.pads = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     if solid is not None:
         s = np.ascontiguousarray(solid, dtype=np.uint8)
         keep.append(s)
-        p.solid = s.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        q.solid = s.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
     h = _H()
-    rc = load().lelbm_create(ctypes.byref(h), ctypes.byref(p))
+    rc = load().lelbm_create(ctypes.byref(h), ctypes.byref(q))
     _check(rc, None)
     return h.value
 

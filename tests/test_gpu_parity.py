@@ -161,7 +161,7 @@ def test_zero_steps_and_roundtrip():
 
 def test_invalid_arguments_are_rejected():
     p = L.lelbm_default_params()
-    p.dims = 3
+    p.dims = 4
     with pytest.raises(L.LelbmError) as e:
         L.lelbm_create(p)
     assert e.value.code == L.LELBM_E_INVAL
