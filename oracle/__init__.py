@@ -7,8 +7,9 @@ compiled without FMA contraction); this module only builds that file with gcc
 and marshals numpy arrays through ctypes.
 
 Every C function cites the equation of the paper it follows; see the header
-comment of ``lelbm_oracle.c``.  Functions without an independent pin are marked
-"parity unpinned" in their docstring.
+comment of ``lelbm_oracle.c``, which lists the parts without an independent pin
+("parity unpinned"; each is marked again at its function).  ``mlp.py`` (the
+FP64 network of the learned warm start) is pinned by calculus only.
 """
 from __future__ import annotations
 

@@ -23,8 +23,18 @@
  *   EPR Newton, Maxwellian start ..... Eq. (IID7)-(IID13)
  *   moment streaming ................. Eq. (IIE3)
  *   fluid boundaries ................. Sec. III.A
- *   solid boundaries (slip wall) ..... Sec. III.B, Eq. (IIIB10)-(IIIB15)
+ *   solid boundaries ................. Sec. III.B, Eq. (IIIB10)-(IIIB15)
+ *     (slip walls, no-slip walls at rest and moving no-slip walls)
  * Readings of passages the paper leaves open are marked "reading:" below.
+ *
+ * Parity unpinned (no test independent of this file fixes them; each place is
+ * marked "parity unpinned" below):
+ *   - how a refined point's share spreads beyond its centre of mass (the
+ *     cloud-in-cell reading in orc_step; the centre of mass itself is pinned);
+ *   - the quadrature weights dC inside the last-resort Maxwellian weights of
+ *     solve_cell (the weights' mean, variance and mass are pinned);
+ *   - the wall rules at an isolated convex corner in orc_trace_path (flat
+ *     walls and box corners are pinned by the method of images).
  *
  * Build with -ffp-contract=off: every operation then rounds once, on x86-64
  * and on aarch64 alike, so the stencil membership tests are reproducible.
@@ -546,7 +556,9 @@ static void equilibrium_constraints(int D, double RT, double* cf, double* cg)
 /* reading (failure handling, not in the paper): a solve that breaks down
  * is redone for f and g with the equilibrium constraints (omega = 1, the
  * Knudsen limiter's end state); if that also fails, the populations are the
- * Maxwellian weights of Eq. (IID12) scaled to carry the exact mass. */
+ * Maxwellian weights of Eq. (IID12) scaled to carry the exact mass.
+ * parity unpinned: the dC factor of those weights (it moves their moments by
+ * less than the quadrature error the pins allow). */
 static int solve_cell(const orc_params* p, int q, const orc_point* pts, const orc_collision* co,
                       double* popf, double* popg, orc_stats* st)
 {
@@ -740,6 +752,8 @@ static int solid_at(const orc_grid* g, int NX, int NY, int i, int j)
  * cell corner whose diagonal cell is solid reflects only the component normal
  * to a flat wall (one of the two side cells solid, the other fluid) and both
  * components otherwise; with the diagonal cell fluid it passes the corner.
+ * parity unpinned: the corner rule at an isolated convex corner, which has no
+ * image construction (conservation and mirror symmetry still hold there).
  * Returns the walls the path touched (bit 1: a slip wall, bit 2: a no-slip wall at rest,
  * bit 4: a moving no-slip wall; 0: none) and, in bits 4-5, the last no-slip boundary it
  * touched (1 at rest, 2 moving); *fi, *fj receive the final cell, off[] the final offset
@@ -947,7 +961,8 @@ static void stream_one(const orc_grid* g, int NX, int NY, int NZ, int ix, int iy
  * T_N(c_i) rho f'_i and T_N(c_i) rho K RT g'_i to x + c_i (Eq. IIE3).
  * reading: a refined point lands off the lattice; its fractions are shared
  * between the cells it overlaps by cloud-in-cell weights (cell averaging,
- * Eq. IIA10-11).  Min and Mout are SoA [nmom][NY*NX]; Min is not modified.
+ * Eq. IIA10-11).  parity unpinned: that spread beyond the share's centre of
+ * mass.  Min and Mout are SoA [nmom][NY*NX]; Min is not modified.
  * Returns 0, or -1 on allocation failure. */
 int orc_step(const orc_grid* g, const orc_params* p, const double* Min, double* Mout, orc_stats* st)
 {

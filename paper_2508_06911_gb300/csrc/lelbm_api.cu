@@ -584,9 +584,15 @@ extern "C" int lelbm_set_state(lelbm_t h, const double* rho, const double* u, co
         if (!ok) return fail(h, LELBM_E_STATE, "non-physical state at cell %lld", i);
     }
     double *dr = nullptr, *du = nullptr, *dT = nullptr;
-    CUDA_TRY(h, cudaMalloc((void**)&dr, sizeof(double) * n));
-    CUDA_TRY(h, cudaMalloc((void**)&du, sizeof(double) * n * h->D));
-    CUDA_TRY(h, cudaMalloc((void**)&dT, sizeof(double) * n));
+    if (cudaMalloc((void**)&dr, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc((void**)&du, sizeof(double) * n * h->D) != cudaSuccess ||
+        cudaMalloc((void**)&dT, sizeof(double) * n) != cudaSuccess) {
+        cudaFree(dr);
+        cudaFree(du);
+        cudaFree(dT);
+        cudaGetLastError();  // clear the allocation error so later launch checks do not see it
+        return fail(h, LELBM_E_NOMEM, "set_state: device allocation of the fields failed");
+    }
     cudaMemcpyAsync(dr, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(du, u, sizeof(double) * n * h->D, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dT, RT, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);

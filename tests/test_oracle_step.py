@@ -302,3 +302,60 @@ def test_failed_solve_falls_back_to_equilibrium_constraints():
     assert st_eq.fallback_eq == 0
     scale = np.abs(out_eq).max(axis=1, keepdims=True)
     assert (np.abs(out_bad - out_eq) / scale).max() < 1e-13
+
+
+# The last resort of the failure handling: when even the equilibrium constraints cannot be met
+# (here forced by allowing a single Newton update, which cannot reach 1e-12 on a discrete
+# stencil), the populations are Maxwellian weights on the cell's own stencil, normalised to carry
+# the cell's mass.  Such weights are a quadrature of the Gaussian of mean u and variance RT per
+# axis: on a stencil reaching about n_conf = 4 standard deviations the truncated tails and the
+# lattice's aliasing (Poisson summation) leave the mean within 1e-2 sqrt(RT) and the variance
+# within 3 % (cold refined stencils; about 1e-3 on the integer lattice).  A weight taken at
+# c instead of c - u, a flipped exponent sign or a missing normalisation each fail these.
+# Dropping the quadrature weights dC of a refined stencil moves the mean and variance by less
+# than the quadrature's own error (a few parts per thousand), so they are not pinned here.
+LAST_RESORT_CASES = [
+    (1, 0.0, (2.5,), 1.0),
+    (1, 2.0, (0.3,), 0.2),  # refined (RT < 4/9): dC of 1/2 and 1
+    (2, 0.0, (2.5, -1.2), 1.0),
+    (2, 2.0, (0.4, 0.7), 0.15),  # refined: dC of 1/4, 1/2 and 1
+    (2, 0.0, (0.0, 0.0), 8.0),
+    (3, 0.0, (1.5, 0.2, -0.7), 1.0),
+]
+
+
+@pytest.mark.parametrize("D,K,u,RT", LAST_RESORT_CASES)
+def test_last_resort_weights_are_a_gaussian_quadrature(D, K, u, RT):
+    p = O.params(D, K, max_iter=1)
+    u = np.array(u)
+    M = O.eq_moments(D, K, 1.3, u, RT)
+    _, c, dC, pf, pg, level = O.cell_populations(p, M)
+    assert level == 2  # both the solve and the equilibrium-constraint solve failed
+    assert (pf > 0).all()
+    assert abs(pf.sum() - 1.0) < 1e-14
+    mean = pf @ c
+    assert np.abs(mean - u).max() < 1e-2 * np.sqrt(RT), mean - u
+    var = (pf * ((c - u) ** 2).sum(1)).sum() / D
+    assert abs(var / RT - 1.0) < 0.03, var / RT
+    if K > 0:
+        np.testing.assert_array_equal(pg, pf)  # the phonons take the same weights
+
+
+def test_last_resort_step_conserves_mass_and_stays_uniform():
+    """A uniform periodic grid in which every cell takes the last resort: each cell falls back
+    once, mass is conserved to rounding, the state stays uniform (every cell emits the same
+    populations) and the momentum is rho times the quadrature's mean, within 1e-2 of rho u."""
+    D, K, nx, ny = 2, 0.0, 8, 6
+    g = O.grid(D, nx, ny, periodic=(True, True))
+    p = O.params(D, K, max_iter=1)
+    rho = np.full((ny, nx), 1.3)
+    u = np.zeros((D, ny, nx))
+    u[0], u[1] = 0.4, 0.7
+    RT = np.full((ny, nx), 1.0)
+    M = O.state_from_primitives(g, p, rho, u, RT)
+    st = O.Stats()
+    out = O.step(g, p, M, st)
+    assert st.fallback_mx == nx * ny and st.fallback_eq == 0
+    assert abs(out[0].sum() / M[0].sum() - 1.0) < 1e-13
+    assert (np.abs(out - out[:, :1]).max(axis=1) <= 1e-13 * np.abs(out).max(axis=1)).all()
+    assert np.abs(out[1:3, 0] / out[0, 0] - np.array([0.4, 0.7])).max() < 1e-2
