@@ -76,9 +76,10 @@ INVALID = {
 
 def _create_rc(p, lengths=None, pads=None, solid=None):
     try:
-        L.lelbm_create(p, lengths=lengths, pads=pads, solid=solid)
+        h = L.lelbm_create(p, lengths=lengths, pads=pads, solid=solid)
     except L.LelbmError as e:
         return e.code, str(e)
+    L.lelbm_destroy(h)
     return L.LELBM_OK, ""
 
 
