@@ -10,7 +10,7 @@ cell (fluid-boundary fill, collision, LAS, EPR, moment streaming).  MLUPS = inte
 updates per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload batch1d|hotbox2d|riemann2d|cylinder2d]
+                  [--workload batch1d|hotbox2d|riemann2d|cylinder2d|hotbox3d|riemann3d]
 
 --impl reference times the plain FP64 CPU oracle (the correctness reference) on a
 bounded sample of the same workload.  Under torchrun each rank runs its own batch
